@@ -1,0 +1,51 @@
+"""Each pin must bite: plant a plausible mistake in a copy of the oracle, on the
+CPU, and check that the pin suite fails on it.
+
+Mutants cover a dropped term, a wrong sign, a transposed operand or index and a
+wrong factor in every oracle routine the GPU path is compared with.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle as oracle_mod
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(os.path.dirname(HERE), "oracle", "oracle.c")
+
+MUTANTS = {
+    "noise_term_dropped": ("for (int64_t i = 0; i < n; ++i) K[i * n + i] += hyp[2];", ""),
+    "kernel_factor_2": ("/ (2.0 * l * l));\n}", "/ (l * l));\n}"),
+    "cholesky_transposed": ("s -= L[i * n + k] * L[j * n + k];", "s -= L[i * n + k] * L[k * n + j];"),
+    "forward_sign": ("s -= L[i * n + k] * x[k];", "s += L[i * n + k] * x[k];"),
+    "backward_transposed": ("s -= L[k * n + i] * x[k];", "s -= L[i * n + k] * x[k];"),
+    "mean_uses_beta": ("s += Kc[i * n + j] * alpha[j];", "s += Kc[i * n + j] * beta[j];"),
+    "variance_sign": ("var[i] = prior - s;", "var[i] = prior + s;"),
+    "covariance_sign": ("cov[i * m + k] -= s;", "cov[i * m + k] += s;"),
+    "nlml_half_dropped": ("return 0.5 * fit + logdet_half", "return fit + logdet_half"),
+    "grad_l_factor": ("g_l += w * kf * r2 / (l * l);", "g_l += w * kf * r2 / l;"),
+    "grad_noise_delta_dropped": ("if (i == j) g_s2 += w * s2;", "g_s2 += w * s2;"),
+    "adam_bias_correction_dropped": ("double mhat = mom[p] / (1.0 - pow(beta1, (double)t));",
+                                     "double mhat = mom[p];"),
+    "mlp_relu_mask_dropped": ("d2[k] = h2[k] > 0.0 ? a : 0.0;", "d2[k] = a;"),
+    "summary_lag_off_by_one": ("c += (y[i] - ybar) * (y[i + lag] - ybar);",
+                               "c += (y[i] - ybar) * (y[i + lag - 1] - ybar);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    orig, repl = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(orig) == 1, f"mutation site for {name} not unique/present"
+    mut_c = tmp_path / "oracle_mut.c"
+    mut_c.write_text(src.replace(orig, repl))
+    (tmp_path / "oracle.h").write_text(open(os.path.join(os.path.dirname(SRC), "oracle.h")).read())
+    lib = oracle_mod.build(str(mut_c), str(tmp_path / "liboracle_mut.so"))
+    env = dict(os.environ, GPRAT_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(HERE, "test_oracle_pins.py")],
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
