@@ -1,0 +1,163 @@
+/*
+ * gprat_gb.h - C ABI of the GB300-native exact Gaussian-process regression
+ * library (GPRat, arXiv 2505.00136).
+ *
+ * The calls follow the paper's statement of the problem (Section 4.3): a GP
+ * object is created from training data, a tile configuration and the
+ * hyperparameters of the squared-exponential kernel (Eq. 2); it can then be
+ * factored (tiled Cholesky, Section 4.2 / Fig. 1), asked for predictions with
+ * or without uncertainty (Eqs. 3-4), for its loss (Eq. 5) and its gradient,
+ * and optimised with Adam (Section 4.1).
+ *
+ * Conventions shared by every call:
+ *  - Matrices are row-major float64: X is n x d, Xs is m x d, cov is m x m.
+ *  - Pointers may be host or device memory; each call detects which with
+ *    cudaPointerGetAttributes.  Host outputs are written before the call
+ *    returns; device outputs are written in order on the handle's stream.
+ *  - gp_create copies X and y into device memory owned by the handle; the
+ *    caller owns every output buffer; gp_destroy frees all handle memory.
+ *  - Work is issued on gp_options.cuda_stream (NULL: the legacy default
+ *    stream).  Calls that return host scalars or status from the device
+ *    synchronise that stream.
+ *  - No call throws, aborts or exits.  Each returns a gp_status;
+ *    gp_last_error_info gives detail (failing pivot row for GP_ERR_NOT_PD,
+ *    the cudaError_t for GP_ERR_CUDA).
+ *  - Hyperparameters are given on their natural scale (length scale l,
+ *    vertical scale nu, noise variance sigma^2); internally, and for
+ *    gradients and Adam, the library works with (log l, log nu, log sigma^2).
+ *  - Ragged sizes are allowed: n need not be a multiple of the tile size (the
+ *    factor is padded with an identity block that changes no result), m is
+ *    any value >= 1, n >= 1, 1 <= d <= 1024.
+ */
+#ifndef GPRAT_GB_H
+#define GPRAT_GB_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_handle* gp_t;
+
+typedef enum {
+    GP_OK = 0,
+    GP_ERR_ARG = 1,     /* bad argument (NULL, size, option); nothing was changed */
+    GP_ERR_NOT_PD = 2,  /* K + sigma^2 I not positive definite in working precision */
+    GP_ERR_CUDA = 3,    /* a CUDA runtime call failed */
+    GP_ERR_OOM = 4,     /* device allocation failed */
+    GP_ERR_TIMEOUT = 5, /* a bounded device-side wait expired (persistent scheduler) */
+    GP_ERR_STATE = 6    /* call not valid in the handle's current state */
+} gp_status;
+
+typedef enum { GP_FP64 = 0, GP_MIXED = 1 } gp_precision;
+
+typedef enum {
+    GP_SCHED_STREAM = 0,     /* one launch per tile step, stream ordered */
+    GP_SCHED_PERSISTENT = 1  /* persistent kernel walking the tile DAG */
+} gp_scheduler;
+
+/* Eq. 2 hyperparameters.  trainable[p] = 0 freezes parameter p in gp_optimize
+ * (the paper's trainable-parameter flags, Section 4.3). */
+typedef struct {
+    double lengthscale; /* l > 0 */
+    double vertical;    /* nu > 0 (linear factor, not squared) */
+    double noise_var;   /* sigma^2 >= 0 */
+    int trainable[3];   /* order: l, nu, sigma^2 */
+} gp_hyper;
+
+typedef struct {
+    int n_tiles;            /* tiles per dimension T (paper: 1, 4, 16); tile size is
+                               ceil(n / T) rounded up to a multiple of 64 */
+    gp_precision prec;      /* GP_FP64 or GP_MIXED */
+    int noisy_test_var;     /* 1: add sigma^2 to predictive (co)variances */
+    double refine_tol;      /* GP_MIXED: stop refinement at ||r|| / ||y|| < tol */
+    int refine_max_iter;    /* GP_MIXED: at most this many refinement sweeps */
+    double adam_beta1, adam_beta2, adam_eps;
+    void* cuda_stream;      /* cudaStream_t used for all work */
+    gp_scheduler scheduler; /* how the Cholesky tile DAG is executed */
+} gp_options;
+
+/* Fills defaults: n_tiles 16, FP64, latent variance, refine_tol 1e-14,
+ * refine_max_iter 20, Adam (0.9, 0.999, 1e-8), default stream, stream scheduler. */
+void gp_default_options(gp_options* opt);
+
+/* Creates a GP over n training points X (n x d) with targets y (n).  Copies
+ * X and y to the device.  Fails with GP_ERR_ARG on NULL pointers, n < 1,
+ * d < 1 or d > 1024, n_tiles < 1, non-positive l or nu or negative sigma^2. */
+gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d,
+                    const gp_hyper* hyper, const gp_options* opt, gp_t* out);
+
+/* Assembles K = K_f + sigma^2 I in lower tiles (Eq. 2) and factors it in
+ * place, K = L L^T, by the tiled right-looking Cholesky of Fig. 1 (POTRF,
+ * TRSM, SYRK, GEMM tiles), then solves beta = L^{-1} y and
+ * alpha = L^{-T} beta.  Idempotent until the hyperparameters change.
+ * Synchronises.  GP_ERR_NOT_PD: gp_last_error_info gives the first row whose
+ * pivot was not positive. */
+gp_status gp_factor(gp_t h);
+
+/* Predictive mean at m test points (Eq. 3): mean = K_{Z*,Z} K^{-1} y. */
+gp_status gp_predict_mean(gp_t h, const double* Xs, int64_t m, double* mean);
+
+/* Mean and predictive variance (diagonal of Eq. 4):
+ * var_i = k(x*_i, x*_i) - || L^{-1} k_*i ||^2 (+ sigma^2 if noisy_test_var). */
+gp_status gp_predict_var(gp_t h, const double* Xs, int64_t m, double* mean, double* var);
+
+/* Mean and full posterior covariance (Eq. 4), cov m x m row-major:
+ * cov = K_{Z*,Z*} - V^T V with V = L^{-1} K_{Z*,Z}^T. */
+gp_status gp_predict_full_cov(gp_t h, const double* Xs, int64_t m, double* mean, double* cov);
+
+/* Negative log marginal likelihood, the negative of Eq. 5:
+ * 1/2 y^T K^{-1} y + 1/2 log|K| + n/2 log(2 pi).  Synchronises. */
+gp_status gp_nlml(gp_t h, double* nlml);
+
+/* NLML and its gradient with respect to (log l, log nu, log sigma^2):
+ * g_p = 1/2 tr((K^{-1} - alpha alpha^T) dK/dtheta_p), with K^{-1} formed as
+ * L^{-T} L^{-1} from tiles and dK/dtheta regenerated inside the reduction (no
+ * dK is stored).  Synchronises. */
+gp_status gp_nlml_grad(gp_t h, double* nlml, double grad_log_theta[3]);
+
+/* steps Adam iterations (lr, the handle's beta1/beta2/eps) on the trainable
+ * log-hyperparameters, each on the NLML gradient at the current point.
+ * nlml_hist (host or device, steps entries, may be NULL) receives the NLML
+ * before each update.  Adam state persists across calls (see gp_get_state). */
+gp_status gp_optimize(gp_t h, int steps, double lr, double* nlml_hist);
+
+gp_status gp_get_hyper(gp_t h, gp_hyper* out);
+/* Sets new hyperparameters; invalidates the factor.  Does not reset Adam. */
+gp_status gp_set_hyper(gp_t h, const gp_hyper* hyper);
+
+/* Optimiser checkpoint: theta[3] (log scale), m[3], v[3] and step count t. */
+typedef struct {
+    double log_theta[3];
+    double adam_m[3];
+    double adam_v[3];
+    int64_t adam_t;
+} gp_state;
+gp_status gp_get_state(gp_t h, gp_state* out);
+gp_status gp_set_state(gp_t h, const gp_state* st);
+
+/* Copies the Cholesky factor L (n x n row-major, upper triangle zero) to L_out
+ * (host or device).  Factors first if needed. */
+gp_status gp_get_factor(gp_t h, double* L_out);
+
+/* Copies alpha = K^{-1} y (n entries, host or device), the weights of the
+ * predictive mean (Eq. 3: mean = K_{Z*,Z} alpha).  Factors first if needed. */
+gp_status gp_get_alpha(gp_t h, double* alpha_out);
+
+/* Tile geometry and last-call diagnostics. */
+typedef struct {
+    int64_t n, d, tile, n_tiles, n_padded;
+    int64_t device_bytes;      /* bytes currently held on the device */
+    int refine_iters;          /* GP_MIXED: sweeps used by the last alpha solve */
+    double refine_residual;    /* GP_MIXED: ||y - K alpha|| / ||y|| after refinement */
+} gp_info_t;
+gp_status gp_info(gp_t h, gp_info_t* out);
+
+int64_t gp_last_error_info(gp_t h);
+const char* gp_status_str(gp_status s);
+void gp_destroy(gp_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,103 @@
+// Internal declarations of the GB300 exact-GP library: handle, tile geometry,
+// launch helpers.  Not part of the C ABI (see include/gprat_gb.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gprat_gb.h"
+
+// Square tiles of TB x TB doubles; the tile size b is a multiple of TB.
+#define GP_TB 64
+#define GP_THREADS 256
+
+// Device-side hyperparameter record, updated in place by the Adam kernel so
+// that an optimisation loop never round-trips through the host.
+struct GpHyperDev {
+    double l, nu, s2;         // natural scale (Eq. 2)
+    double inv2l2;            // 1 / (2 l^2)
+    double log_theta[3];      // (log l, log nu, log sigma^2)
+};
+
+struct GpAdamDev {
+    double m[3], v[3];
+    double t;                 // step count as a double (Adam's bias correction)
+};
+
+// Lower-triangular tile storage: tile (i, j), i >= j, holds rows i*b.. and
+// columns j*b.. of the matrix, row-major with leading dimension b, at
+// offset tri_index(i, j) * b * b.  Only T (T + 1) / 2 tiles exist.
+__host__ __device__ inline int64_t tri_index(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
+
+struct gp_handle {
+    int64_t n, d, b, T, Np;   // Np = T * b >= n; rows n..Np-1 are identity padding
+    gp_options opt;
+    cudaStream_t st;
+    int device;
+
+    // Resident training data (padded rows are zero).
+    double* X;                // Np x d
+    double* y;                // Np
+    GpHyperDev* hyp;          // device copy
+    GpHyperDev h_hyp;         // host mirror
+    int trainable[3];
+    GpAdamDev* adam;
+
+    // Factor and solves.
+    double* L;                // T(T+1)/2 tiles: K, then L in place
+    double* Linv;             // T tiles: inverses of the diagonal tiles of L
+    double* beta;             // L^{-1} y
+    double* alpha;            // K^{-1} y
+    double* work;             // Np scratch vector
+    double* logdet_part;      // T partial sums of log L_ii
+    unsigned long long* info; // first failing pivot row (ULLONG_MAX: none)
+    double* scal;             // device scalars: [0] nlml, [1..3] grad, [4..] reductions
+    bool factored;
+
+    // Gradient buffers (allocated on first use).
+    double* Xinv;             // T(T+1)/2 tiles of L^{-1}
+    double* Kinv;             // T(T+1)/2 tiles of K^{-1} (lower)
+    double* gpart;            // per-block partial gradient sums
+    int64_t gpart_cap;
+
+    // Prediction workspace (grown on demand).
+    int64_t m_cap;            // capacity in test points (multiple of 64)
+    double* Xs;               // m_cap x d
+    double* B;                // Np x m_cap: K_{Z*,Z}^T, overwritten by the solve
+    double* V;                // Np x m_cap: L^{-1} K_{Z*,Z}^T
+    double* part;             // (Np/64) x m_cap x 2 partial column sums
+    double* outm;             // m_cap mean
+    double* outv;             // m_cap var
+    double* cov;              // m_cap x m_cap (full covariance), allocated on demand
+    int64_t cov_cap;
+
+    int64_t bytes;            // device bytes held
+    int64_t last_info;
+    int refine_iters;
+    double refine_residual;
+};
+
+// ---------------------------------------------------------------- kernels.cu
+namespace gpk {
+void assemble_train(gp_t h);                                   // K tiles into h->L
+void assemble_cross(gp_t h, int64_t m, int64_t ldm);           // B = K_{Z*,Z}^T (Np x ldm)
+void assemble_test_prior(gp_t h, int64_t m, double* out);      // out = K_{Z*,Z*} (+ noise), m x m
+void factor_fp64(gp_t h);                                      // tiled Cholesky in place
+void solve_lower(gp_t h, const double* rhs, double* out);      // out = L^{-1} rhs
+void solve_upper(gp_t h, const double* rhs, double* out);      // out = L^{-T} rhs
+void nlml_reduce(gp_t h);                                      // scal[0] = NLML
+void predict_solve(gp_t h, int64_t m, int64_t ldm);            // V, partial sums
+void predict_finish(gp_t h, int64_t m, int64_t ldm, bool want_var);  // outm, outv
+void predict_mean_only(gp_t h, int64_t m, int64_t ldm);      // outm = K_{Z*,Z} alpha
+void full_cov(gp_t h, int64_t m, int64_t ldm, double* cov);    // cov -= V^T V (mirrored)
+void inverse_tiles(gp_t h);                                    // Xinv = L^{-1}, Kinv = K^{-1}
+void adjoint_grad(gp_t h);                                     // scal[1..3] = grad
+void adam_step(gp_t h, double lr, double* hist_slot);          // Adam on log theta
+void copy_factor_dense(gp_t h, double* out);                   // L as dense n x n
+void set_info_none(gp_t h);
+}  // namespace gpk
+
+#define GP_CUDA_OK(call)                                                   \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return e_;                                  \
+    } while (0)

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every symbol include/*.h declares.
+
+No compute call is made here (no GPU): only argument validation that returns
+before any CUDA call.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_00136_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(gp_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_paper_calls():
+    names = declared_functions()
+    for required in ["gp_create", "gp_factor", "gp_predict_mean", "gp_predict_var",
+                     "gp_predict_full_cov", "gp_nlml", "gp_nlml_grad", "gp_optimize", "gp_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_declares_same_names(lib):
+    from paper_2505_00136_gb300 import gprat
+    for n in declared_functions():
+        assert hasattr(gprat, n), n
+
+
+def test_invalid_arguments_rejected_before_any_cuda_call(lib):
+    from paper_2505_00136_gb300 import gprat as g
+    X = np.zeros((4, 2))
+    y = np.zeros(4)
+    h = g._H()
+    hp = g.gp_hyper(1.0, 1.0, 0.1, (ctypes.c_int * 3)(1, 1, 1))
+    opt = g.default_options()
+    assert opt.n_tiles == 16 and opt.adam_beta1 == 0.9
+    px, py = X.ctypes.data, y.ctypes.data
+    calls = [
+        (None, py, 4, 2, hp, opt),          # NULL X
+        (px, py, 0, 2, hp, opt),            # n < 1
+        (px, py, 4, 0, hp, opt),            # d < 1
+        (px, py, 4, 2000, hp, opt),         # d > 1024
+    ]
+    for args in calls:
+        st = g.gp_create(args[0], args[1], args[2], args[3], ctypes.byref(args[4]),
+                         ctypes.byref(args[5]), ctypes.byref(h))
+        assert st == g.GP_ERR_ARG
+    bad = g.gp_hyper(-1.0, 1.0, 0.1, (ctypes.c_int * 3)(1, 1, 1))
+    assert g.gp_create(px, py, 4, 2, ctypes.byref(bad), ctypes.byref(opt), ctypes.byref(h)) == g.GP_ERR_ARG
+    opt.n_tiles = 0
+    assert g.gp_create(px, py, 4, 2, ctypes.byref(hp), ctypes.byref(opt), ctypes.byref(h)) == g.GP_ERR_ARG
+    assert g.gp_factor(None) == g.GP_ERR_ARG
+    assert g.gp_status_str(g.GP_ERR_NOT_PD) == b"matrix not positive definite"
