@@ -1,0 +1,329 @@
+"""Benchmark of the exact-GP hot path on one GB300 (or N replicas).
+
+Workload (default): N = 32768 training and M = 8192 test points of the seeded
+mass-spring-damper generator, 8 lagged-input regressors, 128 x 128 tiles of
+256, (l, nu, sigma^2) = (1, 1, 0.1).  Inputs are resident in HBM before the
+timed region; the factor alone (4.3 GB of tiles) is far larger than L2.
+
+One step = one pass of the whole hot path:
+  set_hyper(theta0) ; gp_predict(Xs -> mean, var, full cov)      (assembly, Cholesky,
+                                                                  solves, cross-covariance,
+                                                                  multi-RHS solve, mean,
+                                                                  variance, covariance)
+                    ; gp_optimize(1 step, reusing the factor)    (NLML, K^{-1}, adjoint
+                                                                  gradient, Adam)
+Headline value: predict+variance ms (the predict call minus its covariance
+phase), plus NLML+grad steps/s, both from per-launch CUDA events of the timed
+steps.  --impl reference times the plain FP64 CPU oracle on a bounded sample of
+the same workload and scales it by the algorithmic flop count.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "predict+variance ms & NLML+grad steps/s @n=32768; mixed vs FP64 at 1e-8 rel"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+NOMINAL_BF16_TFLOPS = 2250.0      # dense, per GPU
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--m", type=int, default=8192)
+    ap.add_argument("--d", type=int, default=8)
+    ap.add_argument("--tiles", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=4096)
+    ap.add_argument("--cpu-sample-m", type=int, default=128)
+    return ap.parse_args()
+
+
+HYP0 = (1.0, 1.0, 0.1)
+
+
+def predict_flops(n, m):
+    """Algorithmic flops of predict with variance: Cholesky n^3/3 + forward solve n^2 m."""
+    return n ** 3 / 3.0 + float(n) * n * m
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def fp64_peak():
+    """FP64 tensor peak: measured bf16 burst x nominal FP64/BF16 ratio (or the fallback)."""
+    pk = peaks()
+    if pk and "bf16_tflops" in pk:
+        return pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS, \
+            "of measured (bf16 burst x nominal fp64/bf16)"
+    return 1900.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS, "of fallback (1.9 PF bf16 x nominal fp64/bf16)"
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+def cpu_baseline(args, d, seed):
+    import oracle
+    from paper_2505_00136_gb300 import datagen as dg
+    orc = oracle.Oracle()
+    ns, ms = args.cpu_sample_n, args.cpu_sample_m
+    X, y, Xs, _ = dg.msd_dataset(ns, ms, d, seed)
+    t0 = time.perf_counter()
+    orc.predict(X, y, Xs, HYP0)
+    dt = time.perf_counter() - t0
+    scale = predict_flops(args.n, args.m) / predict_flops(ns, ms)
+    return {"value": dt * scale * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"oracle predict mean+var at N={ns}, M={ms}, D={d} took {dt:.2f} s on 1 core; "
+                      f"scaled x{scale:.0f} by (N^3/3 + N^2 M) to N={args.n}, M={args.m}"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    seed = 1002
+    samples = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args, args.d, seed)
+        if i >= args.warmup:
+            samples.append(cb["value"])
+    value = float(np.mean(samples))
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic mass-spring-damper (seeded)",
+            "config": workload_config(args),
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"exact GP regression, SE kernel, N={args.n} train, M={args.m} test, "
+                        f"D={args.d} lagged regressors, {args.tiles} tiles/dim",
+            "n_train": args.n, "n_test": args.m, "regressors": args.d, "tiles_per_dim": args.tiles,
+            "hyper": list(HYP0), "precision": args.precision,
+            "l2": "inputs larger than L2 (factor tiles 4.3 GB at N=32768)"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def update_flops(T, b):
+    """Algorithmic flops of all trailing SYRK/GEMM launches: sum_k sum over trailing tiles."""
+    tot = 0.0
+    for tt in range(1, T):
+        tot += (tt * (tt - 1)) * b ** 3 + tt * float(b) ** 3   # GEMM: 2b^3 each (tt(tt-1)/2 of them); SYRK: b^3
+    return tot
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2505_00136_gb300 import datagen as dg
+    from paper_2505_00136_gb300 import gprat
+
+    seed = 1002 + rank
+    Xh, yh, Xsh, _ = dg.msd_dataset(args.n, args.m, args.d, seed)
+    X = torch.from_numpy(Xh).to(dev)
+    y = torch.from_numpy(yh).to(dev)
+    Xs = torch.from_numpy(Xsh).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    gp = gprat.GP(X, y, HYP0, n_tiles=args.tiles, precision=args.precision)
+    info = gp.info()
+    T, b = info["n_tiles"], info["tile"]
+
+    def step():
+        gp.set_hyper(HYP0)
+        gp.predict(Xs, mean=True, var=True, cov=True)
+        gp.optimize(1, lr=0.1)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    gp.profile(True)
+    gp.profile_read()
+    l0 = gp.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    total_ms = e0.elapsed_time(e1)
+    launches = gp.launch_count() - l0
+    prof = gp.profile_read()
+    gp.profile(False)
+    K = args.steps
+    ph = {k: v[0] / K for k, v in prof.items()}
+    factor_ms = ph["assemble"] + ph["potrf"] + ph["trsm"] + ph["update"] + ph["solve"]
+    # predict+variance = factor + cross-covariance + multi-RHS solve + reductions of the predict call
+    predict_var_ms = factor_ms + ph["cross"] + ph["vsolve"]
+    grad_ms = factor_ms + ph["trtri"] + ph["lauum"] + ph["adjoint"] + ph["adam"]
+    ms_per_step = total_ms / K
+    vals = torch.tensor([predict_var_ms, grad_ms, ms_per_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    predict_var_ms, grad_ms, ms_per_step = (float(v) for v in vals.cpu())
+
+    # roofline of the dominant kernel family (FP64 tensor pipe, DMMA)
+    peak, peak_note = fp64_peak()
+    upd_launch_ms = prof["update"][0] / max(prof["update"][1], 1)
+    upd_flops_per_launch = update_flops(T, b) / max(T - 1, 1)
+    achieved = upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "kernel": "k_update (trailing SYRK/GEMM, mma.sync f64)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_note": peak_note, "traffic": None,
+            "algorithmic_flops_per_launch": upd_flops_per_launch,
+            "avg_launch_ms": upd_launch_ms, "launches": prof["update"][1] // K}
+    chol_flops = args.n ** 3 / 3.0
+    chol_ms = ph["potrf"] + ph["trsm"] + ph["update"]
+
+    line = {"metric": METRIC, "value": predict_var_ms, "unit": "ms", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "mixed",
+            "data": "synthetic mass-spring-damper (seeded), inputs resident in HBM",
+            "config": workload_config(args),
+            "nlml_grad_steps_per_s": 1e3 / grad_ms, "nlml_grad_ms": grad_ms,
+            "cholesky_tflops": chol_flops / (chol_ms * 1e-3) / 1e12,
+            "cholesky_frac_of_fp64_peak": chol_flops / (chol_ms * 1e-3) / 1e12 / peak,
+            "phases_ms": {k: round(v, 3) for k, v in ph.items()},
+            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary()}
+
+    if rank == 0 and world == 1 and not args.no_e2e:
+        line["e2e"] = e2e(args, gprat, torch, dev, Xh, yh, Xsh)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, args.d, seed)
+    gp.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e(args, gprat, torch, dev, Xh, yh, Xsh):
+    """predict+variance through the public API from pinned host buffers:
+    H2D of X, y, Xs and D2H of mean and var inside the timed region."""
+    Xp = torch.from_numpy(Xh).pin_memory()
+    yp = torch.from_numpy(yh).pin_memory()
+    Xsp = torch.from_numpy(Xsh).pin_memory()
+    mean = torch.empty(args.m, dtype=torch.float64).pin_memory()
+    var = torch.empty(args.m, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with gprat.GP(Xp, yp, HYP0, n_tiles=args.tiles, precision=args.precision,
+                  stream=stream.cuda_stream) as g2:
+        st = gprat._lib.gp_predict_var(g2.h, Xsp.data_ptr(), args.m, mean.data_ptr(), var.data_ptr())
+        if st != 0:
+            raise gprat.GPError(st, -1, "gp_predict_var")
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return {"value": e0.elapsed_time(e1), "unit": "ms",
+            "h2d_bytes_per_step": int(Xh.nbytes + yh.nbytes + Xsh.nbytes),
+            "d2h_bytes_per_step": int(mean.numel() * 8 + var.numel() * 8),
+            "note": "gp_create + gp_predict_var + gp_destroy from pinned host buffers, 1 step"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,6 +140,40 @@ gp_status gp_set_state(gp_t h, const gp_state* st);
  * (host or device).  Factors first if needed. */
 gp_status gp_get_factor(gp_t h, double* L_out);
 
+/* General prediction: any of mean (m), var (m) and cov (m x m) may be NULL;
+ * all requested outputs come from one forward solve V = L^{-1} K_{Z*,Z}^T
+ * (Eqs. 3-4).  At least one output must be non-NULL. */
+gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* var, double* cov);
+
+/* Per-launch timing of the library's kernels with CUDA events on the handle's
+ * stream, accumulated by phase.  Off by default. */
+typedef enum {
+    GP_PH_ASSEMBLE = 0, /* K tiles (Eq. 2) */
+    GP_PH_POTRF,        /* diagonal-tile Cholesky + inverse */
+    GP_PH_TRSM,         /* panel solves */
+    GP_PH_UPDATE,       /* trailing SYRK / GEMM */
+    GP_PH_SOLVE,        /* beta, alpha (single right-hand side) */
+    GP_PH_CROSS,        /* K_{Z*,Z}, K_{Z*,Z*} */
+    GP_PH_VSOLVE,       /* V = L^{-1} K_{Z*,Z}^T with fused row sums */
+    GP_PH_REDUCE,       /* mean / variance / NLML / gradient reductions */
+    GP_PH_COV,          /* K_{Z*,Z*} - V^T V */
+    GP_PH_TRTRI,        /* L^{-1} tiles */
+    GP_PH_LAUUM,        /* K^{-1} = L^{-T} L^{-1} tiles */
+    GP_PH_ADJOINT,      /* fused dK/dtheta reduction */
+    GP_PH_ADAM,
+    GP_PH_REFINE,       /* mixed path: FP64 residuals and corrections */
+    GP_PH_OTHER,
+    GP_NPHASE
+} gp_phase;
+/* enable != 0 turns per-launch event timing on. */
+gp_status gp_profile(gp_t h, int enable);
+/* Synchronises, then writes per-phase milliseconds and launch counts
+ * accumulated since the last read (arrays of nphase <= GP_NPHASE entries,
+ * either may be NULL) and resets them. */
+gp_status gp_profile_read(gp_t h, double* ms, int64_t* launches, int nphase);
+/* Kernels launched by this handle since it was created. */
+int64_t gp_launch_count(gp_t h);
+
 /* Copies alpha = K^{-1} y (n entries, host or device), the weights of the
  * predictive mean (Eq. 3: mean = K_{Z*,Z} alpha).  Factors first if needed. */
 gp_status gp_get_alpha(gp_t h, double* alpha_out);

@@ -92,18 +92,54 @@ gp_status copy_any(gp_t h, void* dst, const void* src, int64_t count)
 
 gp_status ensure_grad_buffers(gp_t h)
 {
-    if (h->Xinv) return GP_OK;
     gp_status s;
     const int64_t tiles = ntri(h) * h->b * h->b;
     const int64_t P = h->b / TB;
+    if (h->opt.prec == GP_MIXED) {
+        if (h->ZP) return GP_OK;
+        if ((s = dev_alloc(h, &h->ZP, 3 * tiles)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->U32, tiles)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->Kinv32, tiles)) != GP_OK) return s;
+        h->gpart_cap = ntri(h) * P * P * 3;
+        return dev_alloc(h, &h->gpart, h->gpart_cap);
+    }
+    if (h->Xinv) return GP_OK;
     if ((s = dev_alloc(h, &h->Xinv, tiles)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->Kinv, tiles)) != GP_OK) return s;
     h->gpart_cap = ntri(h) * P * P * 3;
     return dev_alloc(h, &h->gpart, h->gpart_cap);
 }
 
+gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
+{
+    const int64_t ldm = round_up(m, 2 * TB);
+    if (ldm <= h->m_cap) return GP_OK;
+    const int64_t old = h->m_cap;
+    dev_free(h, &h->Xs, old * h->d);
+    dev_free(h, &h->R32, old * h->Np);
+    dev_free(h, &h->RP, 3 * old * h->b);
+    dev_free(h, &h->WP, 3 * old * h->Np);
+    dev_free(h, &h->mpart, old * (h->Np / TB));
+    dev_free(h, &h->vpart, old * (h->Np / (2 * TB)));
+    dev_free(h, &h->outm, old);
+    dev_free(h, &h->outv, old);
+    h->m_cap = 0;
+    gp_status s;
+    if ((s = dev_alloc(h, &h->Xs, ldm * h->d)) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->R32, ldm * h->Np)) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->RP, 3 * ldm * h->b)) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->WP, 3 * ldm * h->Np)) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->mpart, ldm * (h->Np / TB))) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->vpart, ldm * (h->Np / (2 * TB)))) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->outm, ldm)) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->outv, ldm)) != GP_OK) return s;
+    h->m_cap = ldm;
+    return GP_OK;
+}
+
 gp_status ensure_predict_space(gp_t h, int64_t m)
 {
+    if (h->opt.prec == GP_MIXED) return ensure_predict_space_mixed(h, m);
     const int64_t ldm = round_up(m, TB);
     if (ldm <= h->m_cap) return GP_OK;
     const int64_t old = h->m_cap;
@@ -137,15 +173,21 @@ gp_status ensure_cov_space(gp_t h, int64_t m)
     return s;
 }
 
-// Assemble, factor and solve for beta and alpha; NLML into scal[0].  No sync.
-void launch_factor(gp_t h)
+// Assemble, factor and solve for beta and alpha; NLML into scal[0].  No sync,
+// no reset of the failure flag (a failure stays visible to later kernels).
+void launch_factor_body(gp_t h)
 {
-    gpk::set_info_none(h);
     gpk::assemble_train(h);
     gpk::factor_fp64(h);
     gpk::solve_lower(h, h->y, h->beta);
     gpk::solve_upper(h, h->beta, h->alpha);
     gpk::nlml_reduce(h);
+}
+
+void launch_factor(gp_t h)
+{
+    gpk::set_info_none(h);
+    launch_factor_body(h);
 }
 
 gp_status read_info(gp_t h)
@@ -162,11 +204,46 @@ gp_status read_info(gp_t h)
     return GP_OK;
 }
 
+// GP_MIXED: mixed factor, then alpha by iterative refinement against the
+// FP64 residual (host loop; one small device-to-host read per sweep).
+gp_status factor_mixed_refined(gp_t h)
+{
+    gpk::set_info_none(h);
+    gpk::assemble_train(h);
+    gpk::factor_mixed(h);
+    gp_status s = check_launch(h);
+    if (s != GP_OK) return s;
+    if ((s = read_info(h)) != GP_OK) return s;
+    gpk::refine_start(h, h->y, h->alpha);
+    double prev = INFINITY, nrm[2];
+    int it = 0;
+    while (it < h->opt.refine_max_iter) {
+        gpk::refine_step(h, h->y, h->alpha, h->res, h->norms);
+        ++it;
+        if ((s = cuda_status(h, cudaMemcpyAsync(nrm, h->norms, sizeof(nrm), cudaMemcpyDeviceToHost, h->st))) != GP_OK)
+            return s;
+        if ((s = sync(h)) != GP_OK) return s;
+        const double rel = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
+        h->refine_residual = rel;
+        if (!(rel > h->opt.refine_tol) || rel > 0.5 * prev) break;
+        prev = rel;
+    }
+    h->refine_iters = it;
+    gpk::nlml_mixed(h);
+    return check_launch(h);
+}
+
 gp_status ensure_factored(gp_t h)
 {
     if (h->factored) return GP_OK;
+    gp_status s;
+    if (h->opt.prec == GP_MIXED) {
+        if ((s = factor_mixed_refined(h)) != GP_OK) return s;
+        h->factored = true;
+        return GP_OK;
+    }
     launch_factor(h);
-    gp_status s = check_launch(h);
+    s = check_launch(h);
     if (s != GP_OK) return s;
     if ((s = read_info(h)) != GP_OK) return s;
     h->factored = true;
@@ -180,9 +257,9 @@ gp_status predict_common(gp_t h, const double* Xs, int64_t m, int64_t* ldm_out)
     gp_status s;
     if ((s = ensure_factored(h)) != GP_OK) return s;
     if ((s = ensure_predict_space(h, m)) != GP_OK) return s;
-    *ldm_out = round_up(m, TB);
+    *ldm_out = round_up(m, h->opt.prec == GP_MIXED ? 2 * TB : TB);
     if ((s = copy_any(h, h->Xs, Xs, m * h->d)) != GP_OK) return s;
-    gpk::assemble_cross(h, m, *ldm_out);
+    if (h->opt.prec != GP_MIXED) gpk::assemble_cross(h, m, *ldm_out);
     return check_launch(h);
 }
 
@@ -194,6 +271,85 @@ gp_status finish_outputs(gp_t h, bool any_host)
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- launch profiling
+bool prof_begin(gp_t h, int phase)
+{
+    if (h->ev_used + 2 > h->ev_cap) {
+        int64_t cap = h->ev_cap ? 2 * h->ev_cap : 4096;
+        cudaEvent_t* pool = (cudaEvent_t*)realloc(h->ev_pool, (size_t)cap * sizeof(cudaEvent_t));
+        int* ph = (int*)realloc(h->ev_phase, (size_t)(cap / 2) * sizeof(int));
+        if (!pool || !ph) {
+            if (pool) h->ev_pool = pool;
+            if (ph) h->ev_phase = ph;
+            return false;
+        }
+        for (int64_t i = h->ev_cap; i < cap; ++i) cudaEventCreate(&pool[i]);
+        h->ev_pool = pool;
+        h->ev_phase = ph;
+        h->ev_cap = cap;
+    }
+    h->ev_phase[h->ev_used / 2] = phase;
+    cudaEventRecord(h->ev_pool[h->ev_used], h->st);
+    return true;
+}
+
+void prof_end(gp_t h)
+{
+    cudaEventRecord(h->ev_pool[h->ev_used + 1], h->st);
+    h->ev_used += 2;
+}
+
+namespace {
+gp_status prof_collect(gp_t h)
+{
+    if (h->ev_used == 0) return GP_OK;
+    gp_status s = sync(h);
+    if (s != GP_OK) return s;
+    for (int64_t i = 0; i < h->ev_used; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int ph = h->ev_phase[i / 2];
+        h->prof_ms[ph] += ms;
+        h->prof_cnt[ph] += 1;
+    }
+    h->ev_used = 0;
+    return GP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gp_status gp_profile(gp_t h, int enable)
+{
+    if (!h) return GP_ERR_ARG;
+    gp_status s = prof_collect(h);
+    h->prof_on = enable != 0;
+    return s;
+}
+
+gp_status gp_profile_read(gp_t h, double* ms, int64_t* launches, int nphase)
+{
+    if (!h || nphase < 0 || nphase > GP_NPHASE) return GP_ERR_ARG;
+    gp_status s = prof_collect(h);
+    if (s != GP_OK) return s;
+    for (int p = 0; p < nphase; ++p) {
+        if (ms) ms[p] = h->prof_ms[p];
+        if (launches) launches[p] = h->prof_cnt[p];
+    }
+    for (int p = 0; p < GP_NPHASE; ++p) {
+        h->prof_ms[p] = 0.0;
+        h->prof_cnt[p] = 0;
+    }
+    return GP_OK;
+}
+
+int64_t gp_launch_count(gp_t h) { return h ? h->launches : -1; }
+
+}  // extern "C"
 
 extern "C" {
 
@@ -235,9 +391,14 @@ void gp_destroy(gp_t h)
     cudaStreamSynchronize(h->st);
     void* ptrs[] = {h->X, h->y, h->hyp, h->adam, h->L, h->Linv, h->beta, h->alpha, h->work,
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
-                    h->V, h->part, h->outm, h->outv, h->cov};
+                    h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
+                    h->PA, h->D64, h->X64, h->r32, h->t32, h->w32, h->res, h->norms, h->R32, h->RP,
+                    h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (int64_t i = 0; i < h->ev_cap; ++i) cudaEventDestroy(h->ev_pool[i]);
+    free(h->ev_pool);
+    free(h->ev_phase);
     delete h;
 }
 
@@ -262,7 +423,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     h->n = n;
     h->d = d;
     int64_t per = (n + opt.n_tiles - 1) / opt.n_tiles;
-    h->b = round_up(per, TB);
+    h->b = round_up(per, opt.prec == GP_MIXED ? 2 * TB : TB);
     h->T = (n + h->b - 1) / h->b;
     h->Np = h->T * h->b;
     for (int p = 0; p < 3; ++p) h->trainable[p] = hyper->trainable[p] ? 1 : 0;
@@ -287,6 +448,21 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     TRY(dev_alloc(h, &h->logdet_part, h->T));
     TRY(dev_alloc(h, &h->info, 1));
     TRY(dev_alloc(h, &h->scal, 16));
+    if (opt.prec == GP_MIXED) {
+        const int64_t bb = h->b * h->b;
+        TRY(dev_alloc(h, &h->A32, tiles));
+        TRY(dev_alloc(h, &h->LP, 3 * tiles));
+        TRY(dev_alloc(h, &h->Linv32, h->T * bb));
+        TRY(dev_alloc(h, &h->LinvP, 3 * h->T * bb));
+        TRY(dev_alloc(h, &h->PA, 3 * (h->T > 1 ? h->T - 1 : 1) * bb));
+        TRY(dev_alloc(h, &h->D64, bb));
+        TRY(dev_alloc(h, &h->X64, bb));
+        TRY(dev_alloc(h, &h->r32, h->Np));
+        TRY(dev_alloc(h, &h->t32, h->Np));
+        TRY(dev_alloc(h, &h->w32, h->Np));
+        TRY(dev_alloc(h, &h->res, h->Np));
+        TRY(dev_alloc(h, &h->norms, 2));
+    }
     TRY(cuda_status(h, cudaMemsetAsync(h->X, 0, (size_t)(h->Np * d) * sizeof(double), h->st)));
     TRY(cuda_status(h, cudaMemsetAsync(h->y, 0, (size_t)h->Np * sizeof(double), h->st)));
     TRY(cuda_status(h, cudaMemsetAsync(h->adam, 0, sizeof(GpAdamDev), h->st)));
@@ -305,48 +481,62 @@ gp_status gp_factor(gp_t h)
     return ensure_factored(h);
 }
 
-gp_status gp_predict_mean(gp_t h, const double* Xs, int64_t m, double* mean)
+gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* var, double* cov)
 {
-    if (!mean) return GP_ERR_ARG;
+    if (!mean && !var && !cov) return GP_ERR_ARG;
     int64_t ldm;
     gp_status s = predict_common(h, Xs, m, &ldm);
     if (s != GP_OK) return s;
-    gpk::predict_mean_only(h, m, ldm);
-    if ((s = copy_any(h, mean, h->outm, m)) != GP_OK) return s;
-    return finish_outputs(h, !is_device_ptr(mean));
+    bool any_host = false;
+    if (h->opt.prec == GP_MIXED) {
+        gpk::predict_mixed(h, m, ldm, var != nullptr || cov != nullptr);
+    } else if (!var && !cov) {  // Eq. 3 alone: one pass K_{Z*,Z} alpha, no solve
+        gpk::predict_mean_only(h, m, ldm);
+    } else {
+        gpk::predict_solve(h, m, ldm);
+        gpk::predict_finish(h, m, ldm, var != nullptr);
+    }
+    if (cov) {
+        const bool cov_dev = is_device_ptr(cov);
+        double* target = cov;
+        if (!cov_dev) {
+            if ((s = ensure_cov_space(h, m)) != GP_OK) return s;
+            target = h->cov;
+        }
+        if (h->opt.prec == GP_MIXED) gpk::full_cov_mixed(h, m, ldm, target);
+        else gpk::full_cov(h, m, ldm, target);
+        if (!cov_dev) {
+            if ((s = copy_any(h, cov, target, m * m)) != GP_OK) return s;
+            any_host = true;
+        }
+    }
+    if (mean) {
+        if ((s = copy_any(h, mean, h->outm, m)) != GP_OK) return s;
+        any_host = any_host || !is_device_ptr(mean);
+    }
+    if (var) {
+        if ((s = copy_any(h, var, h->outv, m)) != GP_OK) return s;
+        any_host = any_host || !is_device_ptr(var);
+    }
+    return finish_outputs(h, any_host);
+}
+
+gp_status gp_predict_mean(gp_t h, const double* Xs, int64_t m, double* mean)
+{
+    if (!mean) return GP_ERR_ARG;
+    return gp_predict(h, Xs, m, mean, nullptr, nullptr);
 }
 
 gp_status gp_predict_var(gp_t h, const double* Xs, int64_t m, double* mean, double* var)
 {
     if (!var) return GP_ERR_ARG;
-    int64_t ldm;
-    gp_status s = predict_common(h, Xs, m, &ldm);
-    if (s != GP_OK) return s;
-    gpk::predict_solve(h, m, ldm);
-    gpk::predict_finish(h, m, ldm, true);
-    if (mean && (s = copy_any(h, mean, h->outm, m)) != GP_OK) return s;
-    if ((s = copy_any(h, var, h->outv, m)) != GP_OK) return s;
-    return finish_outputs(h, (mean && !is_device_ptr(mean)) || !is_device_ptr(var));
+    return gp_predict(h, Xs, m, mean, var, nullptr);
 }
 
 gp_status gp_predict_full_cov(gp_t h, const double* Xs, int64_t m, double* mean, double* cov)
 {
     if (!cov) return GP_ERR_ARG;
-    int64_t ldm;
-    gp_status s = predict_common(h, Xs, m, &ldm);
-    if (s != GP_OK) return s;
-    gpk::predict_solve(h, m, ldm);
-    gpk::predict_finish(h, m, ldm, false);
-    const bool cov_dev = is_device_ptr(cov);
-    double* target = cov;
-    if (!cov_dev) {
-        if ((s = ensure_cov_space(h, m)) != GP_OK) return s;
-        target = h->cov;
-    }
-    gpk::full_cov(h, m, ldm, target);
-    if (mean && (s = copy_any(h, mean, h->outm, m)) != GP_OK) return s;
-    if (!cov_dev && (s = copy_any(h, cov, target, m * m)) != GP_OK) return s;
-    return finish_outputs(h, (mean && !is_device_ptr(mean)) || !cov_dev);
+    return gp_predict(h, Xs, m, mean, nullptr, cov);
 }
 
 gp_status gp_nlml(gp_t h, double* nlml)
@@ -364,7 +554,8 @@ gp_status gp_nlml_grad(gp_t h, double* nlml, double grad[3])
     gp_status s = ensure_factored(h);
     if (s != GP_OK) return s;
     if ((s = ensure_grad_buffers(h)) != GP_OK) return s;
-    gpk::inverse_tiles(h);
+    if (h->opt.prec == GP_MIXED) gpk::inverse_mixed(h);
+    else gpk::inverse_tiles(h);
     gpk::adjoint_grad(h);
     if ((s = check_launch(h)) != GP_OK) return s;
     double tmp[4];
@@ -391,19 +582,27 @@ gp_status gp_optimize(gp_t h, int steps, double lr, double* nlml_hist)
     } else {
         hist = nlml_hist;
     }
+    // A factor that is current for the starting hyperparameters is reused by
+    // the first iteration; every later iteration refactors at the updated ones.
+    const bool reuse_first = h->factored;
     h->factored = false;
-    gpk::set_info_none(h);
+    if (!reuse_first) gpk::set_info_none(h);
+    const bool mixed = h->opt.prec == GP_MIXED;
     for (int it = 0; it < steps; ++it) {
-        gpk::assemble_train(h);
-        gpk::factor_fp64(h);
-        gpk::solve_lower(h, h->y, h->beta);
-        gpk::solve_upper(h, h->beta, h->alpha);
-        gpk::nlml_reduce(h);
-        gpk::inverse_tiles(h);
+        if (!(it == 0 && reuse_first)) {
+            if (mixed) {
+                // the refinement loop synchronises per sweep; a failed factor ends the loop
+                if ((s = factor_mixed_refined(h)) != GP_OK) break;
+            } else {
+                launch_factor_body(h);
+            }
+        }
+        if (mixed) gpk::inverse_mixed(h);
+        else gpk::inverse_tiles(h);
         gpk::adjoint_grad(h);
         gpk::adam_step(h, lr, hist ? hist + it : nullptr);
     }
-    s = check_launch(h);
+    if (s == GP_OK) s = check_launch(h);
     if (s == GP_OK) s = read_info(h);
     if (s == GP_OK && nlml_hist && !hist_dev) {
         s = copy_any(h, nlml_hist, hist, steps);
@@ -488,13 +687,17 @@ gp_status gp_get_factor(gp_t h, double* L_out)
     if (!h || !L_out) return GP_ERR_ARG;
     gp_status s = ensure_factored(h);
     if (s != GP_OK) return s;
+    auto dense = [&](double* out) {
+        if (h->opt.prec == GP_MIXED) gpk::copy_factor_dense_mixed(h, out);
+        else gpk::copy_factor_dense(h, out);
+    };
     if (is_device_ptr(L_out)) {
-        gpk::copy_factor_dense(h, L_out);
+        dense(L_out);
         return finish_outputs(h, false);
     }
     double* tmp = nullptr;
     if ((s = dev_alloc(h, &tmp, h->n * h->n)) != GP_OK) return s;
-    gpk::copy_factor_dense(h, tmp);
+    dense(tmp);
     s = copy_any(h, L_out, tmp, h->n * h->n);
     if (s == GP_OK) s = finish_outputs(h, true);
     dev_free(h, &tmp, h->n * h->n);

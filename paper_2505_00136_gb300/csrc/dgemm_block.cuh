@@ -77,7 +77,7 @@ __device__ __forceinline__ void dmma(double (&c)[2], double a, double b)
 // acc += A[:, kb:ke] * Bt[:, kb:ke]^T.  smem must hold DG_SMEM_DOUBLES.
 // Starts and ends with a CTA barrier, so callers may overwrite the operands
 // (in place) right after it returns.
-__device__ void dgemm_acc(DAcc& acc, const DView& A, const DView& B, int64_t kb, int64_t ke,
+static __device__ __forceinline__ void dgemm_acc(DAcc& acc, const DView& A, const DView& B, int64_t kb, int64_t ke,
                           double* smem)
 {
     __syncthreads();

@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 exact-GP library: handle, tile geometry,
 // launch helpers.  Not part of the C ABI (see include/gprat_gb.h).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,11 +71,51 @@ struct gp_handle {
     double* cov;              // m_cap x m_cap (full covariance), allocated on demand
     int64_t cov_cap;
 
+    // Mixed precision (GP_MIXED).  h->L then holds the FP64 K (never factored).
+    float* A32;               // T(T+1)/2 tiles: FP32 K, then the mixed factor in place
+    __nv_bfloat16* LP;        // T(T+1)/2 tiles x 3 BF16 planes of the off-diagonal factor tiles
+    float* Linv32;            // T tiles: inverses of the diagonal factor tiles
+    __nv_bfloat16* LinvP;     // T tiles x 3 planes of Linv32
+    __nv_bfloat16* PA;        // (T-1) tiles x 3 planes: panel operand scratch
+    double* D64;              // b x b FP64 diagonal tile scratch
+    double* X64;              // b x b FP64 inverse scratch
+    float *r32, *t32, *w32;   // Np FP32 vectors of the refinement solves
+    double* res;              // Np FP64 residual
+    double* norms;            // 2 FP64 norms
+    float* R32;               // m_cap x Np: K_{Z*,Z}, overwritten by the W solve
+    __nv_bfloat16 *RP, *WP;   // planes: RP 3 x m_cap x b (scratch), WP 3 x m_cap x Np (all of W)
+    double* mpart;            // (Np/64) x m_cap mean partial sums
+    double* vpart;            // (Np/128) x m_cap variance partial sums
+    __nv_bfloat16* ZP;        // T(T+1)/2 tiles x 3 planes of (L^{-1})^T tiles (gradient)
+    float* U32;               // T(T+1)/2 tiles: TRTRI accumulators (gradient)
+    float* Kinv32;            // T(T+1)/2 tiles: K^{-1} lower (gradient)
+
     int64_t bytes;            // device bytes held
     int64_t last_info;
     int refine_iters;
     double refine_residual;
+
+    // Launch accounting and optional per-launch event timing (gp_profile).
+    int64_t launches;
+    bool prof_on;
+    cudaEvent_t* ev_pool;     // grown on demand
+    int64_t ev_cap, ev_used;
+    int* ev_phase;            // phase of each recorded (start, stop) pair
+    double prof_ms[GP_NPHASE];
+    int64_t prof_cnt[GP_NPHASE];
 };
+
+// Launch wrapper: counts the launch and, when profiling is on, brackets it
+// with a pair of events tagged with its phase.
+bool prof_begin(gp_t h, int phase);
+void prof_end(gp_t h);
+#define GPK_LAUNCH(h, phase, kern, grid, block, smem, ...)                   \
+    do {                                                                     \
+        bool p_ = (h)->prof_on && prof_begin((h), (phase));                  \
+        kern<<<(grid), (block), (smem), (h)->st>>>(__VA_ARGS__);             \
+        (h)->launches++;                                                     \
+        if (p_) prof_end(h);                                                 \
+    } while (0)
 
 // ---------------------------------------------------------------- kernels.cu
 namespace gpk {
@@ -94,6 +135,20 @@ void adjoint_grad(gp_t h);                                     // scal[1..3] = g
 void adam_step(gp_t h, double lr, double* hist_slot);          // Adam on log theta
 void copy_factor_dense(gp_t h, double* out);                   // L as dense n x n
 void set_info_none(gp_t h);
+// FP64 POTRF + inverse of one b x b diagonal tile A (in place) into X; adds
+// sum log L_ii to *logdet_slot; a failing pivot records row0 + its row.
+void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot);
+
+// kernels_mixed.cu
+void factor_mixed(gp_t h);                                     // mixed factor of h->A32
+void refine_start(gp_t h, const double* rhs, double* x);       // x = L~^{-T} L~^{-1} rhs
+void refine_step(gp_t h, const double* rhs, double* x, double* r, double* norms);  // r = rhs - K x; x += correction
+void residual64(gp_t h, const double* x, const double* y, double* r);              // r = y - K x (FP64)
+void nlml_mixed(gp_t h);                                       // scal[0] from y^T alpha and log|K|
+void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var);
+void copy_factor_dense_mixed(gp_t h, double* out);
+void full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov);  // cov (prefilled prior) -= W W^T
+void inverse_mixed(gp_t h);                                    // Kinv32 = (L~ L~^T)^{-1}
 }  // namespace gpk
 
 #define GP_CUDA_OK(call)                                                   \

@@ -10,68 +10,12 @@
 
 #include "dgemm_block.cuh"
 #include "gp_internal.cuh"
+#include "se_common.cuh"
 
 namespace gpk {
 
 constexpr int TB = GP_TB;
 constexpr int NT = GP_THREADS;
-
-__device__ __forceinline__ bool failed(const unsigned long long* info)
-{
-    return *(volatile const unsigned long long*)info != ~0ull;
-}
-
-// Row index i' of the u-th entry of a lower triangle enumerated row by row.
-__device__ __forceinline__ void tri_decode(int64_t u, int64_t& i, int64_t& j)
-{
-    int64_t r = (int64_t)((sqrt(8.0 * (double)u + 1.0) - 1.0) * 0.5);
-    while (r * (r + 1) / 2 > u) --r;
-    while ((r + 1) * (r + 2) / 2 <= u) ++r;
-    i = r;
-    j = u - r * (r + 1) / 2;
-}
-
-// ---------------------------------------------------------------- distances
-// r2[a][c] for rows p0 + ty + 16a of P and rows q0 + tx + 16c of Q
-// (ty = tid / 16, tx = tid % 16), summed over the d coordinates by direct
-// differences.  Rows at or beyond np / nq contribute garbage that callers mask.
-__device__ void dist_block(double (&r2)[4][4], const double* P, int64_t p0, int64_t np,
-                           const double* Q, int64_t q0, int64_t nq, int64_t d, double* sm)
-{
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    double* sp = sm;
-    double* sq = sm + 64 * 17;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) r2[a][c] = 0.0;
-    for (int64_t d0 = 0; d0 < d; d0 += 16) {
-        __syncthreads();
-        for (int idx = tid; idx < 1024; idx += NT) {
-            int r = idx >> 4, k = idx & 15;
-            int64_t gp = p0 + r, gq = q0 + r;
-            bool kin = d0 + k < d;
-            sp[r * 17 + k] = (gp < np && kin) ? P[gp * d + d0 + k] : 0.0;
-            sq[r * 17 + k] = (gq < nq && kin) ? Q[gq * d + d0 + k] : 0.0;
-        }
-        __syncthreads();
-        const int kmax = (int)((d - d0) < 16 ? (d - d0) : 16);
-        for (int k = 0; k < kmax; ++k) {
-            double pa[4], qc[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) pa[a] = sp[(ty + 16 * a) * 17 + k];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) qc[c] = sq[(tx + 16 * c) * 17 + k];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    double t = pa[a] - qc[c];
-                    r2[a][c] = fma(t, t, r2[a][c]);
-                }
-        }
-    }
-}
 
 // ---------------------------------------------------------------- assembly (Eq. 2)
 enum SeMode { SE_TRAIN = 0, SE_CROSS = 1, SE_PRIOR = 2 };
@@ -79,7 +23,7 @@ enum SeMode { SE_TRAIN = 0, SE_CROSS = 1, SE_PRIOR = 2 };
 // SE_TRAIN : lower tiles of K = K_f + sigma^2 I, identity on padding rows.
 // SE_CROSS : B (Np x ldm) = K_{Z*,Z}^T, zero outside n x m.
 // SE_PRIOR : out (m x m, ld m) = K_{Z*,Z*} (+ sigma^2 I when noisy).
-__global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, int64_t ldo,
+__global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, float* out32, int64_t ldo,
                                                  const double* X, int64_t n, const double* Xs,
                                                  int64_t m, int64_t d, int64_t b, int P,
                                                  const GpHyperDev* hyp, int noisy)
@@ -87,6 +31,7 @@ __global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, int64_t 
     __shared__ double sm[2 * 64 * 17];
     int64_t r0, c0;          // global row / column of the block's first element
     double* dst;             // block origin
+    float* dst32 = nullptr;  // optional FP32 copy (SE_TRAIN, mixed precision)
     int64_t ld;
     const double *Pp = X, *Qp = X;
     int64_t np = n, nq = n;
@@ -99,6 +44,7 @@ __global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, int64_t 
         c0 = tj * b + cb * TB;
         ld = b;
         dst = out + tri_index(ti, tj) * b * b + (int64_t)rb * TB * b + cb * TB;
+        if (out32) dst32 = out32 + tri_index(ti, tj) * b * b + (int64_t)rb * TB * b + cb * TB;
     } else if (mode == SE_CROSS) {
         r0 = (int64_t)blockIdx.x * TB;
         c0 = (int64_t)blockIdx.y * TB;
@@ -137,6 +83,7 @@ __global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, int64_t 
                 v = nu * exp(-r2[a][c] * c2) + ((noisy && gi == gj) ? s2 : 0.0);
             }
             dst[(int64_t)rr * ld + cc] = v;
+            if (dst32) dst32[(int64_t)rr * ld + cc] = (float)v;
         }
 }
 
@@ -145,20 +92,18 @@ __global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, int64_t 
 // panels), then the blocked inverse of its factor into Linv[k].  Adds
 // sum log L_ii of the tile to logdet_part[k]; on a non-positive pivot records
 // the global row in *info and stops.
-__global__ __launch_bounds__(NT) void k_potrf_diag(double* Lt, double* Linv, int64_t b, int64_t k,
-                                                   double* logdet_part, unsigned long long* info)
+__global__ __launch_bounds__(NT) void k_potrf_diag(double* A, double* Xk, int64_t b, int64_t row0,
+                                                   double* logdet_slot, unsigned long long* info)
 {
     extern __shared__ double smem[];
     double* gsm = smem;                              // dgemm staging
     double* S = smem + DG_SMEM_DOUBLES;              // 64 x 65 factor block
     double* Iv = S + 64 * 65;                        // 64 x 65 inverse block
-    __shared__ double logacc;
+    __shared__ double logacc, rcp;
     __shared__ int fail;
     if (failed(info)) return;
     const int tid = threadIdx.x;
     const int P = (int)(b / TB);
-    double* A = Lt + tri_index(k, k) * b * b;
-    double* Xk = Linv + k * b * b;
     if (tid == 0) { logacc = 0.0; fail = 0; }
 
     for (int p = 0; p < P; ++p) {
@@ -184,16 +129,16 @@ __global__ __launch_bounds__(NT) void k_potrf_diag(double* Lt, double* Linv, int
                 if (piv > 0.0) {
                     double s = sqrt(piv);
                     S[j * 65 + j] = s;
-                    logacc += log(s);
+                    rcp = 1.0 / s;
                 } else {
                     fail = 1;
-                    atomicMin(info, (unsigned long long)(k * b + p * TB + j));
+                    atomicMin(info, (unsigned long long)(row0 + p * TB + j));
                 }
             }
             __syncthreads();
             if (fail) return;
-            const double djj = S[j * 65 + j];
-            for (int r = j + 1 + tid; r < 64; r += NT) S[r * 65 + j] /= djj;
+            const double djj_inv = rcp;
+            for (int r = j + 1 + tid; r < 64; r += NT) S[r * 65 + j] *= djj_inv;
             __syncthreads();
             const int ty = tid >> 4, tx = tid & 15;
             for (int r = j + 1 + ty; r < 64; r += 16) {
@@ -201,6 +146,12 @@ __global__ __launch_bounds__(NT) void k_potrf_diag(double* Lt, double* Linv, int
                 for (int c = j + 1 + tx; c <= r; c += 16) S[r * 65 + c] -= lr * S[c * 65 + j];
             }
             __syncthreads();
+        }
+        if (tid < 32) {  // sum log L_jj of the block
+            double lg = log(S[tid * 65 + tid]) + log(S[(tid + 32) * 65 + tid + 32]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
+            if (tid == 0) logacc += lg;
         }
         // inverse of the 64 x 64 factor, row by row; 4 threads per column
         {
@@ -265,7 +216,7 @@ __global__ __launch_bounds__(NT) void k_potrf_diag(double* Lt, double* Linv, int
         }
     }
     __syncthreads();
-    if (tid == 0) logdet_part[k] = logacc;
+    if (tid == 0) *logdet_slot = logacc;
 }
 
 // Panel TRSM of step k: L_ik = A_ik L_kk^{-T} = A_ik Linv_kk^T for i > k.
@@ -614,7 +565,8 @@ __global__ __launch_bounds__(NT) void k_lauum(const double* Xinv, double* Kinv, 
 //   sum W_ij K_f,ij r2_ij,  sum W_ij K_f,ij,  sum_i W_ii
 // with W = K^{-1} - alpha alpha^T, weight 2 off the diagonal; dK/dtheta is
 // regenerated from X here and never stored.
-__global__ __launch_bounds__(NT) void k_adjoint(const double* Kinv, const double* alpha, const double* X,
+template <class KT>
+__global__ __launch_bounds__(NT) void k_adjoint(const KT* Kinv, const double* alpha, const double* X,
                                                 int64_t n, int64_t d, int64_t b,
                                                 const GpHyperDev* hyp, double* gpart)
 {
@@ -630,7 +582,7 @@ __global__ __launch_bounds__(NT) void k_adjoint(const double* Kinv, const double
         double r2[4][4];
         dist_block(r2, X, r0, n, X, c0, n, d, sm);
         const double nu = hyp->nu, c2 = hyp->inv2l2;
-        const double* tile = Kinv + tri_index(i, j) * b * b + (int64_t)rb * TB * b + cb * TB;
+        const KT* tile = Kinv + tri_index(i, j) * b * b + (int64_t)rb * TB * b + cb * TB;
         const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -639,7 +591,7 @@ __global__ __launch_bounds__(NT) void k_adjoint(const double* Kinv, const double
                 int rr = ty + 16 * a, cc = tx + 16 * c;
                 int64_t gi = r0 + rr, gj = c0 + cc;
                 if (gi >= n || gj >= n || gj > gi) continue;
-                double w = tile[(int64_t)rr * b + cc] - alpha[gi] * alpha[gj];
+                double w = (double)tile[(int64_t)rr * b + cc] - alpha[gi] * alpha[gj];
                 double kf = nu * exp(-r2[a][c] * c2);
                 double wt = (gi == gj) ? 1.0 : 2.0;
                 s_l = fma(wt * w * kf, r2[a][c], s_l);
@@ -729,40 +681,47 @@ static int grid_for(int64_t work, int per = NT)
     return (int)g;
 }
 
-static bool g_attr_done = false;
+constexpr int POTRF_SMEM = DG_SMEM_BYTES + 2 * 64 * 65 * 8;
+
 static void ensure_attrs()
 {
-    if (g_attr_done) return;
-    const int dg = DG_SMEM_BYTES;
-    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         DG_SMEM_BYTES + 2 * 64 * 65 * 8);
-    (void)dg;
-    g_attr_done = true;
+    static int done_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done_dev == dev) return;
+    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, POTRF_SMEM);
+    done_dev = dev;
 }
 
 void assemble_train(gp_t h)
 {
     const int P = (int)(h->b / TB);
     dim3 grid((unsigned)(h->T * (h->T + 1) / 2), (unsigned)(P * P));
-    k_se_block<<<grid, NT, 0, h->st>>>(SE_TRAIN, h->L, h->b, h->X, h->n, nullptr, 0, h->d, h->b, P,
-                                       h->hyp, 0);
+    GPK_LAUNCH(h, GP_PH_ASSEMBLE, k_se_block, grid, NT, 0, SE_TRAIN, h->L, h->A32, h->b, h->X, h->n,
+               (const double*)nullptr, (int64_t)0, h->d, h->b, P, h->hyp, 0);
 }
 
 void assemble_cross(gp_t h, int64_t m, int64_t ldm)
 {
     dim3 grid((unsigned)(h->Np / TB), (unsigned)(ldm / TB));
-    k_se_block<<<grid, NT, 0, h->st>>>(SE_CROSS, h->B, ldm, h->X, h->n, h->Xs, m, h->d, h->b, 1,
-                                       h->hyp, 0);
+    GPK_LAUNCH(h, GP_PH_CROSS, k_se_block, grid, NT, 0, SE_CROSS, h->B, (float*)nullptr, ldm, h->X, h->n, h->Xs, m,
+               h->d, h->b, 1, h->hyp, 0);
 }
 
 void assemble_test_prior(gp_t h, int64_t m, double* out)
 {
     unsigned g = (unsigned)((m + TB - 1) / TB);
-    k_se_block<<<dim3(g, g), NT, 0, h->st>>>(SE_PRIOR, out, m, nullptr, 0, h->Xs, m, h->d, h->b, 1,
-                                             h->hyp, h->opt.noisy_test_var);
+    GPK_LAUNCH(h, GP_PH_COV, k_se_block, dim3(g, g), NT, 0, SE_PRIOR, out, (float*)nullptr, m, (const double*)nullptr,
+               (int64_t)0, h->Xs, m, h->d, h->b, 1, h->hyp, h->opt.noisy_test_var);
 }
 
-void set_info_none(gp_t h) { k_set_u64<<<1, 1, 0, h->st>>>(h->info, ~0ull); }
+void set_info_none(gp_t h) { GPK_LAUNCH(h, GP_PH_OTHER, k_set_u64, 1, 1, 0, h->info, ~0ull); }
+
+void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot)
+{
+    ensure_attrs();
+    GPK_LAUNCH(h, GP_PH_POTRF, k_potrf_diag, 1, NT, POTRF_SMEM, A, X, b, row0, logdet_slot, h->info);
+}
 
 void factor_fp64(gp_t h)
 {
@@ -770,14 +729,14 @@ void factor_fp64(gp_t h)
     const int64_t T = h->T, b = h->b;
     const int P = (int)(b / TB);
     for (int64_t k = 0; k < T; ++k) {
-        k_potrf_diag<<<1, NT, DG_SMEM_BYTES + 2 * 64 * 65 * 8, h->st>>>(h->L, h->Linv, b, k,
-                                                                        h->logdet_part, h->info);
+        potrf_diag_launch(h, h->L + tri_index(k, k) * b * b, h->Linv + k * b * b, b, k * b,
+                          h->logdet_part + k);
         if (k + 1 < T) {
-            k_panel<<<dim3((unsigned)P, (unsigned)(T - k - 1)), NT, DG_SMEM_BYTES, h->st>>>(
-                h->L, h->Linv, b, k, h->info);
+            GPK_LAUNCH(h, GP_PH_TRSM, k_panel, dim3((unsigned)P, (unsigned)(T - k - 1)), NT,
+                       DG_SMEM_BYTES, h->L, (const double*)h->Linv, b, k, (const unsigned long long*)h->info);
             const int64_t tt = T - k - 1;
-            k_update<<<dim3((unsigned)(tt * (tt + 1) / 2), (unsigned)(P * P)), NT, DG_SMEM_BYTES,
-                       h->st>>>(h->L, b, k, h->info);
+            GPK_LAUNCH(h, GP_PH_UPDATE, k_update, dim3((unsigned)(tt * (tt + 1) / 2), (unsigned)(P * P)),
+                       NT, DG_SMEM_BYTES, h->L, b, k, (const unsigned long long*)h->info);
         }
     }
 }
@@ -786,11 +745,13 @@ void solve_lower(gp_t h, const double* rhs, double* out)
 {
     const int64_t T = h->T, b = h->b;
     cudaMemcpyAsync(h->work, rhs, h->Np * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+    const unsigned g_apply = (unsigned)((b + 7) / 8 < 64 ? (b + 7) / 8 : 64);
     for (int64_t j = 0; j < T; ++j) {
-        k_tri_apply<<<(unsigned)((b + 7) / 8 < 64 ? (b + 7) / 8 : 64), NT, 0, h->st>>>(h->Linv, b, j,
-                                                                                      h->work, out, 0);
+        GPK_LAUNCH(h, GP_PH_SOLVE, k_tri_apply, g_apply, NT, 0, (const double*)h->Linv, b, j,
+                   (const double*)h->work, out, 0);
         if (j + 1 < T)
-            k_gemv_lower<<<grid_for((T - j - 1) * b, 8), NT, 0, h->st>>>(h->L, b, j, T, out, h->work);
+            GPK_LAUNCH(h, GP_PH_SOLVE, k_gemv_lower, grid_for((T - j - 1) * b, 8), NT, 0,
+                       (const double*)h->L, b, j, T, (const double*)out, h->work);
     }
 }
 
@@ -799,15 +760,18 @@ void solve_upper(gp_t h, const double* rhs, double* out)
     const int64_t T = h->T, b = h->b;
     cudaMemcpyAsync(h->work, rhs, h->Np * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
     for (int64_t j = T - 1; j >= 0; --j) {
-        k_tri_apply<<<(unsigned)((b + NT - 1) / NT), NT, 0, h->st>>>(h->Linv, b, j, h->work, out, 1);
+        GPK_LAUNCH(h, GP_PH_SOLVE, k_tri_apply, (unsigned)((b + NT - 1) / NT), NT, 0,
+                   (const double*)h->Linv, b, j, (const double*)h->work, out, 1);
         if (j > 0)
-            k_gemv_upper<<<(unsigned)((j * b + 63) / 64), NT, 0, h->st>>>(h->L, b, j, out, h->work);
+            GPK_LAUNCH(h, GP_PH_SOLVE, k_gemv_upper, (unsigned)((j * b + 63) / 64), NT, 0,
+                       (const double*)h->L, b, j, (const double*)out, h->work);
     }
 }
 
 void nlml_reduce(gp_t h)
 {
-    k_nlml<<<1, NT, 0, h->st>>>(h->beta, h->n, h->logdet_part, h->T, h->scal);
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_nlml, 1, NT, 0, (const double*)h->beta, h->n,
+               (const double*)h->logdet_part, h->T, h->scal);
 }
 
 void predict_solve(gp_t h, int64_t m, int64_t ldm)
@@ -817,51 +781,56 @@ void predict_solve(gp_t h, int64_t m, int64_t ldm)
     const int P = (int)(b / TB);
     const int64_t nq = h->Np / TB;
     for (int64_t j = 0; j < T; ++j) {
-        k_diagV<<<dim3((unsigned)P, (unsigned)(ldm / TB)), NT, DG_SMEM_BYTES, h->st>>>(
-            h->Linv, h->B, h->V, h->beta, h->part, b, j, ldm, nq);
+        GPK_LAUNCH(h, GP_PH_VSOLVE, k_diagV, dim3((unsigned)P, (unsigned)(ldm / TB)), NT, DG_SMEM_BYTES,
+                   (const double*)h->Linv, (const double*)h->B, h->V, (const double*)h->beta, h->part,
+                   b, j, ldm, nq);
         if (j + 1 < T)
-            k_updV<<<dim3((unsigned)((T - j - 1) * P), (unsigned)(ldm / TB)), NT, DG_SMEM_BYTES,
-                     h->st>>>(h->L, h->B, h->V, b, j, ldm);
+            GPK_LAUNCH(h, GP_PH_VSOLVE, k_updV, dim3((unsigned)((T - j - 1) * P), (unsigned)(ldm / TB)),
+                       NT, DG_SMEM_BYTES, (const double*)h->L, h->B, (const double*)h->V, b, j, ldm);
     }
 }
 
 void predict_finish(gp_t h, int64_t m, int64_t ldm, bool want_var)
 {
     const int64_t nq = h->Np / TB;
-    k_predict_finish<<<(unsigned)((m + 255) / 256), 256, 0, h->st>>>(
-        h->part, nq, ldm, m, h->hyp, h->opt.noisy_test_var, h->outm, want_var ? h->outv : nullptr);
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_predict_finish, (unsigned)((m + 255) / 256), 256, 0,
+               (const double*)h->part, nq, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
+               h->outm, want_var ? h->outv : (double*)nullptr);
 }
 
 void predict_mean_only(gp_t h, int64_t m, int64_t ldm)
 {
     const int64_t chunks = 64, rows_per = (h->Np + chunks - 1) / chunks;
-    k_mean_gemv<<<dim3((unsigned)((ldm + 255) / 256), (unsigned)chunks), 256, 0, h->st>>>(
-        h->B, h->alpha, rows_per, h->Np, ldm, h->part);
-    k_sum_rows<<<(unsigned)((m + 255) / 256), 256, 0, h->st>>>(h->part, chunks, ldm, m, h->outm);
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_mean_gemv, dim3((unsigned)((ldm + 255) / 256), (unsigned)chunks), 256,
+               0, (const double*)h->B, (const double*)h->alpha, rows_per, h->Np, ldm, h->part);
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_sum_rows, (unsigned)((m + 255) / 256), 256, 0,
+               (const double*)h->part, chunks, ldm, m, h->outm);
 }
 
 void full_cov(gp_t h, int64_t m, int64_t ldm, double* cov)
 {
     assemble_test_prior(h, m, cov);
     const int64_t nb = (m + TB - 1) / TB;
-    k_syrk_cov<<<(unsigned)(nb * (nb + 1) / 2), NT, DG_SMEM_BYTES, h->st>>>(h->V, h->Np, ldm, m, cov);
+    GPK_LAUNCH(h, GP_PH_COV, k_syrk_cov, (unsigned)(nb * (nb + 1) / 2), NT, DG_SMEM_BYTES,
+               (const double*)h->V, h->Np, ldm, m, cov);
 }
 
 void inverse_tiles(gp_t h)
 {
     const int64_t T = h->T, b = h->b;
     const int P = (int)(b / TB);
-    k_copy_diag<<<grid_for(T * b * b), NT, 0, h->st>>>(h->Linv, h->Xinv, b, T);
+    GPK_LAUNCH(h, GP_PH_TRTRI, k_copy_diag, grid_for(T * b * b), NT, 0, (const double*)h->Linv,
+               h->Xinv, b, T);
     for (int64_t t = 0; t < T; ++t) {
         if (t > 0)
-            k_trtri_scale<<<dim3((unsigned)P, (unsigned)t), NT, DG_SMEM_BYTES, h->st>>>(h->Linv, h->Xinv,
-                                                                                      b, t);
+            GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_scale, dim3((unsigned)P, (unsigned)t), NT, DG_SMEM_BYTES,
+                       (const double*)h->Linv, h->Xinv, b, t);
         if (t + 1 < T)
-            k_trtri_accum<<<dim3((unsigned)((T - t - 1) * (t + 1)), (unsigned)(P * P)), NT,
-                            DG_SMEM_BYTES, h->st>>>(h->L, h->Xinv, b, t);
+            GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_accum, dim3((unsigned)((T - t - 1) * (t + 1)), (unsigned)(P * P)),
+                       NT, DG_SMEM_BYTES, (const double*)h->L, h->Xinv, b, t);
     }
-    k_lauum<<<dim3((unsigned)(T * (T + 1) / 2), (unsigned)(P * P)), NT, DG_SMEM_BYTES, h->st>>>(
-        h->Xinv, h->Kinv, b, T);
+    GPK_LAUNCH(h, GP_PH_LAUUM, k_lauum, dim3((unsigned)(T * (T + 1) / 2), (unsigned)(P * P)), NT,
+               DG_SMEM_BYTES, (const double*)h->Xinv, h->Kinv, b, T);
 }
 
 void adjoint_grad(gp_t h)
@@ -869,20 +838,29 @@ void adjoint_grad(gp_t h)
     const int64_t T = h->T;
     const int P = (int)(h->b / TB);
     dim3 grid((unsigned)(T * (T + 1) / 2), (unsigned)(P * P));
-    k_adjoint<<<grid, NT, 0, h->st>>>(h->Kinv, h->alpha, h->X, h->n, h->d, h->b, h->hyp, h->gpart);
-    k_grad_finish<<<1, NT, 0, h->st>>>(h->gpart, (int64_t)grid.x * grid.y, h->hyp, h->scal);
+    if (h->opt.prec == GP_MIXED)
+        GPK_LAUNCH(h, GP_PH_ADJOINT, k_adjoint<float>, grid, NT, 0, (const float*)h->Kinv32,
+                   (const double*)h->alpha, (const double*)h->X, h->n, h->d, h->b, (const GpHyperDev*)h->hyp,
+                   h->gpart);
+    else
+        GPK_LAUNCH(h, GP_PH_ADJOINT, k_adjoint<double>, grid, NT, 0, (const double*)h->Kinv,
+                   (const double*)h->alpha, (const double*)h->X, h->n, h->d, h->b, (const GpHyperDev*)h->hyp,
+                   h->gpart);
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_grad_finish, 1, NT, 0, (const double*)h->gpart,
+               (int64_t)grid.x * grid.y, (const GpHyperDev*)h->hyp, h->scal);
 }
 
 void adam_step(gp_t h, double lr, double* hist_slot)
 {
-    k_adam<<<1, 32, 0, h->st>>>(h->hyp, h->adam, h->scal, lr, h->opt.adam_beta1, h->opt.adam_beta2,
-                               h->opt.adam_eps, h->trainable[0], h->trainable[1], h->trainable[2],
-                               hist_slot, h->info);
+    GPK_LAUNCH(h, GP_PH_ADAM, k_adam, 1, 32, 0, h->hyp, h->adam, (const double*)h->scal, lr,
+               h->opt.adam_beta1, h->opt.adam_beta2, h->opt.adam_eps, h->trainable[0], h->trainable[1],
+               h->trainable[2], hist_slot, (const unsigned long long*)h->info);
 }
 
 void copy_factor_dense(gp_t h, double* out)
 {
-    k_factor_dense<<<grid_for(h->n * h->n), NT, 0, h->st>>>(h->L, h->b, h->n, out);
+    GPK_LAUNCH(h, GP_PH_OTHER, k_factor_dense, grid_for(h->n * h->n), NT, 0, (const double*)h->L,
+               h->b, h->n, out);
 }
 
 }  // namespace gpk

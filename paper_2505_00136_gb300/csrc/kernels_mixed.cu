@@ -1,0 +1,737 @@
+// Mixed-precision hot path (GP_MIXED): FP32-accurate split-BF16 tile products
+// on the BF16 tensor pipe, FP64 where accuracy is decided.
+//
+//  - K is assembled once in FP64 (kept for residuals) and in FP32 (working copy).
+//  - Tiled right-looking Cholesky (Fig. 1) on the FP32 copy: each diagonal tile
+//    is factored and inverted in FP64 (same kernel as the FP64 path), the panel
+//    TRSM (L_ik = A_ik Linv_kk^T) and the trailing SYRK/GEMM run as bf16x6
+//    products with FP32 accumulation.  Every finished off-diagonal tile of L is
+//    also kept as three BF16 planes, the operand format of later products.
+//  - log|K| comes from the FP64 diagonal factors.
+//  - alpha = K^{-1} y by iterative refinement: FP32 triangular solves with the
+//    mixed factor, residual y - K alpha in FP64 against the FP64 K.
+//  - Prediction: the mean is K_{Z*,Z} alpha in FP64 (fused into the cross-
+//    covariance assembly); the variance uses W = K_{Z*,Z} L^{-T} from bf16x6
+//    products, var = k** - rowsum(W^2).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "bgemm_block.cuh"
+#include "gp_internal.cuh"
+#include "se_common.cuh"
+
+namespace gpk {
+
+constexpr int MB = 128;   // block edge of the split-BF16 products
+constexpr int NTH = 256;
+
+// ---------------------------------------------------------------- conversions
+__global__ void k_tile_up64(const float* src, double* dst, int64_t count)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (double)src[e];
+}
+
+// FP64 factor tile and its inverse back to FP32 (zero upper triangle) and to
+// the three-plane operand format of the inverse.
+__global__ void k_tile_down(const double* D, const double* X, float* A32, float* Linv32,
+                            __nv_bfloat16* LinvP, int64_t b)
+{
+    const int64_t bb = b * b;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < bb;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e / b, c = e % b;
+        A32[e] = (c <= r) ? (float)D[e] : 0.f;
+        float xv = (c <= r) ? (float)X[e] : 0.f;
+        Linv32[e] = xv;
+        __nv_bfloat16 hi, mid, lo;
+        split3(xv, hi, mid, lo);
+        LinvP[e] = hi;
+        LinvP[bb + e] = mid;
+        LinvP[2 * bb + e] = lo;
+    }
+}
+
+// Planes of the panel tiles A32_(i,k), i = k+1..T-1, into PA (one slot per tile).
+__global__ void k_split_panel(const float* A32, __nv_bfloat16* PA, int64_t b, int64_t k)
+{
+    const int64_t bb = b * b;
+    const int64_t i = k + 1 + blockIdx.y;
+    const float* src = A32 + tri_index(i, k) * bb;
+    __nv_bfloat16* dst = PA + (int64_t)blockIdx.y * 3 * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < bb;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        __nv_bfloat16 hi, mid, lo;
+        split3(src[e], hi, mid, lo);
+        dst[e] = hi;
+        dst[bb + e] = mid;
+        dst[2 * bb + e] = lo;
+    }
+}
+
+// ---------------------------------------------------------------- mixed Cholesky steps
+// Panel: L_ik = A_ik Linv_kk^T (128-blocks; Linv lower so k runs to (cb+1)*128).
+// Writes L_ik in FP32 and its planes into LP.
+__global__ __launch_bounds__(NTH) void k_mpanel(float* A32, __nv_bfloat16* LP, const __nv_bfloat16* PA,
+                                                const __nv_bfloat16* LinvP, int64_t b, int64_t k,
+                                                const unsigned long long* info)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (failed(info)) return;
+    const int Q = (int)(b / MB);
+    const int rb = blockIdx.x / Q, cb = blockIdx.x % Q;
+    const int64_t i = k + 1 + blockIdx.y, bb = b * b;
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{PA + (int64_t)blockIdx.y * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
+    BView vb{LinvP + k * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
+    bgemm_acc(acc, va, vb, 0, (int64_t)(cb + 1) * MB, (__nv_bfloat16*)smem_raw);
+    const int64_t off = (int64_t)rb * MB * b + cb * MB;
+    float* dst = A32 + tri_index(i, k) * bb + off;
+    __nv_bfloat16* lp = LP + tri_index(i, k) * 3 * bb + off;
+    bacc_for_each(acc, [&](int r, int c, float v) {
+        int64_t o = (int64_t)r * b + c;
+        dst[o] = v;
+        __nv_bfloat16 hi, mid, lo;
+        split3(v, hi, mid, lo);
+        lp[o] = hi;
+        lp[bb + o] = mid;
+        lp[2 * bb + o] = lo;
+    });
+}
+
+// Trailing update: A_ij -= L_ik L_jk^T for k < j <= i.
+__global__ __launch_bounds__(NTH) void k_mupdate(float* A32, const __nv_bfloat16* LP, int64_t b, int64_t k,
+                                                 const unsigned long long* info)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (failed(info)) return;
+    const int Q = (int)(b / MB);
+    int64_t ii, jj;
+    tri_decode(blockIdx.x, ii, jj);
+    const int64_t i = k + 1 + ii, j = k + 1 + jj, bb = b * b;
+    const int rb = blockIdx.y / Q, cb = blockIdx.y % Q;
+    if (i == j && cb > rb) return;
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{LP + tri_index(i, k) * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
+    BView vb{LP + tri_index(j, k) * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
+    bgemm_acc(acc, va, vb, 0, b, (__nv_bfloat16*)smem_raw);
+    float* dst = A32 + tri_index(i, j) * bb + (int64_t)rb * MB * b + cb * MB;
+    bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * b + c] -= v; });
+}
+
+// ---------------------------------------------------------------- FP32 single-RHS solves
+__global__ __launch_bounds__(NTH) void k_tri_apply32(const float* Linv, int64_t b, int64_t j, const float* w,
+                                                     float* out, int upper)
+{
+    const float* Xj = Linv + j * b * b;
+    const float* wj = w + j * b;
+    float* oj = out + j * b;
+    if (!upper) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < b; r += (int64_t)gridDim.x * 8) {
+            float s = 0.f;
+            for (int64_t t = lane; t <= r; t += 32) s = fmaf(Xj[r * b + t], wj[t], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) oj[r] = s;
+        }
+    } else {
+        for (int64_t c = (int64_t)blockIdx.x * NTH + threadIdx.x; c < b; c += (int64_t)gridDim.x * NTH) {
+            float s = 0.f;
+            for (int64_t t = c; t < b; ++t) s = fmaf(Xj[t * b + c], wj[t], s);
+            oj[c] = s;
+        }
+    }
+}
+
+__global__ __launch_bounds__(NTH) void k_gemv_lower32(const float* Lt, int64_t b, int64_t j, int64_t T,
+                                                      const float* x, float* w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t rows = (T - j - 1) * b;
+    const float* xj = x + j * b;
+    for (int64_t R = (int64_t)blockIdx.x * 8 + warp; R < rows; R += (int64_t)gridDim.x * 8) {
+        int64_t i = j + 1 + R / b, r = R % b;
+        const float* row = Lt + tri_index(i, j) * b * b + r * b;
+        float s = 0.f;
+        for (int64_t t = lane; t < b; t += 32) s = fmaf(row[t], xj[t], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) w[i * b + r] -= s;
+    }
+}
+
+__global__ __launch_bounds__(NTH) void k_gemv_upper32(const float* Lt, int64_t b, int64_t j, const float* x,
+                                                      float* w)
+{
+    __shared__ float red[4][64];
+    const int c = threadIdx.x & 63, q = threadIdx.x >> 6;
+    const int64_t cols = j * b;
+    const int64_t C = (int64_t)blockIdx.x * 64 + c;
+    const float* xj = x + j * b;
+    float s = 0.f;
+    if (C < cols) {
+        int64_t i = C / b, cc = C % b;
+        const float* tile = Lt + tri_index(j, i) * b * b;
+        for (int64_t r = q; r < b; r += 4) s = fmaf(tile[r * b + cc], xj[r], s);
+    }
+    red[q][c] = s;
+    __syncthreads();
+    if (q == 0 && C < cols) w[C] -= red[0][c] + red[1][c] + red[2][c] + red[3][c];
+}
+
+// ---------------------------------------------------------------- FP64 residual r = y - K x
+// One CTA per 64 rows: row part from the lower tiles (j <= i), transposed
+// part from the tiles below (j > i).  Every product in FP64; deterministic.
+__global__ __launch_bounds__(NTH) void k_sym_resid(const double* K64, const double* x, const double* y,
+                                                   double* r, int64_t b, int64_t T)
+{
+    __shared__ double acc_s[64];
+    __shared__ double red[4][64];
+    const int64_t R0 = (int64_t)blockIdx.x * 64;
+    const int64_t i = R0 / b, ro = R0 % b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 64) acc_s[threadIdx.x] = 0.0;
+    __syncthreads();
+    // row part: sum_{j < i} K_ij[ro + rr][:] . x_j, plus the diagonal tile's
+    // lower triangle (t <= ro + rr); the upper triangle of a diagonal tile is
+    // never read (it is taken from the transposed lower triangle below)
+    for (int rr = warp; rr < 64; rr += 8) {
+        double s = 0.0;
+        for (int64_t j = 0; j <= i; ++j) {
+            const double* row = K64 + tri_index(i, j) * b * b + (ro + rr) * b;
+            const double* xj = x + j * b;
+            const int64_t tend = (j == i) ? ro + rr + 1 : b;
+            for (int64_t t = lane; t < tend; t += 32) s = fma(row[t], xj[t], s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) acc_s[rr] = s;
+    }
+    // transposed part: sum_{j > i} K_ji[:, ro + c] . x_j and, in the diagonal
+    // tile, rows t > ro + c of column ro + c
+    const int c = threadIdx.x & 63, q = threadIdx.x >> 6;
+    double s = 0.0;
+    for (int64_t j = i; j < T; ++j) {
+        const double* tile = K64 + tri_index(j, i) * b * b + ro + c;
+        const double* xj = x + j * b;
+        const int64_t t0 = (j == i) ? ro + c + 1 : 0;
+        for (int64_t t = t0 + ((q - t0) % 4 + 4) % 4; t < b; t += 4) s = fma(tile[t * b], xj[t], s);
+    }
+    red[q][c] = s;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        int64_t row = R0 + threadIdx.x;
+        double kx = acc_s[threadIdx.x] + red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] +
+                    red[3][threadIdx.x];
+        r[row] = y[row] - kx;
+    }
+}
+
+// out[0] = ||a||^2, out[1] = ||b||^2 (single CTA, deterministic)
+__global__ void k_norms2(const double* a, const double* b, int64_t n, double* out)
+{
+    __shared__ double ra[NTH], rb[NTH];
+    double sa = 0.0, sb = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += NTH) {
+        sa = fma(a[e], a[e], sa);
+        sb = fma(b[e], b[e], sb);
+    }
+    ra[threadIdx.x] = sa;
+    rb[threadIdx.x] = sb;
+    __syncthreads();
+    for (int o = NTH / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ra[threadIdx.x] += ra[threadIdx.x + o];
+            rb[threadIdx.x] += rb[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = ra[0];
+        out[1] = rb[0];
+    }
+}
+
+__global__ void k_d2f(const double* a, float* b, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
+}
+
+__global__ void k_axpy_f(double* x, const float* d, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        x[e] += (double)d[e];
+}
+
+// NLML from the refined alpha: 1/2 y^T alpha + sum log L_ii + n/2 log(2 pi).
+__global__ void k_nlml_mixed(const double* y, const double* alpha, int64_t n, const double* logdet_part,
+                             int64_t T, double* scal)
+{
+    __shared__ double red[NTH];
+    double s = 0.0, ld = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += NTH) s = fma(y[e], alpha[e], s);
+    for (int64_t e = threadIdx.x; e < T; e += NTH) ld += logdet_part[e];
+    red[threadIdx.x] = 0.5 * s + ld;
+    __syncthreads();
+    for (int o = NTH / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scal[0] = red[0] + 0.5 * (double)n * log(2.0 * M_PI);
+}
+
+// ---------------------------------------------------------------- mixed prediction
+// R32 (ldr = Np) = fp32(K_{Z*,Z}) for a 64 x 64 block, and the FP64 partial
+// sums of K_{Z*,Z} alpha over the block's 64 training points (Eq. 3).
+__global__ __launch_bounds__(NTH) void k_cross_mixed(const double* Xs, int64_t m, const double* X, int64_t n,
+                                                     int64_t d, const double* alpha, const GpHyperDev* hyp,
+                                                     float* R32, int64_t ldr, double* mpart, int64_t ldp)
+{
+    __shared__ double sm[2 * 64 * 17];
+    const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    double r2[4][4];
+    dist_block(r2, Xs, m0, m, X, n0, n, d, sm);
+    const double nu = hyp->nu, c2 = hyp->inv2l2;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t gm = m0 + ty + 16 * a;
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t gn = n0 + tx + 16 * c;
+            double kv = (gm < m && gn < n) ? nu * exp(-r2[a][c] * c2) : 0.0;
+            R32[gm * ldr + gn] = (float)kv;
+            if (gn < n) s = fma(kv, alpha[gn], s);
+        }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (tx == 0) mpart[(int64_t)blockIdx.x * ldp + gm] = s;
+    }
+}
+
+// Planes of the column block R32[:, j*b .. (j+1)*b) into RP ([3][ldm][b]).
+__global__ void k_split_cols(const float* R32, int64_t ldr, int64_t j, int64_t b, int64_t rows,
+                             __nv_bfloat16* RP)
+{
+    const int64_t total = rows * b, ps = rows * b;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e / b, c = e % b;
+        __nv_bfloat16 hi, mid, lo;
+        split3(R32[r * ldr + j * b + c], hi, mid, lo);
+        RP[e] = hi;
+        RP[ps + e] = mid;
+        RP[2 * ps + e] = lo;
+    }
+}
+
+// W_j = R_j Linv_jj^T (128 x 128 blocks); planes of W_j into WP and FP64 row
+// sums of W_j^2 into vpart[(j*Q + cb)][row].
+__global__ __launch_bounds__(NTH) void k_mdiagW(const __nv_bfloat16* RP, const __nv_bfloat16* LinvP,
+                                                __nv_bfloat16* WP, int64_t ldw, double* vpart, int64_t ldm,
+                                                int64_t b, int64_t j)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double rs[4][MB];
+    const int Q = (int)(b / MB);
+    const int cb = blockIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.y * MB, bb = b * b, ps = ldm * b;
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{RP + m0 * b, b, ps, MB};
+    BView vb{LinvP + j * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
+    bgemm_acc(acc, va, vb, 0, (int64_t)(cb + 1) * MB, (__nv_bfloat16*)smem_raw);
+    __nv_bfloat16* wp = WP + m0 * ldw + j * b + cb * MB;
+    const int64_t psw = ldm * ldw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wn = warp & 3, wm = warp >> 2;
+    double rowsq[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    bacc_for_each(acc, [&](int r, int c, float v) {
+        int64_t o = (int64_t)r * ldw + c;
+        __nv_bfloat16 hi, mid, lo;
+        split3(v, hi, mid, lo);
+        wp[o] = hi;
+        wp[psw + o] = mid;
+        wp[2 * psw + o] = lo;
+    });
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const float* f = acc.c[mt][nt];
+            rowsq[mt][0] += (double)f[0] * f[0] + (double)f[1] * f[1];
+            rowsq[mt][1] += (double)f[2] * f[2] + (double)f[3] * f[3];
+        }
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            double v = rowsq[mt][h];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            rowsq[mt][h] = v;
+        }
+    if ((lane & 3) == 0) {
+        const int g = lane >> 2;
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+            rs[wn][wm * 64 + mt * 16 + g] = rowsq[mt][0];
+            rs[wn][wm * 64 + mt * 16 + g + 8] = rowsq[mt][1];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < MB) {
+        int r = threadIdx.x;
+        vpart[(j * Q + cb) * ldm + m0 + r] = rs[0][r] + rs[1][r] + rs[2][r] + rs[3][r];
+    }
+}
+
+// R_i -= W_j L_ij^T for all tiles i > j.
+__global__ __launch_bounds__(NTH) void k_mupdW(float* R32, int64_t ldr, const __nv_bfloat16* WP,
+                                               const __nv_bfloat16* LP, int64_t ldm, int64_t b, int64_t j)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Q = (int)(b / MB);
+    const int64_t i = j + 1 + blockIdx.x / Q;
+    const int cb = blockIdx.x % Q;
+    const int64_t m0 = (int64_t)blockIdx.y * MB, bb = b * b;
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{WP + m0 * ldr + j * b, ldr, ldm * ldr, MB};
+    BView vb{LP + tri_index(i, j) * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
+    bgemm_acc(acc, va, vb, 0, b, (__nv_bfloat16*)smem_raw);
+    float* dst = R32 + m0 * ldr + i * b + cb * MB;
+    bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * ldr + c] -= v; });
+}
+
+// mean = sum of the mean partials, var = k** - sum of the variance partials.
+__global__ void k_mixed_finish(const double* mpart, int64_t nmp, const double* vpart, int64_t nvp, int64_t ldm,
+                               int64_t m, const GpHyperDev* hyp, int noisy, double* mean, double* var)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    double sm = 0.0, sv = 0.0;
+    for (int64_t q = 0; q < nmp; ++q) sm += mpart[q * ldm + c];
+    for (int64_t q = 0; q < nvp; ++q) sv += vpart[q * ldm + c];
+    if (mean) mean[c] = sm;
+    if (var) var[c] = hyp->nu + (noisy ? hyp->s2 : 0.0) - sv;
+}
+
+// ---------------------------------------------------------------- mixed full covariance
+// cov (m x m, FP64, prefilled with K_{Z*,Z*}) -= W W^T on lower 128-blocks, mirrored.
+__global__ __launch_bounds__(NTH) void k_msyrk_cov(const __nv_bfloat16* WP, int64_t ldw, int64_t ps,
+                                                   int64_t kdim, int64_t m, double* cov)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int64_t a, c;
+    tri_decode(blockIdx.x, a, c);
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{WP + a * MB * ldw, ldw, ps, MB};
+    BView vb{WP + c * MB * ldw, ldw, ps, MB};
+    bgemm_acc(acc, va, vb, 0, kdim, (__nv_bfloat16*)smem_raw);
+    bacc_for_each(acc, [&](int r, int cc, float v) {
+        int64_t R = a * MB + r, C = c * MB + cc;
+        if (R >= m || C >= m || (a == c && cc > r)) return;
+        double x = cov[R * m + C] - (double)v;
+        cov[R * m + C] = x;
+        cov[C * m + R] = x;
+    });
+}
+
+// ---------------------------------------------------------------- mixed inverse for the gradient
+// With X = L^{-1} (lower tiles X_ij), the tiles Z_ij = X_ij^T satisfy
+//   Z_jj = Linv_jj^T,
+//   U_ij = sum_{t=j}^{i-1} Z_tj L_it^T,   Z_ij = -U_ij Linv_ii^T   (i > j),
+// and K^{-1}_ij = sum_{t >= i} Z_ti Z_tj^T, all products in NT form.
+
+// ZP_tt = planes of Linv_tt^T, for every t.
+__global__ void k_zdiag(const float* Linv32, __nv_bfloat16* ZP, int64_t b)
+{
+    const int64_t bb = b * b, t = blockIdx.y;
+    const float* src = Linv32 + t * bb;
+    __nv_bfloat16* dst = ZP + tri_index(t, t) * 3 * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < bb;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = e / b, c = e % b;
+        __nv_bfloat16 hi, mid, lo;
+        split3(src[c * b + a], hi, mid, lo);
+        dst[e] = hi;
+        dst[bb + e] = mid;
+        dst[2 * bb + e] = lo;
+    }
+}
+
+// Planes of U32 tiles (t, j), j < t, into PA slots j.
+__global__ void k_split_row(const float* U32, __nv_bfloat16* PA, int64_t b, int64_t t)
+{
+    const int64_t bb = b * b, j = blockIdx.y;
+    const float* src = U32 + tri_index(t, j) * bb;
+    __nv_bfloat16* dst = PA + j * 3 * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < bb;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        __nv_bfloat16 hi, mid, lo;
+        split3(src[e], hi, mid, lo);
+        dst[e] = hi;
+        dst[bb + e] = mid;
+        dst[2 * bb + e] = lo;
+    }
+}
+
+// Z_tj = -U_tj Linv_tt^T for j < t (grid.y = j), planes into ZP.
+__global__ __launch_bounds__(NTH) void k_mtrtri_fin(const __nv_bfloat16* PA, const __nv_bfloat16* LinvP,
+                                                    __nv_bfloat16* ZP, int64_t b, int64_t t)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Q = (int)(b / MB);
+    const int rb = blockIdx.x / Q, cb = blockIdx.x % Q;
+    const int64_t j = blockIdx.y, bb = b * b;
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{PA + j * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
+    BView vb{LinvP + t * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
+    bgemm_acc(acc, va, vb, 0, (int64_t)(cb + 1) * MB, (__nv_bfloat16*)smem_raw);
+    __nv_bfloat16* zp = ZP + tri_index(t, j) * 3 * bb + (int64_t)rb * MB * b + cb * MB;
+    bacc_for_each(acc, [&](int r, int c, float v) {
+        int64_t o = (int64_t)r * b + c;
+        __nv_bfloat16 hi, mid, lo;
+        split3(-v, hi, mid, lo);
+        zp[o] = hi;
+        zp[bb + o] = mid;
+        zp[2 * bb + o] = lo;
+    });
+}
+
+// U_ij (+)= Z_tj L_it^T for i > t >= j; the first contribution (t == j) overwrites.
+__global__ __launch_bounds__(NTH) void k_mtrtri_acc(const __nv_bfloat16* ZP, const __nv_bfloat16* LP, float* U32,
+                                                    int64_t b, int64_t t)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Q = (int)(b / MB);
+    const int64_t i = t + 1 + blockIdx.x / (t + 1), j = blockIdx.x % (t + 1), bb = b * b;
+    const int rb = blockIdx.y / Q, cb = blockIdx.y % Q;
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{ZP + tri_index(t, j) * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
+    BView vb{LP + tri_index(i, t) * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
+    bgemm_acc(acc, va, vb, 0, b, (__nv_bfloat16*)smem_raw);
+    float* dst = U32 + tri_index(i, j) * bb + (int64_t)rb * MB * b + cb * MB;
+    const bool first = (t == j);
+    bacc_for_each(acc, [&](int r, int c, float v) {
+        float* p = dst + (int64_t)r * b + c;
+        *p = first ? v : *p + v;
+    });
+}
+
+// K^{-1}_ij = sum_{t >= i} Z_ti Z_tj^T on lower tiles (FP32 out).
+__global__ __launch_bounds__(NTH) void k_mlauum(const __nv_bfloat16* ZP, float* Kinv32, int64_t b, int64_t T)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Q = (int)(b / MB);
+    int64_t i, j;
+    tri_decode(blockIdx.x, i, j);
+    const int rb = blockIdx.y / Q, cb = blockIdx.y % Q;
+    if (i == j && cb > rb) return;
+    const int64_t bb = b * b;
+    BAcc acc;
+    bacc_zero(acc);
+    for (int64_t t = i; t < T; ++t) {
+        BView va{ZP + tri_index(t, i) * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
+        BView vb{ZP + tri_index(t, j) * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
+        bgemm_acc(acc, va, vb, (t == i) ? (int64_t)rb * MB : 0, b, (__nv_bfloat16*)smem_raw);
+    }
+    float* dst = Kinv32 + tri_index(i, j) * bb + (int64_t)rb * MB * b + cb * MB;
+    bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * b + c] = v; });
+}
+
+__global__ void k_factor_dense32(const float* Lt, int64_t b, int64_t n, double* out)
+{
+    int64_t total = n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e / n, c = e % n;
+        out[e] = (c <= r) ? (double)Lt[tri_index(r / b, c / b) * b * b + (r % b) * b + (c % b)] : 0.0;
+    }
+}
+
+// ================================================================ host launchers
+static int grid_for(int64_t work, int per = NTH)
+{
+    int64_t g = (work + per - 1) / per;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+static void ensure_attrs_mixed()
+{
+    static int done_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done_dev == dev) return;
+    cudaFuncSetAttribute(k_mpanel, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mdiagW, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mupdW, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    cudaFuncSetAttribute(k_msyrk_cov, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mtrtri_fin, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mtrtri_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mlauum, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    done_dev = dev;
+}
+
+void factor_mixed(gp_t h)
+{
+    ensure_attrs_mixed();
+    const int64_t T = h->T, b = h->b, bb = b * b;
+    const int Q = (int)(b / MB);
+    for (int64_t k = 0; k < T; ++k) {
+        float* Akk = h->A32 + tri_index(k, k) * bb;
+        GPK_LAUNCH(h, GP_PH_POTRF, k_tile_up64, grid_for(bb), NTH, 0, (const float*)Akk, h->D64, bb);
+        potrf_diag_launch(h, h->D64, h->X64, b, k * b, h->logdet_part + k);
+        GPK_LAUNCH(h, GP_PH_POTRF, k_tile_down, grid_for(bb), NTH, 0, (const double*)h->D64,
+                   (const double*)h->X64, Akk, h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b);
+        if (k + 1 < T) {
+            const unsigned tt = (unsigned)(T - k - 1);
+            GPK_LAUNCH(h, GP_PH_TRSM, k_split_panel, dim3((unsigned)grid_for(bb) / 4 + 1, tt), NTH, 0,
+                       (const float*)h->A32, h->PA, b, k);
+            GPK_LAUNCH(h, GP_PH_TRSM, k_mpanel, dim3((unsigned)(Q * Q), tt), NTH, BG_SMEM_BYTES, h->A32, h->LP,
+                       (const __nv_bfloat16*)h->PA, (const __nv_bfloat16*)h->LinvP, b, k,
+                       (const unsigned long long*)h->info);
+            GPK_LAUNCH(h, GP_PH_UPDATE, k_mupdate, dim3(tt * (tt + 1) / 2, (unsigned)(Q * Q)), NTH,
+                       BG_SMEM_BYTES, h->A32, (const __nv_bfloat16*)h->LP, b, k,
+                       (const unsigned long long*)h->info);
+        }
+    }
+}
+
+// out32 = L~^{-1} in32 (lower) or L~^{-T} in32 (upper), FP32 throughout.
+static void solve32(gp_t h, const float* in32, float* out32, bool upper)
+{
+    const int64_t T = h->T, b = h->b;
+    cudaMemcpyAsync(h->w32, in32, h->Np * sizeof(float), cudaMemcpyDeviceToDevice, h->st);
+    if (!upper) {
+        const unsigned g_apply = (unsigned)((b + 7) / 8 < 64 ? (b + 7) / 8 : 64);
+        for (int64_t j = 0; j < T; ++j) {
+            GPK_LAUNCH(h, GP_PH_SOLVE, k_tri_apply32, g_apply, NTH, 0, (const float*)h->Linv32, b, j,
+                       (const float*)h->w32, out32, 0);
+            if (j + 1 < T)
+                GPK_LAUNCH(h, GP_PH_SOLVE, k_gemv_lower32, grid_for((T - j - 1) * b, 8), NTH, 0,
+                           (const float*)h->A32, b, j, T, (const float*)out32, h->w32);
+        }
+    } else {
+        for (int64_t j = T - 1; j >= 0; --j) {
+            GPK_LAUNCH(h, GP_PH_SOLVE, k_tri_apply32, (unsigned)((b + NTH - 1) / NTH), NTH, 0,
+                       (const float*)h->Linv32, b, j, (const float*)h->w32, out32, 1);
+            if (j > 0)
+                GPK_LAUNCH(h, GP_PH_SOLVE, k_gemv_upper32, (unsigned)((j * b + 63) / 64), NTH, 0,
+                           (const float*)h->A32, b, j, (const float*)out32, h->w32);
+        }
+    }
+}
+
+// One correction sweep: d = L~^{-T} L~^{-1} r32 (FP32), x += d.
+static void correct(gp_t h, double* x)
+{
+    solve32(h, h->r32, h->t32, false);
+    solve32(h, h->t32, h->r32, true);
+    GPK_LAUNCH(h, GP_PH_REFINE, k_axpy_f, grid_for(h->Np), NTH, 0, x, (const float*)h->r32, h->Np);
+}
+
+void residual64(gp_t h, const double* x, const double* y, double* r)
+{
+    GPK_LAUNCH(h, GP_PH_REFINE, k_sym_resid, (unsigned)(h->Np / 64), NTH, 0, (const double*)h->L, x, y, r,
+               h->b, h->T);
+}
+
+void refine_start(gp_t h, const double* rhs, double* x)
+{
+    // x0 = L~^{-T} L~^{-1} rhs
+    cudaMemsetAsync(x, 0, h->Np * sizeof(double), h->st);
+    GPK_LAUNCH(h, GP_PH_REFINE, k_d2f, grid_for(h->Np), NTH, 0, rhs, h->r32, h->Np);
+    correct(h, x);
+}
+
+void refine_step(gp_t h, const double* rhs, double* x, double* r, double* norms)
+{
+    residual64(h, x, rhs, r);
+    GPK_LAUNCH(h, GP_PH_REFINE, k_norms2, 1, NTH, 0, (const double*)r, rhs, h->Np, norms);
+    GPK_LAUNCH(h, GP_PH_REFINE, k_d2f, grid_for(h->Np), NTH, 0, (const double*)r, h->r32, h->Np);
+    correct(h, x);
+}
+
+void nlml_mixed(gp_t h)
+{
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_nlml_mixed, 1, NTH, 0, (const double*)h->y, (const double*)h->alpha, h->n,
+               (const double*)h->logdet_part, h->T, h->scal);
+}
+
+void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
+{
+    ensure_attrs_mixed();
+    const int64_t T = h->T, b = h->b, Np = h->Np;
+    const int Q = (int)(b / MB);
+    const int64_t nmp = Np / 64, nvp = Np / MB;
+    GPK_LAUNCH(h, GP_PH_CROSS, k_cross_mixed, dim3((unsigned)(Np / 64), (unsigned)(ldm / 64)), NTH, 0,
+               (const double*)h->Xs, m, (const double*)h->X, h->n, h->d, (const double*)h->alpha,
+               (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm);
+    if (want_var) {
+        for (int64_t j = 0; j < T; ++j) {
+            GPK_LAUNCH(h, GP_PH_VSOLVE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np, j, b,
+                       ldm, h->RP);
+            GPK_LAUNCH(h, GP_PH_VSOLVE, k_mdiagW, dim3((unsigned)Q, (unsigned)(ldm / MB)), NTH, BG_SMEM_BYTES,
+                       (const __nv_bfloat16*)h->RP, (const __nv_bfloat16*)h->LinvP, h->WP, Np, h->vpart, ldm, b, j);
+            if (j + 1 < T)
+                GPK_LAUNCH(h, GP_PH_VSOLVE, k_mupdW, dim3((unsigned)((T - j - 1) * Q), (unsigned)(ldm / MB)), NTH,
+                           BG_SMEM_BYTES, h->R32, Np, (const __nv_bfloat16*)h->WP, (const __nv_bfloat16*)h->LP,
+                           ldm, b, j);
+        }
+    }
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_mixed_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->mpart,
+               nmp, (const double*)h->vpart, want_var ? nvp : (int64_t)0, ldm, m, (const GpHyperDev*)h->hyp,
+               h->opt.noisy_test_var, h->outm, want_var ? h->outv : (double*)nullptr);
+}
+
+void full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)
+{
+    ensure_attrs_mixed();
+    assemble_test_prior(h, m, cov);
+    const int64_t nb = (m + MB - 1) / MB;
+    GPK_LAUNCH(h, GP_PH_COV, k_msyrk_cov, (unsigned)(nb * (nb + 1) / 2), NTH, BG_SMEM_BYTES,
+               (const __nv_bfloat16*)h->WP, h->Np, ldm * h->Np, h->Np, m, cov);
+}
+
+void inverse_mixed(gp_t h)
+{
+    ensure_attrs_mixed();
+    const int64_t T = h->T, b = h->b, bb = b * b;
+    const int Q = (int)(b / MB);
+    GPK_LAUNCH(h, GP_PH_TRTRI, k_zdiag, dim3((unsigned)grid_for(bb) / 4 + 1, (unsigned)T), NTH, 0,
+               (const float*)h->Linv32, h->ZP, b);
+    for (int64_t t = 0; t < T; ++t) {
+        if (t > 0) {
+            GPK_LAUNCH(h, GP_PH_TRTRI, k_split_row, dim3((unsigned)grid_for(bb) / 4 + 1, (unsigned)t), NTH, 0,
+                       (const float*)h->U32, h->PA, b, t);
+            GPK_LAUNCH(h, GP_PH_TRTRI, k_mtrtri_fin, dim3((unsigned)(Q * Q), (unsigned)t), NTH, BG_SMEM_BYTES,
+                       (const __nv_bfloat16*)h->PA, (const __nv_bfloat16*)h->LinvP, h->ZP, b, t);
+        }
+        if (t + 1 < T)
+            GPK_LAUNCH(h, GP_PH_TRTRI, k_mtrtri_acc, dim3((unsigned)((T - t - 1) * (t + 1)), (unsigned)(Q * Q)),
+                       NTH, BG_SMEM_BYTES, (const __nv_bfloat16*)h->ZP, (const __nv_bfloat16*)h->LP, h->U32, b, t);
+    }
+    GPK_LAUNCH(h, GP_PH_LAUUM, k_mlauum, dim3((unsigned)(T * (T + 1) / 2), (unsigned)(Q * Q)), NTH, BG_SMEM_BYTES,
+               (const __nv_bfloat16*)h->ZP, h->Kinv32, b, T);
+}
+
+void copy_factor_dense_mixed(gp_t h, double* out)
+{
+    GPK_LAUNCH(h, GP_PH_OTHER, k_factor_dense32, grid_for(h->n * h->n), NTH, 0, (const float*)h->A32, h->b,
+               h->n, out);
+}
+
+}  // namespace gpk

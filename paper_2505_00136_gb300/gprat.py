@@ -26,6 +26,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 GP_OK, GP_ERR_ARG, GP_ERR_NOT_PD, GP_ERR_CUDA, GP_ERR_OOM, GP_ERR_TIMEOUT, GP_ERR_STATE = range(7)
 GP_FP64, GP_MIXED = 0, 1
 GP_SCHED_STREAM, GP_SCHED_PERSISTENT = 0, 1
+PHASES = ["assemble", "potrf", "trsm", "update", "solve", "cross", "vsolve", "reduce", "cov",
+          "trtri", "lauum", "adjoint", "adam", "refine", "other"]
 
 
 class gp_hyper(ctypes.Structure):
@@ -61,6 +63,7 @@ _SIGS = {
     "gp_create": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.POINTER(gp_hyper),
                                  ctypes.POINTER(gp_options), ctypes.POINTER(_H)]),
     "gp_factor": (ctypes.c_int, [_H]),
+    "gp_predict": (ctypes.c_int, [_H, _vp, _i64, _vp, _vp, _vp]),
     "gp_predict_mean": (ctypes.c_int, [_H, _vp, _i64, _vp]),
     "gp_predict_var": (ctypes.c_int, [_H, _vp, _i64, _vp, _vp]),
     "gp_predict_full_cov": (ctypes.c_int, [_H, _vp, _i64, _vp, _vp]),
@@ -74,6 +77,9 @@ _SIGS = {
     "gp_get_factor": (ctypes.c_int, [_H, _vp]),
     "gp_get_alpha": (ctypes.c_int, [_H, _vp]),
     "gp_info": (ctypes.c_int, [_H, ctypes.POINTER(gp_info_t)]),
+    "gp_profile": (ctypes.c_int, [_H, ctypes.c_int]),
+    "gp_profile_read": (ctypes.c_int, [_H, _vp, _vp, ctypes.c_int]),
+    "gp_launch_count": (_i64, [_H]),
     "gp_last_error_info": (_i64, [_H]),
     "gp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "gp_destroy": (None, [_H]),
@@ -205,6 +211,30 @@ class GP:
         mean, var = self._out(m), self._out(m)
         _check(_lib.gp_predict_var(self.h, _ptr(Xs), m, _ptr(mean), _ptr(var)), self.h, "gp_predict_var")
         return mean, var
+
+    def predict(self, Xs, mean=True, var=True, cov=False):
+        """One solve for any of mean, variance and full covariance (``gp_predict``)."""
+        Xs = self._in(Xs)
+        m = Xs.shape[0]
+        mu = self._out(m) if mean else None
+        va = self._out(m) if var else None
+        cv = self._out(m, m) if cov else None
+        _check(_lib.gp_predict(self.h, _ptr(Xs), m, _ptr(mu), _ptr(va), _ptr(cv)), self.h, "gp_predict")
+        return mu, va, cv
+
+    def profile(self, enable=True):
+        _check(_lib.gp_profile(self.h, int(bool(enable))), self.h, "gp_profile")
+
+    def profile_read(self):
+        """Per-phase (ms, launches) accumulated since the last read."""
+        ms = np.zeros(len(PHASES))
+        cnt = np.zeros(len(PHASES), dtype=np.int64)
+        _check(_lib.gp_profile_read(self.h, ms.ctypes.data, cnt.ctypes.data, len(PHASES)), self.h,
+               "gp_profile_read")
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+    def launch_count(self):
+        return int(_lib.gp_launch_count(self.h))
 
     def predict_full_cov(self, Xs):
         Xs = self._in(Xs)

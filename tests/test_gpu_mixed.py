@@ -1,0 +1,108 @@
+"""Mixed-precision path (split-BF16 products, FP64 diagonal POTRF, FP64-residual
+refinement) against the FP64 oracle and against the FP64 GPU path.
+
+alpha and the predictive mean are refined to FP64 accuracy (mean = K_{Z*,Z}
+alpha): 1e-8 relative.  The factor itself is FP32-accurate.  Reported errors
+are printed for the record (pytest -s).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from paper_2505_00136_gb300 import datagen as dg
+from _util import rel
+
+pytestmark = pytest.mark.gpu
+
+MEAN_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_00136_gb300 import build
+    build.build()
+    from paper_2505_00136_gb300 import gprat
+    return gprat
+
+
+@pytest.mark.parametrize("n,m,d,n_tiles", [(1024, 1024, 8, 4), (1000, 77, 3, 4), (130, 5, 2, 1),
+                                           (2048, 200, 8, 16)])
+def test_mixed_against_oracle(g, orc, n, m, d, n_tiles):
+    X, y, Xs, _ = dg.msd_dataset(n, m, d, seed=1001 + n)
+    hyp = (1.0, 1.0, 0.1)
+    mu_o, va_o, _ = orc.predict(X, y, Xs, hyp)
+    f_o = orc.nlml(X, y, hyp)
+    K = orc.cov_train(X, hyp)
+    alpha_o = sla.cho_solve(sla.cho_factor(K, lower=True), y)
+    with g.GP(X, y, hyp, n_tiles=n_tiles, precision="mixed") as gp:
+        mu, va = gp.predict_var(Xs)
+        alpha = gp.get_alpha()
+        f = gp.nlml()
+        info = gp.info()
+        L = gp.get_factor()
+    errs = {"alpha": rel(alpha, alpha_o), "mean": rel(mu, mu_o), "var": rel(va, va_o),
+            "nlml": abs(f - f_o) / abs(f_o), "factor": rel(L, orc.cholesky(K)),
+            "refine_iters": info["refine_iters"], "refine_residual": info["refine_residual"]}
+    print("mixed vs oracle", n, m, d, errs)
+    assert info["tile"] % 128 == 0
+    assert errs["alpha"] < 1e-10
+    assert errs["mean"] < MEAN_TOL
+    assert errs["factor"] < 1e-5
+    assert errs["var"] < 1e-4
+    assert errs["nlml"] < 1e-6
+
+
+def test_mixed_not_pd(g):
+    X = np.zeros((300, 3))
+    with pytest.raises(g.GPError) as e:
+        with g.GP(X, np.ones(300), (1.0, 1.0, 0.0), n_tiles=2, precision="mixed") as gp:
+            gp.factor()
+    assert e.value.status == g.GP_ERR_NOT_PD and e.value.info == 1
+
+
+def test_mixed_vs_fp64_full_size(g):
+    """N = 32768, M = 8192, D = 8: the mixed path against the FP64 GPU path."""
+    import time
+    X, y, Xs, _ = dg.msd_dataset(32768, 8192, 8, seed=1002)
+    hyp = (1.0, 1.0, 0.1)
+    with g.GP(X, y, hyp, n_tiles=256, precision="mixed") as gp:
+        t0 = time.perf_counter()
+        mu_m, va_m = gp.predict_var(Xs)
+        t_mixed = time.perf_counter() - t0
+        f_m = gp.nlml()
+        info = gp.info()
+    with g.GP(X, y, hyp, n_tiles=128) as gp:
+        t0 = time.perf_counter()
+        mu_d, va_d = gp.predict_var(Xs)
+        t_fp64 = time.perf_counter() - t0
+        f_d = gp.nlml()
+    errs = {"mean": rel(mu_m, mu_d), "var": rel(va_m, va_d), "nlml": abs(f_m - f_d) / abs(f_d),
+            "refine_iters": info["refine_iters"], "refine_residual": info["refine_residual"],
+            "t_mixed_s": t_mixed, "t_fp64_s": t_fp64}
+    print("mixed vs fp64 @32768", errs)
+    assert errs["mean"] < MEAN_TOL
+    assert errs["var"] < 1e-3
+
+
+def test_mixed_gradient_full_cov_and_optimize(g, orc):
+    X, y, Xs, _ = dg.msd_dataset(1024, 256, 8, seed=1004)
+    hyp = (0.9, 1.1, 0.08)
+    f_o, g_o = orc.nlml_grad(X, y, hyp)
+    mu_o, va_o, cv_o = orc.predict(X, y, Xs, hyp, cov=True)
+    h_o, hist_o = orc.optimize(X, y, hyp, steps=5, lr=0.1)
+    with g.GP(X, y, hyp, n_tiles=4, precision="mixed") as gp:
+        f, gr = gp.nlml_grad()
+        mu, cv = gp.predict_full_cov(Xs)
+        hist = gp.optimize(5, lr=0.1)
+    errs = {"grad": rel(gr, g_o), "nlml": abs(f - f_o) / abs(f_o), "cov": rel(cv, cv_o),
+            "mean": rel(mu, mu_o), "hist": rel(hist, hist_o)}
+    print("mixed gradient/cov", errs)
+    assert errs["mean"] < MEAN_TOL
+    assert errs["grad"] < 1e-3
+    assert errs["cov"] < 1e-4
+    assert np.array_equal(cv, cv.T)
+    assert errs["hist"] < 1e-5
+    assert hist[-1] < hist[0]
