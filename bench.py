@@ -47,12 +47,17 @@ def parse():
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--m", type=int, default=8192)
     ap.add_argument("--d", type=int, default=8)
-    ap.add_argument("--tiles", type=int, default=128)
+    ap.add_argument("--tiles", type=int, default=None, help="tiles per dimension (default 128 fp64, 256 mixed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=4096)
     ap.add_argument("--cpu-sample-m", type=int, default=128)
-    return ap.parse_args()
+    ap.add_argument("--no-compare", action="store_true", help="mixed: skip the FP64 comparison run")
+    ap.add_argument("--fp64-tiles", type=int, default=128)
+    args = ap.parse_args()
+    if args.tiles is None:
+        args.tiles = 256 if args.precision == "mixed" else 128
+    return args
 
 
 HYP0 = (1.0, 1.0, 0.1)
@@ -246,7 +251,7 @@ def run_ours(args):
     gp.profile(False)
     K = args.steps
     ph = {k: v[0] / K for k, v in prof.items()}
-    factor_ms = ph["assemble"] + ph["potrf"] + ph["trsm"] + ph["update"] + ph["solve"]
+    factor_ms = ph["assemble"] + ph["potrf"] + ph["trsm"] + ph["update"] + ph["solve"] + ph["refine"]
     # predict+variance = factor + cross-covariance + multi-RHS solve + reductions of the predict call
     predict_var_ms = factor_ms + ph["cross"] + ph["vsolve"]
     grad_ms = factor_ms + ph["trtri"] + ph["lauum"] + ph["adjoint"] + ph["adam"]
@@ -256,16 +261,31 @@ def run_ours(args):
         dist.all_reduce(vals, op=dist.ReduceOp.MAX)
     predict_var_ms, grad_ms, ms_per_step = (float(v) for v in vals.cpu())
 
-    # roofline of the dominant kernel family (FP64 tensor pipe, DMMA)
-    peak, peak_note = fp64_peak()
+    # roofline of the trailing-update kernel (the Cholesky's dominant launch)
     upd_launch_ms = prof["update"][0] / max(prof["update"][1], 1)
     upd_flops_per_launch = update_flops(T, b) / max(T - 1, 1)
-    achieved = upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12
-    roof = {"bound": "tensor", "kernel": "k_update (trailing SYRK/GEMM, mma.sync f64)",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_note": peak_note, "traffic": None,
-            "algorithmic_flops_per_launch": upd_flops_per_launch,
-            "avg_launch_ms": upd_launch_ms, "launches": prof["update"][1] // K}
+    if args.precision == "mixed":
+        pk = peaks() or {}
+        peak = pk.get("bf16_tflops", 1900.0)
+        peak_note = "of measured bf16 burst" if "bf16_tflops" in pk else "of fallback bf16"
+        tensor_flops = 6.0 * upd_flops_per_launch      # six BF16 plane products per FP32-accurate product
+        achieved = tensor_flops / (upd_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k_mupdate (trailing SYRK/GEMM, split-BF16 x6, mma.sync bf16)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_note": peak_note, "traffic": None,
+                "algorithmic_flops_per_launch": upd_flops_per_launch,
+                "tensor_flops_per_launch": tensor_flops,
+                "fp32_equivalent_tflops": upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12,
+                "avg_launch_ms": upd_launch_ms, "launches": prof["update"][1] // K}
+    else:
+        peak, peak_note = fp64_peak()
+        achieved = upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k_update (trailing SYRK/GEMM, mma.sync f64)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_note": peak_note, "traffic": None,
+                "algorithmic_flops_per_launch": upd_flops_per_launch,
+                "avg_launch_ms": upd_launch_ms, "launches": prof["update"][1] // K}
+    peak64, _ = fp64_peak()
     chol_flops = args.n ** 3 / 3.0
     chol_ms = ph["potrf"] + ph["trsm"] + ph["update"]
 
@@ -276,10 +296,15 @@ def run_ours(args):
             "config": workload_config(args),
             "nlml_grad_steps_per_s": 1e3 / grad_ms, "nlml_grad_ms": grad_ms,
             "cholesky_tflops": chol_flops / (chol_ms * 1e-3) / 1e12,
-            "cholesky_frac_of_fp64_peak": chol_flops / (chol_ms * 1e-3) / 1e12 / peak,
+            "cholesky_frac_of_fp64_peak": chol_flops / (chol_ms * 1e-3) / 1e12 / peak64,
             "phases_ms": {k: round(v, 3) for k, v in ph.items()},
             "roofline": roof, "gpu_launches": launches, "clocks": clk.summary()}
 
+    if args.precision == "mixed":
+        line["refine_iters"] = gp.info()["refine_iters"]
+        line["refine_residual"] = gp.info()["refine_residual"]
+    if args.precision == "mixed" and not args.no_compare:
+        line["mixed_vs_fp64"] = compare_fp64(args, gprat, torch, dev, gp, X, y, Xs, predict_var_ms)
     if rank == 0 and world == 1 and not args.no_e2e:
         line["e2e"] = e2e(args, gprat, torch, dev, Xh, yh, Xsh)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -289,6 +314,33 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def compare_fp64(args, gprat, torch, dev, gp_mixed, X, y, Xs, mixed_ms):
+    """The FP64 path on the same inputs (one warm run, after one untimed run):
+    its predict+variance time and the mixed path's relative errors against it."""
+    def rel(a, b):
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+    gp_mixed.set_hyper(HYP0)
+    mu_m, va_m, _ = gp_mixed.predict(Xs, mean=True, var=True)
+    f_m = gp_mixed.nlml()
+    stream = torch.cuda.current_stream(dev)
+    with gprat.GP(X, y, HYP0, n_tiles=args.fp64_tiles) as g64:
+        g64.predict(Xs, mean=True, var=True)
+        g64.set_hyper(HYP0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        mu_d, va_d, _ = g64.predict(Xs, mean=True, var=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        f_d = g64.nlml()
+    fp64_ms = e0.elapsed_time(e1)
+    return {"fp64_predict_var_ms": fp64_ms, "speedup": fp64_ms / mixed_ms,
+            "rel_err": {"mean": rel(mu_m, mu_d), "var": rel(va_m, va_d), "nlml": abs(f_m - f_d) / abs(f_d)},
+            "note": "norm-wise relative error of the mixed outputs against the FP64 GPU path, same inputs"}
 
 
 def e2e(args, gprat, torch, dev, Xh, yh, Xsh):

@@ -75,10 +75,13 @@ typedef struct {
     double adam_beta1, adam_beta2, adam_eps;
     void* cuda_stream;      /* cudaStream_t used for all work */
     gp_scheduler scheduler; /* how the Cholesky tile DAG is executed */
+    int var_correction;     /* GP_MIXED: 1 corrects the predictive variances to FP64 level
+                               (see gp_predict_var), 0 returns the mixed-factor variances */
 } gp_options;
 
 /* Fills defaults: n_tiles 16, FP64, latent variance, refine_tol 1e-14,
- * refine_max_iter 20, Adam (0.9, 0.999, 1e-8), default stream, stream scheduler. */
+ * refine_max_iter 20, Adam (0.9, 0.999, 1e-8), default stream, stream
+ * scheduler, variance correction on. */
 void gp_default_options(gp_options* opt);
 
 /* Creates a GP over n training points X (n x d) with targets y (n).  Copies

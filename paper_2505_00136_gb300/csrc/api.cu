@@ -123,10 +123,26 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     dev_free(h, &h->vpart, old * (h->Np / (2 * TB)));
     dev_free(h, &h->outm, old);
     dev_free(h, &h->outv, old);
+    dev_free(h, &h->R64, old * h->Np);
+    dev_free(h, &h->Rr32, old * h->Np);
+    dev_free(h, &h->YP, 3 * old * h->b);
+    dev_free(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * old * h->Np);
+    dev_free(h, &h->mu, old);
+    dev_free(h, &h->qpart, 2 * old * (h->Np / (2 * TB)));
+    dev_free(h, &h->vpart2, old * (h->Np / (2 * TB)));
     h->m_cap = 0;
     gp_status s;
     if ((s = dev_alloc(h, &h->Xs, ldm * h->d)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->R32, ldm * h->Np)) != GP_OK) return s;
+    if (h->opt.var_correction) {
+        if ((s = dev_alloc(h, &h->R64, ldm * h->Np)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->Rr32, ldm * h->Np)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->YP, 3 * ldm * h->b)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * ldm * h->Np)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->mu, ldm)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->qpart, 2 * ldm * (h->Np / (2 * TB)))) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->vpart2, ldm * (h->Np / (2 * TB)))) != GP_OK) return s;
+    }
     if ((s = dev_alloc(h, &h->RP, 3 * ldm * h->b)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->WP, 3 * ldm * h->Np)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->mpart, ldm * (h->Np / TB))) != GP_OK) return s;
@@ -135,6 +151,13 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     if ((s = dev_alloc(h, &h->outv, ldm)) != GP_OK) return s;
     h->m_cap = ldm;
     return GP_OK;
+}
+
+gp_status ensure_kslices(gp_t h)
+{
+    if (h->KS) return GP_OK;
+    h->ks_valid = false;
+    return dev_alloc(h, &h->KS, (int64_t)gpk::GP_OZ_SLICES * h->Np * h->Np);
 }
 
 gp_status ensure_predict_space(gp_t h, int64_t m)
@@ -238,6 +261,7 @@ gp_status ensure_factored(gp_t h)
     if (h->factored) return GP_OK;
     gp_status s;
     if (h->opt.prec == GP_MIXED) {
+        h->ks_valid = false;
         if ((s = factor_mixed_refined(h)) != GP_OK) return s;
         h->factored = true;
         return GP_OK;
@@ -367,6 +391,7 @@ void gp_default_options(gp_options* opt)
     opt->adam_eps = 1e-8;
     opt->cuda_stream = nullptr;
     opt->scheduler = GP_SCHED_STREAM;
+    opt->var_correction = 1;
 }
 
 const char* gp_status_str(gp_status s)
@@ -393,7 +418,8 @@ void gp_destroy(gp_t h)
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
                     h->PA, h->D64, h->X64, h->r32, h->t32, h->w32, h->res, h->norms, h->R32, h->RP,
-                    h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32};
+                    h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32, h->YP,
+                    h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int64_t i = 0; i < h->ev_cap; ++i) cudaEventDestroy(h->ev_pool[i]);
@@ -462,6 +488,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(dev_alloc(h, &h->w32, h->Np));
         TRY(dev_alloc(h, &h->res, h->Np));
         TRY(dev_alloc(h, &h->norms, 2));
+        TRY(dev_alloc(h, &h->kappa, 1));
     }
     TRY(cuda_status(h, cudaMemsetAsync(h->X, 0, (size_t)(h->Np * d) * sizeof(double), h->st)));
     TRY(cuda_status(h, cudaMemsetAsync(h->y, 0, (size_t)h->Np * sizeof(double), h->st)));
@@ -509,6 +536,10 @@ gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* 
             if ((s = copy_any(h, cov, target, m * m)) != GP_OK) return s;
             any_host = true;
         }
+    }
+    if (var && h->opt.prec == GP_MIXED && h->opt.var_correction) {
+        if ((s = ensure_kslices(h)) != GP_OK) return s;
+        gpk::var_correction_mixed(h, m, ldm);
     }
     if (mean) {
         if ((s = copy_any(h, mean, h->outm, m)) != GP_OK) return s;
@@ -592,6 +623,7 @@ gp_status gp_optimize(gp_t h, int steps, double lr, double* nlml_hist)
         if (!(it == 0 && reuse_first)) {
             if (mixed) {
                 // the refinement loop synchronises per sweep; a failed factor ends the loop
+                h->ks_valid = false;
                 if ((s = factor_mixed_refined(h)) != GP_OK) break;
             } else {
                 launch_factor_body(h);

@@ -154,6 +154,94 @@ static __device__ __forceinline__ void bgemm_acc(BAcc& acc, const BView& A, cons
     __syncthreads();
 }
 
+// "NN" form: B is stored k-major, element (k, col) of plane q at
+// p[q * ps + k * ld + col]; `rows` bounds the columns.  Fragments come from
+// ldmatrix.trans on a [k][col] shared-memory layout (rows of 136 BF16).
+constexpr int BN_LD = 136;
+constexpr int BN_PLANE = BG_KS * BN_LD;            // bf16 per plane per stage (B, NN form)
+constexpr int BN_STAGE = 3 * BG_PLANE + 3 * BN_PLANE;
+constexpr int BN_SMEM_BYTES = 2 * BN_STAGE * 2;
+
+__device__ __forceinline__ void bn_stage_load(const BView& v, int64_t k0, __nv_bfloat16* s)
+{
+    // 3 planes x 32 k-rows x 16 chunks of 8 columns = 1536 chunks; 6 per thread
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        int idx = threadIdx.x + q * 256;
+        int plane = idx >> 9, rem = idx & 511;
+        int kr = rem >> 4, ch = rem & 15;
+        bool ok = ch * 8 < v.rows;
+        const __nv_bfloat16* src = v.p + plane * v.ps + (k0 + kr) * v.ld + (ok ? ch * 8 : 0);
+        cp_async16(s + plane * BN_PLANE + kr * BN_LD + ch * 8, src, ok);
+    }
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&d)[4], const __nv_bfloat16* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3])
+                 : "r"(smem_u32(p)));
+}
+
+// acc += A B over k in [kb, ke), A in NT form (rows x k), B in NN form (k x cols).
+// smem: BN_SMEM_BYTES.  Starts and ends with a CTA barrier.
+static __device__ __forceinline__ void bgemm_acc_nn(BAcc& acc, const BView& A, const BView& B, int64_t kb,
+                                                     int64_t ke, __nv_bfloat16* smem)
+{
+    __syncthreads();
+    const int nst = (int)((ke - kb) / BG_KS);
+    if (nst <= 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp >> 2, wn = warp & 3;
+    const int lq = lane >> 3, lr = lane & 7;
+    bg_stage_load(A, kb, smem);
+    bn_stage_load(B, kb, smem + 3 * BG_PLANE);
+    cp_async_commit();
+    for (int s = 0; s < nst; ++s) {
+        __nv_bfloat16* cur = smem + (s & 1) * BN_STAGE;
+        cp_async_wait_all();
+        __syncthreads();
+        if (s + 1 < nst) {
+            __nv_bfloat16* nxt = smem + ((s + 1) & 1) * BN_STAGE;
+            bg_stage_load(A, kb + (int64_t)(s + 1) * BG_KS, nxt);
+            bn_stage_load(B, kb + (int64_t)(s + 1) * BG_KS, nxt + 3 * BG_PLANE);
+            cp_async_commit();
+        }
+        const __nv_bfloat16* As = cur;
+        const __nv_bfloat16* Bs = cur + 3 * BG_PLANE;
+#pragma unroll
+        for (int kk = 0; kk < BG_KS; kk += 16) {
+            uint32_t bf[3][4][2];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int np = 0; np < 2; ++np) {
+                    uint32_t d[4];
+                    const int n0 = wn * 32 + np * 16;
+                    ldsm_x4_t(d, Bs + q * BN_PLANE + (kk + (lq & 1) * 8 + lr) * BN_LD + n0 + (lq >> 1) * 8);
+                    bf[q][np * 2][0] = d[0];
+                    bf[q][np * 2][1] = d[1];
+                    bf[q][np * 2 + 1][0] = d[2];
+                    bf[q][np * 2 + 1][1] = d[3];
+                }
+#pragma unroll
+            for (int qa = 0; qa < 3; ++qa) {
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) {
+                    uint32_t af[4];
+                    const int m0 = wm * 64 + mt * 16;
+                    ldsm_x4(af, As + qa * BG_PLANE + (m0 + lr + (lq & 1) * 8) * BG_LD + kk + (lq >> 1) * 8);
+#pragma unroll
+                    for (int qb = 0; qb + qa < 3; ++qb)
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc.c[mt][nt], af, bf[qb][nt][0], bf[qb][nt][1]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // Visits (row, col, value) of this thread's accumulator entries, rows and
 // columns in [0, 128).
 template <class F>

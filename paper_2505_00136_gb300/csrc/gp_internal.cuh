@@ -86,6 +86,17 @@ struct gp_handle {
     __nv_bfloat16 *RP, *WP;   // planes: RP 3 x m_cap x b (scratch), WP 3 x m_cap x Np (all of W)
     double* mpart;            // (Np/64) x m_cap mean partial sums
     double* vpart;            // (Np/128) x m_cap variance partial sums
+    // variance correction (GP_MIXED)
+    double* R64;              // m_cap x Np: FP64 K_{Z*,Z}
+    float* Rr32;              // m_cap x Np: r0 = K_{Z*,Z} - x0^T K
+    __nv_bfloat16* YP;        // 3 x m_cap x b planes (backward solve)
+    __nv_bfloat16* YS;        // digit slices of x0^T, OZ_S x m_cap x Np
+    __nv_bfloat16* KS;        // digit slices of K, OZ_S x Np x Np (allocated on first use)
+    double* mu;               // m_cap row scales of x0^T
+    double* kappa;            // scale of K
+    double* qpart;            // 2 x (Np/128) x m_cap partial sums
+    double* vpart2;           // (Np/128) x m_cap partial sums of ||L~^{-1} r0||^2
+    bool ks_valid;            // KS matches the current K
     __nv_bfloat16* ZP;        // T(T+1)/2 tiles x 3 planes of (L^{-1})^T tiles (gradient)
     float* U32;               // T(T+1)/2 tiles: TRTRI accumulators (gradient)
     float* Kinv32;            // T(T+1)/2 tiles: K^{-1} lower (gradient)
@@ -149,6 +160,8 @@ void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var);
 void copy_factor_dense_mixed(gp_t h, double* out);
 void full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov);  // cov (prefilled prior) -= W W^T
 void inverse_mixed(gp_t h);                                    // Kinv32 = (L~ L~^T)^{-1}
+void var_correction_mixed(gp_t h, int64_t m, int64_t ldm);     // FP64-level variances into outv
+constexpr int GP_OZ_SLICES = 6;                                // digit slices per operand (kernels_mixed.cu)
 }  // namespace gpk
 
 #define GP_CUDA_OK(call)                                                   \

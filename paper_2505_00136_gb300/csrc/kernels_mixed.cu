@@ -290,7 +290,8 @@ __global__ void k_nlml_mixed(const double* y, const double* alpha, int64_t n, co
 // sums of K_{Z*,Z} alpha over the block's 64 training points (Eq. 3).
 __global__ __launch_bounds__(NTH) void k_cross_mixed(const double* Xs, int64_t m, const double* X, int64_t n,
                                                      int64_t d, const double* alpha, const GpHyperDev* hyp,
-                                                     float* R32, int64_t ldr, double* mpart, int64_t ldp)
+                                                     float* R32, int64_t ldr, double* mpart, int64_t ldp,
+                                                     double* R64)
 {
     __shared__ double sm[2 * 64 * 17];
     const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
@@ -307,6 +308,7 @@ __global__ __launch_bounds__(NTH) void k_cross_mixed(const double* Xs, int64_t m
             const int64_t gn = n0 + tx + 16 * c;
             double kv = (gm < m && gn < n) ? nu * exp(-r2[a][c] * c2) : 0.0;
             R32[gm * ldr + gn] = (float)kv;
+            if (R64) R64[gm * ldr + gn] = kv;
             if (gn < n) s = fma(kv, alpha[gn], s);
         }
 #pragma unroll
@@ -335,7 +337,7 @@ __global__ void k_split_cols(const float* R32, int64_t ldr, int64_t j, int64_t b
 // sums of W_j^2 into vpart[(j*Q + cb)][row].
 __global__ __launch_bounds__(NTH) void k_mdiagW(const __nv_bfloat16* RP, const __nv_bfloat16* LinvP,
                                                 __nv_bfloat16* WP, int64_t ldw, double* vpart, int64_t ldm,
-                                                int64_t b, int64_t j)
+                                                int64_t b, int64_t j, float* Wout)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double rs[4][MB];
@@ -351,6 +353,7 @@ __global__ __launch_bounds__(NTH) void k_mdiagW(const __nv_bfloat16* RP, const _
     const int64_t psw = ldm * ldw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wn = warp & 3, wm = warp >> 2;
     double rowsq[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    float* wout = Wout + m0 * ldw + j * b + cb * MB;   // W_j in FP32 over R_j (same layout as WP)
     bacc_for_each(acc, [&](int r, int c, float v) {
         int64_t o = (int64_t)r * ldw + c;
         __nv_bfloat16 hi, mid, lo;
@@ -358,6 +361,7 @@ __global__ __launch_bounds__(NTH) void k_mdiagW(const __nv_bfloat16* RP, const _
         wp[o] = hi;
         wp[psw + o] = mid;
         wp[2 * psw + o] = lo;
+        wout[o] = v;
     });
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt)
@@ -549,6 +553,319 @@ __global__ __launch_bounds__(NTH) void k_mlauum(const __nv_bfloat16* ZP, float* 
     bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * b + c] = v; });
 }
 
+// ---------------------------------------------------------------- variance correction
+// With x0 = (L~ L~^T)^{-1} k* from the mixed factor and r0 = k* - K x0,
+//   k*^T K^{-1} k* = k*^T x0 + x0^T r0 + r0^T K^{-1} r0,
+// and the last term is taken with the mixed factor, ||L~^{-1} r0||^2 (its
+// error is third order in the factor's error).  Only K x0 must be accurate to
+// FP64 level; it is formed from exactly-accumulated BF16 digit slices (Ozaki
+// et al. 2012): each row of Y = x0^T and all of K are scaled by a power of two
+// and split into 7-bit integer digits, every digit product is exact, sums of
+// at most 1024 of them are exact in FP32, and the partial sums are carried in
+// double-FP32.
+
+// Backward solve, diagonal step: Y_i = S_i Linv_ii (NN form: Linv_ii[t][c],
+// nonzero for t >= c).  Writes Y_i in FP32 over S_i (column block i of R32)
+// and its planes into YP (3 x ldm x b).
+__global__ __launch_bounds__(NTH) void k_mbdiag(const __nv_bfloat16* RP, const __nv_bfloat16* LinvP,
+                                                __nv_bfloat16* YP, float* R32, int64_t ldr, int64_t ldm,
+                                                int64_t b, int64_t i)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int cb = blockIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.y * MB, bb = b * b, ps = ldm * b;
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{RP + m0 * b, b, ps, MB};
+    BView vb{LinvP + i * 3 * bb + (int64_t)cb * MB, b, bb, MB};
+    bgemm_acc_nn(acc, va, vb, (int64_t)cb * MB, b, (__nv_bfloat16*)smem_raw);
+    __nv_bfloat16* yp = YP + m0 * b + cb * MB;
+    float* dst = R32 + m0 * ldr + i * b + cb * MB;
+    bacc_for_each(acc, [&](int r, int c, float v) {
+        dst[(int64_t)r * ldr + c] = v;
+        int64_t o = (int64_t)r * b + c;
+        __nv_bfloat16 hi, mid, lo;
+        split3(v, hi, mid, lo);
+        yp[o] = hi;
+        yp[ps + o] = mid;
+        yp[2 * ps + o] = lo;
+    });
+}
+
+// Backward solve, update: S_j -= Y_i L_ij for j < i (NN form: L_ij[t][c]).
+__global__ __launch_bounds__(NTH) void k_mbupd(float* R32, int64_t ldr, const __nv_bfloat16* YP,
+                                               const __nv_bfloat16* LP, int64_t ldm, int64_t b, int64_t i)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Q = (int)(b / MB);
+    const int64_t j = blockIdx.x / Q;
+    const int cb = blockIdx.x % Q;
+    const int64_t m0 = (int64_t)blockIdx.y * MB, bb = b * b, ps = ldm * b;
+    BAcc acc;
+    bacc_zero(acc);
+    BView va{YP + m0 * b, b, ps, MB};
+    BView vb{LP + tri_index(i, j) * 3 * bb + (int64_t)cb * MB, b, bb, MB};
+    bgemm_acc_nn(acc, va, vb, 0, b, (__nv_bfloat16*)smem_raw);
+    float* dst = R32 + m0 * ldr + j * b + cb * MB;
+    bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * ldr + c] -= v; });
+}
+
+constexpr int OZ_S = GP_OZ_SLICES;   // digit slices per operand (7 bits each)
+constexpr int OZ_LMAX = 7;     // keep digit pairs (s, u), 1-based, with s + u <= OZ_LMAX
+constexpr int OZ_CHUNK = 1024; // k-terms summed exactly in FP32 before a flush
+constexpr int OZ_SMEM_BYTES = 3 * 2 * BG_PLANE * 2;   // 3 stages x {A, B} single planes
+
+__device__ __forceinline__ double pow2_ceil(double x)   // smallest power of two >= x (x > 0)
+{
+    int e;
+    double f = frexp(x, &e);   // x = f 2^e, f in [0.5, 1)
+    return (f == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+// Digits of each row of Y (R32, ldm x Np): mu[row] = power of two >= max |Y|,
+// YS[s][row][col] = s-th 7-bit rounded digit of Y / mu.  One CTA per row.
+__global__ void k_yslices(const float* Y, int64_t Np, __nv_bfloat16* YS, int64_t ps, double* mu)
+{
+    __shared__ float red[NTH];
+    const int64_t row = blockIdx.x;
+    const float* y = Y + row * Np;
+    float mx = 0.f;
+    for (int64_t c = threadIdx.x; c < Np; c += NTH) mx = fmaxf(mx, fabsf(y[c]));
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = NTH / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double m = red[0] > 0.f ? pow2_ceil((double)red[0]) : 1.0;
+    if (threadIdx.x == 0) mu[row] = m;
+    const double inv = 1.0 / m;
+    for (int64_t c = threadIdx.x; c < Np; c += NTH) {
+        double a = (double)y[c] * inv;
+        for (int s = 0; s < OZ_S; ++s) {
+            double dgt = rint(a * 128.0);
+            YS[s * ps + row * Np + c] = __float2bfloat16_rn((float)dgt);
+            a = a * 128.0 - dgt;
+        }
+    }
+}
+
+// Digits of the full symmetric K (from the lower FP64 tiles) scaled by
+// kappa = power of two >= max(nu + sigma^2, 1).
+__global__ void k_kslices(const double* K64, int64_t b, int64_t Np, const GpHyperDev* hyp, __nv_bfloat16* KS,
+                          int64_t ps, double* kappa_out)
+{
+    const double kappa = pow2_ceil(fmax(hyp->nu + hyp->s2, 1.0));
+    if (blockIdx.x == 0 && threadIdx.x == 0) *kappa_out = kappa;
+    const double inv = 1.0 / kappa;
+    const int64_t total = Np * Np;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e / Np, c = e % Np;
+        int64_t rr = r >= c ? r : c, cc = r >= c ? c : r;
+        double a = K64[tri_index(rr / b, cc / b) * b * b + (rr % b) * b + (cc % b)] * inv;
+        for (int s = 0; s < OZ_S; ++s) {
+            double dgt = rint(a * 128.0);
+            KS[s * ps + e] = __float2bfloat16_rn((float)dgt);
+            a = a * 128.0 - dgt;
+        }
+    }
+}
+
+// p-th kept digit pair (s, u), 1-based, enumerated s-major with s + u <= OZ_LMAX.
+__device__ __forceinline__ void oz_pair(int p, int& s, int& u)
+{
+    s = 1;
+    while (true) {
+        const int cnt = max(0, min(OZ_S, OZ_LMAX - s));
+        if (p < cnt) break;
+        p -= cnt;
+        ++s;
+    }
+    u = p + 1;
+}
+
+__device__ __forceinline__ void oz_stage_load(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t Np,
+                                              int64_t k0, __nv_bfloat16* s)
+{
+    // A and B: 128 rows x 4 chunks each = 1024 chunks; 4 per thread
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int idx = threadIdx.x + q * 256;
+        int which = idx >> 9, rem = idx & 511;
+        int r = rem >> 2, ch = rem & 3;
+        const __nv_bfloat16* src = (which ? B : A) + (int64_t)r * Np + k0 + ch * 8;
+        cp_async16(s + which * BG_PLANE + r * BG_LD + ch * 8, src, true);
+    }
+}
+
+// C = Y K for a 128 x 128 block (rows: test points, cols: training points) from
+// the digit pairs, then the fused epilogue: r0 = Kc - C (FP32 into Rr32) and
+// per-row partial sums of Kc Y and Y r0 into qpart[0|1][col block][row].
+__global__ __launch_bounds__(NTH, 1) void k_ozaki_q(const __nv_bfloat16* YS, int64_t yps, const __nv_bfloat16* KS,
+                                                    int64_t kps, int64_t Np, const double* mu,
+                                                    const double* kappa_p, const double* R64, const float* Y,
+                                                    float* Rr32, double* qpart, int64_t ldm, int64_t m,
+                                                    int64_t n_valid)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double rs[2][4][MB];
+    __nv_bfloat16* smem = (__nv_bfloat16*)smem_raw;
+    // grouped raster: 8 row blocks share each column block in flight
+    const int64_t nbn = Np / MB, nbm = ldm / MB;
+    const int64_t g = blockIdx.x, G = 8;
+    const int64_t grp = g / (G * nbn), first = grp * G;
+    const int64_t gsz = (nbm - first) < G ? (nbm - first) : G;
+    const int64_t mb = first + (g % (G * nbn)) % gsz, nb = (g % (G * nbn)) / gsz;
+    const int64_t m0 = mb * MB, n0 = nb * MB;
+
+    float acc[4][4][4], hi[4][4][4], lo[4][4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[a][c][e] = hi[a][c][e] = lo[a][c][e] = 0.f;
+
+    int np = 0;
+    for (int s = 1; s <= OZ_S; ++s) np += max(0, min(OZ_S, OZ_LMAX - s));
+    const int kst = (int)(Np / BG_KS);
+    const int64_t total = (int64_t)np * kst;
+    const int stage_elems = 2 * BG_PLANE;
+    auto issue = [&](int64_t gs) {
+        if (gs < total) {
+            int p = (int)(gs / kst), k = (int)(gs % kst), ps_, pu_;
+            oz_pair(p, ps_, pu_);
+            const __nv_bfloat16* A = YS + (ps_ - 1) * yps + m0 * Np;
+            const __nv_bfloat16* B = KS + (pu_ - 1) * kps + n0 * Np;
+            oz_stage_load(A, B, Np, (int64_t)k * BG_KS, smem + (gs % 3) * stage_elems);
+        }
+        cp_async_commit();
+    };
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp >> 2, wn = warp & 3;
+    const int lq = lane >> 3, lr = lane & 7;
+    issue(0);
+    issue(1);
+    for (int64_t gs = 0; gs < total; ++gs) {
+        asm volatile("cp.async.wait_group 1;\n" ::);
+        __syncthreads();
+        issue(gs + 2);
+        const __nv_bfloat16* As = smem + (gs % 3) * stage_elems;
+        const __nv_bfloat16* Bs = As + BG_PLANE;
+#pragma unroll
+        for (int kk = 0; kk < BG_KS; kk += 16) {
+            uint32_t bf[4][2];
+#pragma unroll
+            for (int npr = 0; npr < 2; ++npr) {
+                uint32_t d[4];
+                const int c0 = wn * 32 + npr * 16;
+                ldsm_x4(d, Bs + (c0 + lr + (lq >> 1) * 8) * BG_LD + kk + (lq & 1) * 8);
+                bf[npr * 2][0] = d[0];
+                bf[npr * 2][1] = d[1];
+                bf[npr * 2 + 1][0] = d[2];
+                bf[npr * 2 + 1][1] = d[3];
+            }
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                uint32_t af[4];
+                ldsm_x4(af, As + (wm * 64 + mt * 16 + lr + (lq & 1) * 8) * BG_LD + kk + (lq >> 1) * 8);
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af, bf[nt][0], bf[nt][1]);
+            }
+        }
+        const int k = (int)(gs % kst);
+        if ((k + 1) % (OZ_CHUNK / BG_KS) == 0 || k + 1 == kst) {
+            int ps_, pu_;
+            oz_pair((int)(gs / kst), ps_, pu_);
+            const float scale = ldexpf(1.f, -7 * (ps_ + pu_));
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        // double-FP32 accumulation (Knuth TwoSum) of an exact term
+                        const float v = acc[a][c][e] * scale;
+                        const float s = hi[a][c][e] + v;
+                        const float bv = s - hi[a][c][e];
+                        const float er = (hi[a][c][e] - (s - bv)) + (v - bv);
+                        hi[a][c][e] = s;
+                        lo[a][c][e] += er;
+                        acc[a][c][e] = 0.f;
+                    }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncthreads();
+
+    const double kappa = *kappa_p;
+    const int gq = lane >> 2, t = lane & 3;
+    double s1[4][2], s2[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) s1[a][0] = s1[a][1] = s2[a][0] = s2[a][1] = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int64_t gm = m0 + wm * 64 + a * 16 + gq + hh * 8;
+            const double scale = (gm < m) ? mu[gm] * kappa : 0.0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int64_t gn = n0 + wn * 32 + c * 8 + 2 * t + e;
+                    const int fe = hh * 2 + e;
+                    const int64_t o = gm * Np + gn;
+                    if (gm < m && gn < n_valid) {
+                        const double Cv = ((double)hi[a][c][fe] + (double)lo[a][c][fe]) * scale;
+                        const double kc = R64[o], x = (double)Y[o];
+                        const double r = kc - Cv;
+                        Rr32[o] = (float)r;
+                        s1[a][hh] = fma(kc, x, s1[a][hh]);
+                        s2[a][hh] = fma(x, r, s2[a][hh]);
+                    } else if (gm < ldm) {
+                        Rr32[o] = 0.f;
+                    }
+                }
+        }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                s1[a][hh] += __shfl_xor_sync(0xffffffffu, s1[a][hh], o);
+                s2[a][hh] += __shfl_xor_sync(0xffffffffu, s2[a][hh], o);
+            }
+            if (t == 0) {
+                const int rr = wm * 64 + a * 16 + gq + hh * 8;
+                rs[0][wn][rr] = s1[a][hh];
+                rs[1][wn][rr] = s2[a][hh];
+            }
+        }
+    __syncthreads();
+    if (threadIdx.x < 2 * MB) {
+        const int w = threadIdx.x / MB, r = threadIdx.x % MB;
+        qpart[((int64_t)w * nbn + nb) * ldm + m0 + r] = rs[w][0][r] + rs[w][1][r] + rs[w][2][r] + rs[w][3][r];
+    }
+}
+
+// var = k** - (sum k*^T x0 + sum x0^T r0 + ||L~^{-1} r0||^2), mean untouched.
+__global__ void k_var_finish(const double* qpart, int64_t nqb, const double* vpart2, int64_t nvp, int64_t ldm,
+                             int64_t m, const GpHyperDev* hyp, int noisy, double* var)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int64_t q = 0; q < nqb; ++q) {
+        s1 += qpart[q * ldm + c];
+        s2 += qpart[(nqb + q) * ldm + c];
+    }
+    for (int64_t q = 0; q < nvp; ++q) s3 += vpart2[q * ldm + c];
+    var[c] = hyp->nu + (noisy ? hyp->s2 : 0.0) - (s1 + s2 + s3);
+}
+
 __global__ void k_factor_dense32(const float* Lt, int64_t b, int64_t n, double* out)
 {
     int64_t total = n * n;
@@ -582,6 +899,9 @@ static void ensure_attrs_mixed()
     cudaFuncSetAttribute(k_mtrtri_fin, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
     cudaFuncSetAttribute(k_mtrtri_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
     cudaFuncSetAttribute(k_mlauum, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mbdiag, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mbupd, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
+    cudaFuncSetAttribute(k_ozaki_q, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
     done_dev = dev;
 }
 
@@ -671,30 +991,69 @@ void nlml_mixed(gp_t h)
                (const double*)h->logdet_part, h->T, h->scal);
 }
 
+// Forward multi-RHS solve W = R L~^{-T} in place over R (ldm x Np, FP32): W
+// planes into WP, FP32 W over R, FP64 row sums of W^2 into vpart.
+static void forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase)
+{
+    const int64_t T = h->T, b = h->b, Np = h->Np;
+    const int Q = (int)(b / MB);
+    for (int64_t j = 0; j < T; ++j) {
+        GPK_LAUNCH(h, phase, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)R, Np, j, b, ldm, h->RP);
+        GPK_LAUNCH(h, phase, k_mdiagW, dim3((unsigned)Q, (unsigned)(ldm / MB)), NTH, BG_SMEM_BYTES,
+                   (const __nv_bfloat16*)h->RP, (const __nv_bfloat16*)h->LinvP, h->WP, Np, vpart, ldm, b, j, R);
+        if (j + 1 < T)
+            GPK_LAUNCH(h, phase, k_mupdW, dim3((unsigned)((T - j - 1) * Q), (unsigned)(ldm / MB)), NTH,
+                       BG_SMEM_BYTES, R, Np, (const __nv_bfloat16*)h->WP, (const __nv_bfloat16*)h->LP, ldm, b, j);
+    }
+}
+
 void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
+{
+    ensure_attrs_mixed();
+    const int64_t Np = h->Np;
+    const int64_t nmp = Np / 64, nvp = Np / MB;
+    GPK_LAUNCH(h, GP_PH_CROSS, k_cross_mixed, dim3((unsigned)(Np / 64), (unsigned)(ldm / 64)), NTH, 0,
+               (const double*)h->Xs, m, (const double*)h->X, h->n, h->d, (const double*)h->alpha,
+               (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm, h->R64);
+    if (want_var) forward_w(h, h->R32, ldm, h->vpart, GP_PH_VSOLVE);
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_mixed_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->mpart,
+               nmp, (const double*)h->vpart, want_var ? nvp : (int64_t)0, ldm, m, (const GpHyperDev*)h->hyp,
+               h->opt.noisy_test_var, h->outm, want_var ? h->outv : (double*)nullptr);
+}
+
+// Corrected variances into h->outv (needs predict_mixed's forward solve: R32
+// holds W, R64 holds K_{Z*,Z}).  Overwrites the W planes (run after full_cov_mixed).
+void var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 {
     ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, Np = h->Np;
     const int Q = (int)(b / MB);
-    const int64_t nmp = Np / 64, nvp = Np / MB;
-    GPK_LAUNCH(h, GP_PH_CROSS, k_cross_mixed, dim3((unsigned)(Np / 64), (unsigned)(ldm / 64)), NTH, 0,
-               (const double*)h->Xs, m, (const double*)h->X, h->n, h->d, (const double*)h->alpha,
-               (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm);
-    if (want_var) {
-        for (int64_t j = 0; j < T; ++j) {
-            GPK_LAUNCH(h, GP_PH_VSOLVE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np, j, b,
-                       ldm, h->RP);
-            GPK_LAUNCH(h, GP_PH_VSOLVE, k_mdiagW, dim3((unsigned)Q, (unsigned)(ldm / MB)), NTH, BG_SMEM_BYTES,
-                       (const __nv_bfloat16*)h->RP, (const __nv_bfloat16*)h->LinvP, h->WP, Np, h->vpart, ldm, b, j);
-            if (j + 1 < T)
-                GPK_LAUNCH(h, GP_PH_VSOLVE, k_mupdW, dim3((unsigned)((T - j - 1) * Q), (unsigned)(ldm / MB)), NTH,
-                           BG_SMEM_BYTES, h->R32, Np, (const __nv_bfloat16*)h->WP, (const __nv_bfloat16*)h->LP,
-                           ldm, b, j);
-        }
+    const unsigned gm = (unsigned)(ldm / MB);
+    // x0^T = W L~^{-1}: backward sweep over tile columns, in place over R32
+    for (int64_t i = T - 1; i >= 0; --i) {
+        GPK_LAUNCH(h, GP_PH_REFINE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np, i, b, ldm,
+                   h->RP);
+        GPK_LAUNCH(h, GP_PH_REFINE, k_mbdiag, dim3((unsigned)Q, gm), NTH, BN_SMEM_BYTES, (const __nv_bfloat16*)h->RP,
+                   (const __nv_bfloat16*)h->LinvP, h->YP, h->R32, Np, ldm, b, i);
+        if (i > 0)
+            GPK_LAUNCH(h, GP_PH_REFINE, k_mbupd, dim3((unsigned)(i * Q), gm), NTH, BN_SMEM_BYTES, h->R32, Np,
+                       (const __nv_bfloat16*)h->YP, (const __nv_bfloat16*)h->LP, ldm, b, i);
     }
-    GPK_LAUNCH(h, GP_PH_REDUCE, k_mixed_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->mpart,
-               nmp, (const double*)h->vpart, want_var ? nvp : (int64_t)0, ldm, m, (const GpHyperDev*)h->hyp,
-               h->opt.noisy_test_var, h->outm, want_var ? h->outv : (double*)nullptr);
+    GPK_LAUNCH(h, GP_PH_REFINE, k_yslices, (unsigned)ldm, NTH, 0, (const float*)h->R32, Np, h->YS, ldm * Np, h->mu);
+    if (!h->ks_valid) {
+        GPK_LAUNCH(h, GP_PH_REFINE, k_kslices, grid_for(Np * Np), NTH, 0, (const double*)h->L, b, Np,
+                   (const GpHyperDev*)h->hyp, h->KS, Np * Np, h->kappa);
+        h->ks_valid = true;
+    }
+    const int64_t nbn = Np / MB;
+    GPK_LAUNCH(h, GP_PH_REFINE, k_ozaki_q, (unsigned)(nbn * (ldm / MB)), NTH, OZ_SMEM_BYTES,
+               (const __nv_bfloat16*)h->YS, ldm * Np, (const __nv_bfloat16*)h->KS, Np * Np, Np,
+               (const double*)h->mu, (const double*)h->kappa, (const double*)h->R64, (const float*)h->R32,
+               h->Rr32, h->qpart, ldm, m, h->n);
+    forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_REFINE);
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, nbn,
+               (const double*)h->vpart2, Np / MB, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
+               h->outv);
 }
 
 void full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)

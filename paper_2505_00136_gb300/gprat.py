@@ -40,7 +40,7 @@ class gp_options(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("refine_max_iter", ctypes.c_int),
                 ("adam_beta1", ctypes.c_double), ("adam_beta2", ctypes.c_double),
                 ("adam_eps", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("scheduler", ctypes.c_int)]
+                ("scheduler", ctypes.c_int), ("var_correction", ctypes.c_int)]
 
 
 class gp_state(ctypes.Structure):
@@ -138,7 +138,7 @@ class GP:
 
     def __init__(self, X, y, hyper=(1.0, 1.0, 0.1), trainable=(1, 1, 1), n_tiles=16,
                  precision="fp64", noisy_test_var=False, stream=None, scheduler="stream",
-                 refine_tol=None, refine_max_iter=None):
+                 refine_tol=None, refine_max_iter=None, var_correction=True):
         if not _is_torch(X):
             X = np.ascontiguousarray(X, dtype=np.float64)
             y = np.ascontiguousarray(y, dtype=np.float64)
@@ -153,6 +153,7 @@ class GP:
             opt.refine_tol = refine_tol
         if refine_max_iter is not None:
             opt.refine_max_iter = refine_max_iter
+        opt.var_correction = int(bool(var_correction))
         if stream is None and self._torch_dev is not None:
             import torch
             stream = torch.cuda.current_stream(self._torch_dev).cuda_stream

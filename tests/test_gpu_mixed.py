@@ -1,9 +1,11 @@
 """Mixed-precision path (split-BF16 products, FP64 diagonal POTRF, FP64-residual
-refinement) against the FP64 oracle and against the FP64 GPU path.
+refinement, Ozaki-corrected variances) against the FP64 oracle and against the
+FP64 GPU path.
 
 alpha and the predictive mean are refined to FP64 accuracy (mean = K_{Z*,Z}
-alpha): 1e-8 relative.  The factor itself is FP32-accurate.  Reported errors
-are printed for the record (pytest -s).
+alpha) and the variances corrected to FP64 level: both to 1e-8 relative.  The
+factor itself, the NLML (through log|K|), the gradient and the full covariance
+are FP32-accurate.  Reported errors are printed for the record (pytest -s).
 """
 import numpy as np
 import pytest
@@ -15,6 +17,7 @@ from _util import rel
 pytestmark = pytest.mark.gpu
 
 MEAN_TOL = 1e-8
+VAR_TOL = 1e-8
 
 
 @pytest.fixture(scope="module")
@@ -50,6 +53,7 @@ def test_mixed_against_oracle(g, orc, n, m, d, n_tiles):
     assert info["tile"] % 128 == 0
     assert errs["alpha"] < 1e-10
     assert errs["mean"] < MEAN_TOL
+    assert errs["var"] < VAR_TOL
     # FP32-accurate factor: its own error, and the NLML through log|K|, stay at that level
     assert errs["factor"] < 1e-4
     assert errs["nlml"] < 1e-4
@@ -84,6 +88,8 @@ def test_mixed_vs_fp64_full_size(g):
             "t_mixed_s": t_mixed, "t_fp64_s": t_fp64}
     print("mixed vs fp64 @32768", errs)
     assert errs["mean"] < MEAN_TOL
+    assert errs["var"] < VAR_TOL
+    assert t_mixed < t_fp64 / 2
 
 
 def test_mixed_gradient_full_cov_and_optimize(g, orc):
@@ -105,3 +111,18 @@ def test_mixed_gradient_full_cov_and_optimize(g, orc):
     assert np.array_equal(cv, cv.T)
     assert errs["hist"] < 1e-4
     assert hist[-1] < hist[0]
+
+
+def test_uncorrected_variance_is_fp32_level(g, orc):
+    X, y, Xs, _ = dg.msd_dataset(1024, 300, 8, seed=1011)
+    hyp = (1.0, 1.0, 0.1)
+    _, va_o, _ = orc.predict(X, y, Xs, hyp)
+    with g.GP(X, y, hyp, n_tiles=8, precision="mixed", var_correction=False) as gp:
+        _, va_u = gp.predict_var(Xs)
+    with g.GP(X, y, hyp, n_tiles=8, precision="mixed") as gp:
+        _, va_c = gp.predict_var(Xs)
+        _, va_c2 = gp.predict_var(Xs)      # second call reuses the cached K digits
+    e_u, e_c = rel(va_u, va_o), rel(va_c, va_o)
+    print("variance uncorrected / corrected", e_u, e_c)
+    assert 1e-9 < e_u < 1e-3
+    assert e_c < VAR_TOL and rel(va_c2, va_c) < 1e-14
