@@ -448,6 +448,11 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     cudaGetDevice(&h->device);
     h->n = n;
     h->d = d;
+    h->oz_lmax = 7;
+    if (const char* e = getenv("GPRAT_OZAKI_LMAX")) {   // accuracy/speed study knob: 6 or 7
+        int v = atoi(e);
+        if (v >= 4 && v <= 2 * gpk::GP_OZ_SLICES) h->oz_lmax = v;
+    }
     int64_t per = (n + opt.n_tiles - 1) / opt.n_tiles;
     h->b = round_up(per, opt.prec == GP_MIXED ? 2 * TB : TB);
     h->T = (n + h->b - 1) / h->b;

@@ -97,6 +97,7 @@ struct gp_handle {
     double* qpart;            // 2 x (Np/128) x m_cap partial sums
     double* vpart2;           // (Np/128) x m_cap partial sums of ||L~^{-1} r0||^2
     bool ks_valid;            // KS matches the current K
+    int oz_lmax;              // digit pairs (s, u) with s + u <= oz_lmax enter the exact product
     __nv_bfloat16* ZP;        // T(T+1)/2 tiles x 3 planes of (L^{-1})^T tiles (gradient)
     float* U32;               // T(T+1)/2 tiles: TRTRI accumulators (gradient)
     float* Kinv32;            // T(T+1)/2 tiles: K^{-1} lower (gradient)

@@ -611,9 +611,10 @@ __global__ __launch_bounds__(NTH) void k_mbupd(float* R32, int64_t ldr, const __
 }
 
 constexpr int OZ_S = GP_OZ_SLICES;   // digit slices per operand (7 bits each)
-constexpr int OZ_LMAX = 7;     // keep digit pairs (s, u), 1-based, with s + u <= OZ_LMAX
+constexpr int OZ_LMAX_DEFAULT = 7;  // keep digit pairs (s, u), 1-based, with s + u <= lmax
 constexpr int OZ_CHUNK = 1024; // k-terms summed exactly in FP32 before a flush
-constexpr int OZ_SMEM_BYTES = 3 * 2 * BG_PLANE * 2;   // 3 stages x {A, B} single planes
+constexpr int OZ_STAGES = 6;
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * 2 * BG_PLANE * 2;   // stages x {A, B} single planes
 
 __device__ __forceinline__ double pow2_ceil(double x)   // smallest power of two >= x (x > 0)
 {
@@ -672,12 +673,12 @@ __global__ void k_kslices(const double* K64, int64_t b, int64_t Np, const GpHype
     }
 }
 
-// p-th kept digit pair (s, u), 1-based, enumerated s-major with s + u <= OZ_LMAX.
-__device__ __forceinline__ void oz_pair(int p, int& s, int& u)
+// p-th kept digit pair (s, u), 1-based, enumerated s-major with s + u <= lmax.
+__device__ __forceinline__ void oz_pair(int p, int lmax, int& s, int& u)
 {
     s = 1;
     while (true) {
-        const int cnt = max(0, min(OZ_S, OZ_LMAX - s));
+        const int cnt = max(0, min(OZ_S, lmax - s));
         if (p < cnt) break;
         p -= cnt;
         ++s;
@@ -706,7 +707,7 @@ __global__ __launch_bounds__(NTH, 1) void k_ozaki_q(const __nv_bfloat16* YS, int
                                                     int64_t kps, int64_t Np, const double* mu,
                                                     const double* kappa_p, const double* R64, const float* Y,
                                                     float* Rr32, double* qpart, int64_t ldm, int64_t m,
-                                                    int64_t n_valid)
+                                                    int64_t n_valid, int lmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double rs[2][4][MB];
@@ -728,30 +729,29 @@ __global__ __launch_bounds__(NTH, 1) void k_ozaki_q(const __nv_bfloat16* YS, int
             for (int e = 0; e < 4; ++e) acc[a][c][e] = hi[a][c][e] = lo[a][c][e] = 0.f;
 
     int np = 0;
-    for (int s = 1; s <= OZ_S; ++s) np += max(0, min(OZ_S, OZ_LMAX - s));
+    for (int s = 1; s <= OZ_S; ++s) np += max(0, min(OZ_S, lmax - s));
     const int kst = (int)(Np / BG_KS);
     const int64_t total = (int64_t)np * kst;
     const int stage_elems = 2 * BG_PLANE;
     auto issue = [&](int64_t gs) {
         if (gs < total) {
             int p = (int)(gs / kst), k = (int)(gs % kst), ps_, pu_;
-            oz_pair(p, ps_, pu_);
+            oz_pair(p, lmax, ps_, pu_);
             const __nv_bfloat16* A = YS + (ps_ - 1) * yps + m0 * Np;
             const __nv_bfloat16* B = KS + (pu_ - 1) * kps + n0 * Np;
-            oz_stage_load(A, B, Np, (int64_t)k * BG_KS, smem + (gs % 3) * stage_elems);
+            oz_stage_load(A, B, Np, (int64_t)k * BG_KS, smem + (gs % OZ_STAGES) * stage_elems);
         }
         cp_async_commit();
     };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wm = warp >> 2, wn = warp & 3;
     const int lq = lane >> 3, lr = lane & 7;
-    issue(0);
-    issue(1);
+    for (int q = 0; q < OZ_STAGES - 1; ++q) issue(q);
     for (int64_t gs = 0; gs < total; ++gs) {
-        asm volatile("cp.async.wait_group 1;\n" ::);
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(OZ_STAGES - 2));
         __syncthreads();
-        issue(gs + 2);
-        const __nv_bfloat16* As = smem + (gs % 3) * stage_elems;
+        issue(gs + OZ_STAGES - 1);
+        const __nv_bfloat16* As = smem + (gs % OZ_STAGES) * stage_elems;
         const __nv_bfloat16* Bs = As + BG_PLANE;
 #pragma unroll
         for (int kk = 0; kk < BG_KS; kk += 16) {
@@ -777,7 +777,7 @@ __global__ __launch_bounds__(NTH, 1) void k_ozaki_q(const __nv_bfloat16* YS, int
         const int k = (int)(gs % kst);
         if ((k + 1) % (OZ_CHUNK / BG_KS) == 0 || k + 1 == kst) {
             int ps_, pu_;
-            oz_pair((int)(gs / kst), ps_, pu_);
+            oz_pair((int)(gs / kst), lmax, ps_, pu_);
             const float scale = ldexpf(1.f, -7 * (ps_ + pu_));
 #pragma unroll
             for (int a = 0; a < 4; ++a)
@@ -1049,7 +1049,7 @@ void var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
     GPK_LAUNCH(h, GP_PH_REFINE, k_ozaki_q, (unsigned)(nbn * (ldm / MB)), NTH, OZ_SMEM_BYTES,
                (const __nv_bfloat16*)h->YS, ldm * Np, (const __nv_bfloat16*)h->KS, Np * Np, Np,
                (const double*)h->mu, (const double*)h->kappa, (const double*)h->R64, (const float*)h->R32,
-               h->Rr32, h->qpart, ldm, m, h->n);
+               h->Rr32, h->qpart, ldm, m, h->n, h->oz_lmax);
     forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_REFINE);
     GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, nbn,
                (const double*)h->vpart2, Np / MB, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
