@@ -190,6 +190,30 @@ typedef struct {
 } gp_info_t;
 gp_status gp_info(gp_t h, gp_info_t* out);
 
+/* Allocation-free predictive mean (no counterpart in the paper).  For callers
+ * that cannot allocate device memory - code running during CUDA graph capture,
+ * servers whose device memory belongs to a pool fixed at start-up, plug-ins of
+ * hosts that forbid allocation - this computes mean = K_{Z*,Z} alpha (Eq. 3)
+ * from trained weights (alpha from gp_get_alpha) without a handle and without
+ * any cudaMalloc, cudaFree or allocating library call.
+ *   X (n x d), alpha (n), Xs (m x d) and mean (m): caller-owned DEVICE memory,
+ *   row-major float64; lengthscale l and vertical nu as in Eq. 2; cuda_stream
+ *   as in gp_options (NULL: legacy default stream).  Stream-ordered, no sync.
+ * Limits: 1 <= m <= GP_NOALLOC_MAX_TEST, 1 <= d <= 1024; larger or invalid
+ * arguments, or host pointers, return GP_ERR_ARG before any work.
+ * Scratch: a fixed GP_NOALLOC_CHUNKS x GP_NOALLOC_MAX_TEST array of doubles
+ * (16 MiB) in the library's device data, held by every GPU that loads the
+ * library until the process exits and shared by all calls on that GPU.  The
+ * first call on a device looks its address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Calls whose
+ * work overlaps on the GPU (different streams, no ordering) race on the scratch
+ * and must not be issued. */
+#define GP_NOALLOC_MAX_TEST 32768
+#define GP_NOALLOC_CHUNKS 64
+gp_status gp_predict_mean_noalloc(const double* X, const double* alpha, int64_t n, int64_t d,
+                                  const double* Xs, int64_t m, double lengthscale, double vertical,
+                                  double* mean, void* cuda_stream);
+
 int64_t gp_last_error_info(gp_t h);
 const char* gp_status_str(gp_status s);
 void gp_destroy(gp_t h);

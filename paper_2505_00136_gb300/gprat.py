@@ -80,6 +80,8 @@ _SIGS = {
     "gp_profile": (ctypes.c_int, [_H, ctypes.c_int]),
     "gp_profile_read": (ctypes.c_int, [_H, _vp, _vp, ctypes.c_int]),
     "gp_launch_count": (_i64, [_H]),
+    "gp_predict_mean_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, ctypes.c_double,
+                                               ctypes.c_double, _vp, _vp]),
     "gp_last_error_info": (_i64, [_H]),
     "gp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "gp_destroy": (None, [_H]),
