@@ -53,7 +53,7 @@ typedef enum { GP_FP64 = 0, GP_MIXED = 1 } gp_precision;
 
 typedef enum {
     GP_SCHED_STREAM = 0,     /* one launch per tile step, stream ordered */
-    GP_SCHED_PERSISTENT = 1  /* persistent kernel walking the tile DAG */
+    GP_SCHED_PERSISTENT = 1  /* one persistent launch walking the tile DAG (GP_FP64 only) */
 } gp_scheduler;
 
 /* Eq. 2 hyperparameters.  trainable[p] = 0 freezes parameter p in gp_optimize
@@ -77,11 +77,13 @@ typedef struct {
     gp_scheduler scheduler; /* how the Cholesky tile DAG is executed */
     int var_correction;     /* GP_MIXED: 1 corrects the predictive variances to FP64 level
                                (see gp_predict_var), 0 returns the mixed-factor variances */
+    int dag_timeout_ms;     /* GP_SCHED_PERSISTENT: bound on any single dependency wait of
+                               the persistent kernel; expiry ends the call with GP_ERR_TIMEOUT */
 } gp_options;
 
 /* Fills defaults: n_tiles 16, FP64, latent variance, refine_tol 1e-14,
  * refine_max_iter 20, Adam (0.9, 0.999, 1e-8), default stream, stream
- * scheduler, variance correction on. */
+ * scheduler, variance correction on, DAG wait bound 10000 ms. */
 void gp_default_options(gp_options* opt);
 
 /* Creates a GP over n training points X (n x d) with targets y (n).  Copies
@@ -180,6 +182,13 @@ int64_t gp_launch_count(gp_t h);
 /* Copies alpha = K^{-1} y (n entries, host or device), the weights of the
  * predictive mean (Eq. 3: mean = K_{Z*,Z} alpha).  Factors first if needed. */
 gp_status gp_get_alpha(gp_t h, double* alpha_out);
+
+/* Testing aid for the persistent scheduler's bounded waits: until called
+ * again with i < 0, every persistent factorisation treats the update counter
+ * of tile (i, j) as never complete, so the waits on it expire after
+ * dag_timeout_ms and the call returns GP_ERR_TIMEOUT with the device still
+ * usable.  GP_ERR_ARG unless 0 <= j <= i < n_tiles (or i < 0). */
+gp_status gp_dag_stall_tile(gp_t h, int64_t i, int64_t j);
 
 /* Tile geometry and last-call diagnostics. */
 typedef struct {

@@ -196,12 +196,52 @@ gp_status ensure_cov_space(gp_t h, int64_t m)
     return s;
 }
 
+// Task queue of the persistent factorisation: POTRF(0), TRSM(., 0), then per
+// step k the updates of column k+1, POTRF(k+1), TRSM(., k+1) (lookahead) and
+// the rest of step k's updates.  Every task follows all tasks it depends on.
+gp_status build_dag(gp_t h)
+{
+    const int64_t T = h->T, nt = T * (T + 1) / 2;
+    int64_t cap = T + T * (T - 1) / 2;
+    for (int64_t k = 0; k < T; ++k) cap += (T - k - 1) * (T - k) / 2;
+    int* host = (int*)malloc((size_t)cap * 4 * sizeof(int));
+    if (!host) return GP_ERR_OOM;
+    int64_t n = 0;
+    auto push = [&](int type, int64_t i, int64_t j, int64_t k) {
+        host[4 * n + 0] = type;
+        host[4 * n + 1] = (int)i;
+        host[4 * n + 2] = (int)j;
+        host[4 * n + 3] = (int)k;
+        ++n;
+    };
+    push(0, 0, 0, 0);
+    for (int64_t i = 1; i < T; ++i) push(1, i, 0, 0);
+    for (int64_t k = 0; k + 1 < T; ++k) {
+        for (int64_t i = k + 1; i < T; ++i) push(2, i, k + 1, k);
+        push(0, k + 1, k + 1, k + 1);
+        for (int64_t i = k + 2; i < T; ++i) push(1, i, k + 1, k + 1);
+        for (int64_t j = k + 2; j < T; ++j)
+            for (int64_t i = j; i < T; ++i) push(2, i, j, k);
+    }
+    gp_status s = dev_alloc(h, &h->dag_tasks, 4 * n);
+    if (s == GP_OK) s = dev_alloc(h, &h->dag_ctl, 2);
+    if (s == GP_OK) s = dev_alloc(h, &h->dag_upd, nt);
+    if (s == GP_OK) s = dev_alloc(h, &h->dag_fin, nt);
+    if (s == GP_OK)
+        s = cuda_status(h, cudaMemcpy(h->dag_tasks, host, (size_t)n * 4 * sizeof(int), cudaMemcpyHostToDevice));
+    if (s == GP_OK) s = cuda_status(h, cudaMemset(h->dag_ctl, 0, 2 * sizeof(int)));
+    free(host);
+    h->dag_ntasks = n;
+    return s;
+}
+
 // Assemble, factor and solve for beta and alpha; NLML into scal[0].  No sync,
 // no reset of the failure flag (a failure stays visible to later kernels).
-void launch_factor_body(gp_t h)
+void launch_factor_body(gp_t h, bool reset_err)
 {
     gpk::assemble_train(h);
-    gpk::factor_fp64(h);
+    if (h->opt.scheduler == GP_SCHED_PERSISTENT) gpk::factor_dag(h, reset_err);
+    else gpk::factor_fp64(h);
     gpk::solve_lower(h, h->y, h->beta);
     gpk::solve_upper(h, h->beta, h->alpha);
     gpk::nlml_reduce(h);
@@ -210,15 +250,24 @@ void launch_factor_body(gp_t h)
 void launch_factor(gp_t h)
 {
     gpk::set_info_none(h);
-    launch_factor_body(h);
+    launch_factor_body(h, true);
 }
 
 gp_status read_info(gp_t h)
 {
     unsigned long long info = 0;
+    int ctl[2] = {0, 0};
     gp_status s = cuda_status(h, cudaMemcpyAsync(&info, h->info, sizeof(info), cudaMemcpyDeviceToHost, h->st));
     if (s != GP_OK) return s;
+    if (h->dag_ctl && (s = cuda_status(h, cudaMemcpyAsync(ctl, h->dag_ctl, sizeof(ctl), cudaMemcpyDeviceToHost,
+                                                          h->st))) != GP_OK)
+        return s;
     if ((s = sync(h)) != GP_OK) return s;
+    if (ctl[1] == 1) {
+        h->last_info = 0;
+        h->factored = false;
+        return GP_ERR_TIMEOUT;
+    }
     if (info != ~0ull) {
         h->last_info = (int64_t)info;
         h->factored = false;
@@ -392,6 +441,7 @@ void gp_default_options(gp_options* opt)
     opt->cuda_stream = nullptr;
     opt->scheduler = GP_SCHED_STREAM;
     opt->var_correction = 1;
+    opt->dag_timeout_ms = 10000;
 }
 
 const char* gp_status_str(gp_status s)
@@ -419,7 +469,8 @@ void gp_destroy(gp_t h)
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
                     h->PA, h->D64, h->X64, h->r32, h->t32, h->w32, h->res, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32, h->YP,
-                    h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2};
+                    h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
+                    h->dag_upd, h->dag_fin};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int64_t i = 0; i < h->ev_cap; ++i) cudaEventDestroy(h->ev_pool[i]);
@@ -438,8 +489,10 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     else gp_default_options(&opt);
     if (!X || !y || n < 1 || d < 1 || d > 1024 || !hyper_ok(hyper) || opt.n_tiles < 1 ||
         (opt.prec != GP_FP64 && opt.prec != GP_MIXED) ||
-        (opt.scheduler != GP_SCHED_STREAM && opt.scheduler != GP_SCHED_PERSISTENT))
+        (opt.scheduler != GP_SCHED_STREAM && opt.scheduler != GP_SCHED_PERSISTENT) ||
+        (opt.scheduler == GP_SCHED_PERSISTENT && opt.prec != GP_FP64) || opt.dag_timeout_ms < 0)
         return GP_ERR_ARG;
+    if (opt.dag_timeout_ms == 0) opt.dag_timeout_ms = 10000;
     gp_t h = new (std::nothrow) gp_handle();
     if (!h) return GP_ERR_OOM;
     memset((void*)h, 0, sizeof(*h));
@@ -449,6 +502,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     h->n = n;
     h->d = d;
     h->oz_lmax = 7;
+    h->dag_stall = -1;
     if (const char* e = getenv("GPRAT_OZAKI_LMAX")) {   // accuracy/speed study knob: 6 or 7
         int v = atoi(e);
         if (v >= 4 && v <= 2 * gpk::GP_OZ_SLICES) h->oz_lmax = v;
@@ -479,6 +533,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     TRY(dev_alloc(h, &h->logdet_part, h->T));
     TRY(dev_alloc(h, &h->info, 1));
     TRY(dev_alloc(h, &h->scal, 16));
+    if (opt.scheduler == GP_SCHED_PERSISTENT) TRY(build_dag(h));
     if (opt.prec == GP_MIXED) {
         const int64_t bb = h->b * h->b;
         TRY(dev_alloc(h, &h->A32, tiles));
@@ -631,7 +686,7 @@ gp_status gp_optimize(gp_t h, int steps, double lr, double* nlml_hist)
                 h->ks_valid = false;
                 if ((s = factor_mixed_refined(h)) != GP_OK) break;
             } else {
-                launch_factor_body(h);
+                launch_factor_body(h, it == 0);
             }
         }
         if (mixed) gpk::inverse_mixed(h);
@@ -748,6 +803,14 @@ gp_status gp_get_alpha(gp_t h, double* alpha_out)
     if (s != GP_OK) return s;
     if ((s = copy_any(h, alpha_out, h->alpha, h->n)) != GP_OK) return s;
     return finish_outputs(h, !is_device_ptr(alpha_out));
+}
+
+gp_status gp_dag_stall_tile(gp_t h, int64_t i, int64_t j)
+{
+    if (!h || (i >= 0 && (j < 0 || j > i || i >= h->T))) return GP_ERR_ARG;
+    h->dag_stall = i < 0 ? -1 : tri_index(i, j);
+    h->factored = false;
+    return GP_OK;
 }
 
 gp_status gp_info(gp_t h, gp_info_t* out)

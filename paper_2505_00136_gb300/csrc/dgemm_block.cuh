@@ -50,7 +50,7 @@ __device__ __forceinline__ void dg_load(const DView& v, int64_t k0, double (&reg
         int r, kk;
         if (v.sk == 1) { r = idx >> 4; kk = idx & 15; }   // contiguous along k
         else           { kk = idx >> 6; r = idx & 63; }   // contiguous along rows
-        reg[q] = (r < v.rows) ? v.p[(int64_t)r * v.sr + (k0 + kk) * v.sk] : 0.0;
+        reg[q] = (r < v.rows) ? __ldcg(v.p + (int64_t)r * v.sr + (k0 + kk) * v.sk) : 0.0;
     }
 }
 

@@ -102,6 +102,14 @@ struct gp_handle {
     float* U32;               // T(T+1)/2 tiles: TRTRI accumulators (gradient)
     float* Kinv32;            // T(T+1)/2 tiles: K^{-1} lower (gradient)
 
+    // Persistent tile-DAG scheduler (GP_SCHED_PERSISTENT).
+    int* dag_tasks;           // int4 (type, i, j, k) per task, topological order
+    int64_t dag_ntasks;
+    int* dag_ctl;             // [0] ticket, [1] abort code (1 timeout, 2 pivot)
+    int* dag_upd;             // T(T+1)/2 update counters
+    int* dag_fin;             // T(T+1)/2 final flags
+    int64_t dag_stall;        // test aid: tile whose counter is poisoned (-1: none)
+
     int64_t bytes;            // device bytes held
     int64_t last_info;
     int refine_iters;
@@ -150,6 +158,7 @@ void set_info_none(gp_t h);
 // FP64 POTRF + inverse of one b x b diagonal tile A (in place) into X; adds
 // sum log L_ii to *logdet_slot; a failing pivot records row0 + its row.
 void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot);
+void factor_dag(gp_t h, bool reset_err);                       // persistent tile-DAG factor (FP64)
 
 // kernels_mixed.cu
 void factor_mixed(gp_t h);                                     // mixed factor of h->A32

@@ -92,16 +92,19 @@ __global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, float* o
 // panels), then the blocked inverse of its factor into Linv[k].  Adds
 // sum log L_ii of the tile to logdet_part[k]; on a non-positive pivot records
 // the global row in *info and stops.
-__global__ __launch_bounds__(NT) void k_potrf_diag(double* A, double* Xk, int64_t b, int64_t row0,
-                                                   double* logdet_slot, unsigned long long* info)
+// Operands that other CTAs of a persistent launch may have written are read
+// through L2 (ld.global.cg), never from a possibly stale L1 line.
+__device__ __forceinline__ double ldl2(const double* p) { return __ldcg(p); }
+
+// Returns false (after recording the row) on a non-positive pivot.
+__device__ bool potrf_tile(double* A, double* Xk, int64_t b, int64_t row0, double* logdet_slot,
+                           unsigned long long* info, double* smem)
 {
-    extern __shared__ double smem[];
     double* gsm = smem;                              // dgemm staging
     double* S = smem + DG_SMEM_DOUBLES;              // 64 x 65 factor block
     double* Iv = S + 64 * 65;                        // 64 x 65 inverse block
     __shared__ double logacc, rcp;
     __shared__ int fail;
-    if (failed(info)) return;
     const int tid = threadIdx.x;
     const int P = (int)(b / TB);
     if (tid == 0) { logacc = 0.0; fail = 0; }
@@ -113,12 +116,15 @@ __global__ __launch_bounds__(NT) void k_potrf_diag(double* A, double* Xk, int64_
             dacc_zero(acc);
             DView va{A + (int64_t)p * TB * b, b, 1, TB};
             dgemm_acc(acc, va, va, 0, (int64_t)p * TB, gsm);
-            dacc_for_each(acc, [&](int r, int c, double v) { App[(int64_t)r * b + c] -= v; });
+            dacc_for_each(acc, [&](int r, int c, double v) {
+                double* q = App + (int64_t)r * b + c;
+                *q = ldl2(q) - v;
+            });
         }
         __syncthreads();
         for (int e = tid; e < 64 * 64; e += NT) {
             int r = e >> 6, c = e & 63;
-            S[r * 65 + c] = (c <= r) ? App[(int64_t)r * b + c] : 0.0;
+            S[r * 65 + c] = (c <= r) ? ldl2(App + (int64_t)r * b + c) : 0.0;
             Iv[r * 65 + c] = 0.0;
         }
         __syncthreads();
@@ -136,7 +142,7 @@ __global__ __launch_bounds__(NT) void k_potrf_diag(double* A, double* Xk, int64_
                 }
             }
             __syncthreads();
-            if (fail) return;
+            if (fail) return false;
             const double djj_inv = rcp;
             for (int r = j + 1 + tid; r < 64; r += NT) S[r * 65 + j] *= djj_inv;
             __syncthreads();
@@ -182,7 +188,10 @@ __global__ __launch_bounds__(NT) void k_potrf_diag(double* A, double* Xk, int64_
                 DView va{A + (int64_t)r * TB * b, b, 1, TB};
                 DView vb{A + (int64_t)p * TB * b, b, 1, TB};
                 dgemm_acc(acc, va, vb, 0, (int64_t)p * TB, gsm);
-                dacc_for_each(acc, [&](int rr, int c, double v) { Arp[(int64_t)rr * b + c] -= v; });
+                dacc_for_each(acc, [&](int rr, int c, double v) {
+                    double* q = Arp + (int64_t)rr * b + c;
+                    *q = ldl2(q) - v;
+                });
             }
             DAcc acc;
             dacc_zero(acc);
@@ -217,20 +226,23 @@ __global__ __launch_bounds__(NT) void k_potrf_diag(double* A, double* Xk, int64_
     }
     __syncthreads();
     if (tid == 0) *logdet_slot = logacc;
+    return true;
+}
+
+__global__ __launch_bounds__(NT) void k_potrf_diag(double* A, double* Xk, int64_t b, int64_t row0,
+                                                   double* logdet_slot, unsigned long long* info)
+{
+    extern __shared__ double smem[];
+    if (failed(info)) return;
+    potrf_tile(A, Xk, b, row0, logdet_slot, info, smem);
 }
 
 // Panel TRSM of step k: L_ik = A_ik L_kk^{-T} = A_ik Linv_kk^T for i > k.
 // One CTA per (64-row block, tile); column blocks right to left keep it in place.
-__global__ __launch_bounds__(NT) void k_panel(double* Lt, const double* Linv, int64_t b, int64_t k,
-                                              const unsigned long long* info)
+__device__ void panel_rows(double* tile, const double* Xk, int64_t b, int rb, double* smem)
 {
-    extern __shared__ double smem[];
-    if (failed(info)) return;
     const int P = (int)(b / TB);
-    const int rb = blockIdx.x;
-    const int64_t i = k + 1 + blockIdx.y;
-    double* Arow = Lt + tri_index(i, k) * b * b + (int64_t)rb * TB * b;
-    const double* Xk = Linv + k * b * b;
+    double* Arow = tile + (int64_t)rb * TB * b;
     for (int cb = P - 1; cb >= 0; --cb) {
         DAcc acc;
         dacc_zero(acc);
@@ -242,8 +254,32 @@ __global__ __launch_bounds__(NT) void k_panel(double* Lt, const double* Linv, in
     }
 }
 
+__global__ __launch_bounds__(NT) void k_panel(double* Lt, const double* Linv, int64_t b, int64_t k,
+                                              const unsigned long long* info)
+{
+    extern __shared__ double smem[];
+    if (failed(info)) return;
+    const int64_t i = k + 1 + blockIdx.y;
+    panel_rows(Lt + tri_index(i, k) * b * b, Linv + k * b * b, b, blockIdx.x, smem);
+}
+
 // Trailing update of step k: A_ij -= L_ik L_jk^T for k < j <= i (SYRK on
 // diagonal tiles, GEMM elsewhere).  grid.x: trailing lower tile, grid.y: 64-block.
+__device__ void update_block(double* Lt, int64_t b, int64_t i, int64_t j, int64_t k, int rb, int cb,
+                             double* smem)
+{
+    DAcc acc;
+    dacc_zero(acc);
+    DView va{Lt + tri_index(i, k) * b * b + (int64_t)rb * TB * b, b, 1, TB};
+    DView vb{Lt + tri_index(j, k) * b * b + (int64_t)cb * TB * b, b, 1, TB};
+    dgemm_acc(acc, va, vb, 0, b, smem);
+    double* dst = Lt + tri_index(i, j) * b * b + (int64_t)rb * TB * b + cb * TB;
+    dacc_for_each(acc, [&](int r, int c, double v) {
+        double* q = dst + (int64_t)r * b + c;
+        *q = ldl2(q) - v;
+    });
+}
+
 __global__ __launch_bounds__(NT) void k_update(double* Lt, int64_t b, int64_t k,
                                                const unsigned long long* info)
 {
@@ -255,14 +291,92 @@ __global__ __launch_bounds__(NT) void k_update(double* Lt, int64_t b, int64_t k,
     const int64_t i = k + 1 + ii, j = k + 1 + jj;
     const int rb = blockIdx.y / P, cb = blockIdx.y % P;
     if (i == j && cb > rb) return;
-    DAcc acc;
-    dacc_zero(acc);
-    DView va{Lt + tri_index(i, k) * b * b + (int64_t)rb * TB * b, b, 1, TB};
-    DView vb{Lt + tri_index(j, k) * b * b + (int64_t)cb * TB * b, b, 1, TB};
-    dgemm_acc(acc, va, vb, 0, b, smem);
-    double* dst = Lt + tri_index(i, j) * b * b + (int64_t)rb * TB * b + cb * TB;
-    dacc_for_each(acc, [&](int r, int c, double v) { dst[(int64_t)r * b + c] -= v; });
+    update_block(Lt, b, i, j, k, rb, cb, smem);
 }
+
+// ---------------------------------------------------------------- persistent tile-DAG Cholesky
+// One launch walks the whole task graph of Fig. 1: POTRF(k), TRSM(i, k) and
+// UPDATE(i, j, k) tasks, queued on the host in a topological order with
+// one-step lookahead.  CTAs claim tasks with an atomic ticket; a task waits
+// only on tasks with smaller tickets, which are already held by running CTAs,
+// so the walk cannot deadlock.  Dependencies are per-tile counters:
+//   upd[tri(i, j)] = number of trailing updates applied to tile (i, j),
+//   fin[tri(i, j)] = 1 once tile (i, j) of L is final (POTRF or TRSM done).
+// Every wait is bounded by a clock-cycle budget; on expiry the CTA sets
+// ctl[1] = 1 (timeout), a failed pivot sets ctl[1] = 2, and all CTAs leave.
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool dag_wait(const int* p, int need, int* ctl, long long budget)
+{
+    if (ld_acquire(p) >= need) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        __nanosleep(256);
+        if (ld_acquire(p) >= need) return true;
+        if (ld_acquire(ctl + 1) != 0) return false;
+        if (clock64() - t0 > budget) {
+            atomicCAS(ctl + 1, 0, 1);
+            return false;
+        }
+    }
+}
+
+__global__ __launch_bounds__(NT) void k_chol_dag(double* Lt, double* Linv, int64_t b, const int4* tasks,
+                                                 int64_t ntasks, int* ctl, int* upd, int* fin,
+                                                 double* logdet_part, unsigned long long* info, long long budget)
+{
+    extern __shared__ double smem[];
+    __shared__ int s_task, s_go;
+    const int P = (int)(b / TB);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(ctl, 1);
+            int go = (t < ntasks) && ld_acquire(ctl + 1) == 0;
+            if (go) {
+                const int4 tk = tasks[t];
+                if (tk.x == 0)
+                    go = dag_wait(upd + tri_index(tk.w, tk.w), tk.w, ctl, budget);
+                else if (tk.x == 1)
+                    go = dag_wait(fin + tri_index(tk.w, tk.w), 1, ctl, budget) &&
+                         dag_wait(upd + tri_index(tk.y, tk.w), tk.w, ctl, budget);
+                else
+                    go = dag_wait(fin + tri_index(tk.y, tk.w), 1, ctl, budget) &&
+                         dag_wait(fin + tri_index(tk.z, tk.w), 1, ctl, budget) &&
+                         dag_wait(upd + tri_index(tk.y, tk.z), tk.w, ctl, budget);
+            }
+            s_task = t;
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const int4 tk = tasks[s_task];   // (type, i, j, k)
+        const int64_t i = tk.y, j = tk.z, k = tk.w;
+        bool ok = true;
+        if (tk.x == 0) {
+            ok = potrf_tile(Lt + tri_index(k, k) * b * b, Linv + k * b * b, b, k * b, logdet_part + k, info, smem);
+        } else if (tk.x == 1) {
+            for (int rb = 0; rb < P; ++rb) panel_rows(Lt + tri_index(i, k) * b * b, Linv + k * b * b, b, rb, smem);
+        } else {
+            for (int rb = 0; rb < P; ++rb)
+                for (int cb = 0; cb <= (i == j ? rb : P - 1); ++cb) update_block(Lt, b, i, j, k, rb, cb, smem);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (!ok) atomicExch(ctl + 1, 2);
+            else if (tk.x == 0) atomicExch(fin + tri_index(k, k), 1);
+            else if (tk.x == 1) atomicExch(fin + tri_index(i, k), 1);
+            else atomicAdd(upd + tri_index(i, j), 1);
+        }
+    }
+}
+
+__global__ void k_dag_stall(int* upd, int64_t idx) { upd[idx] = -(1 << 30); }
 
 // ---------------------------------------------------------------- single right-hand side solves
 // out_j = Linv_jj w_j (lower: rows of the tile inverse) or Linv_jj^T w_j (upper).
@@ -716,6 +830,34 @@ void assemble_test_prior(gp_t h, int64_t m, double* out)
 }
 
 void set_info_none(gp_t h) { GPK_LAUNCH(h, GP_PH_OTHER, k_set_u64, 1, 1, 0, h->info, ~0ull); }
+
+// Persistent tile-DAG factorisation (GP_SCHED_PERSISTENT).  reset_err = false
+// keeps an earlier abort code, so a failure inside an optimisation loop stays
+// visible until the host reads it.
+void factor_dag(gp_t h, bool reset_err)
+{
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaFuncSetAttribute(k_chol_dag, cudaFuncAttributeMaxDynamicSharedMemorySize, POTRF_SMEM);
+        attr_dev = dev;
+    }
+    ensure_attrs();
+    const int64_t nt = h->T * (h->T + 1) / 2;
+    cudaMemsetAsync(h->dag_ctl, 0, sizeof(int) * (reset_err ? 2 : 1), h->st);
+    cudaMemsetAsync(h->dag_upd, 0, sizeof(int) * nt, h->st);
+    cudaMemsetAsync(h->dag_fin, 0, sizeof(int) * nt, h->st);
+    if (h->dag_stall >= 0) GPK_LAUNCH(h, GP_PH_OTHER, k_dag_stall, 1, 1, 0, h->dag_upd, h->dag_stall);
+    int per_sm = 1, sms = 1, khz = 1000000;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_dag, NT, POTRF_SMEM);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    const long long budget = (long long)h->opt.dag_timeout_ms * (long long)khz;
+    const int grid = (per_sm > 0 ? per_sm : 1) * sms;
+    GPK_LAUNCH(h, GP_PH_UPDATE, k_chol_dag, grid, NT, POTRF_SMEM, h->L, h->Linv, h->b, (const int4*)h->dag_tasks,
+               h->dag_ntasks, h->dag_ctl, h->dag_upd, h->dag_fin, h->logdet_part, h->info, budget);
+}
 
 void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot)
 {

@@ -40,7 +40,8 @@ class gp_options(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("refine_max_iter", ctypes.c_int),
                 ("adam_beta1", ctypes.c_double), ("adam_beta2", ctypes.c_double),
                 ("adam_eps", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("scheduler", ctypes.c_int), ("var_correction", ctypes.c_int)]
+                ("scheduler", ctypes.c_int), ("var_correction", ctypes.c_int),
+                ("dag_timeout_ms", ctypes.c_int)]
 
 
 class gp_state(ctypes.Structure):
@@ -76,6 +77,7 @@ _SIGS = {
     "gp_set_state": (ctypes.c_int, [_H, ctypes.POINTER(gp_state)]),
     "gp_get_factor": (ctypes.c_int, [_H, _vp]),
     "gp_get_alpha": (ctypes.c_int, [_H, _vp]),
+    "gp_dag_stall_tile": (ctypes.c_int, [_H, _i64, _i64]),
     "gp_info": (ctypes.c_int, [_H, ctypes.POINTER(gp_info_t)]),
     "gp_profile": (ctypes.c_int, [_H, ctypes.c_int]),
     "gp_profile_read": (ctypes.c_int, [_H, _vp, _vp, ctypes.c_int]),
@@ -140,7 +142,7 @@ class GP:
 
     def __init__(self, X, y, hyper=(1.0, 1.0, 0.1), trainable=(1, 1, 1), n_tiles=16,
                  precision="fp64", noisy_test_var=False, stream=None, scheduler="stream",
-                 refine_tol=None, refine_max_iter=None, var_correction=True):
+                 refine_tol=None, refine_max_iter=None, var_correction=True, dag_timeout_ms=None):
         if not _is_torch(X):
             X = np.ascontiguousarray(X, dtype=np.float64)
             y = np.ascontiguousarray(y, dtype=np.float64)
@@ -156,6 +158,8 @@ class GP:
         if refine_max_iter is not None:
             opt.refine_max_iter = refine_max_iter
         opt.var_correction = int(bool(var_correction))
+        if dag_timeout_ms is not None:
+            opt.dag_timeout_ms = int(dag_timeout_ms)
         if stream is None and self._torch_dev is not None:
             import torch
             stream = torch.cuda.current_stream(self._torch_dev).cuda_stream
@@ -294,6 +298,10 @@ class GP:
         a = self._out(self.n)
         _check(_lib.gp_get_alpha(self.h, _ptr(a)), self.h, "gp_get_alpha")
         return a
+
+    def dag_stall_tile(self, i, j=0):
+        """Testing aid: poison tile (i, j)'s update counter (i < 0 clears)."""
+        _check(_lib.gp_dag_stall_tile(self.h, int(i), int(j)), self.h, "gp_dag_stall_tile")
 
     def info(self):
         inf = gp_info_t()
