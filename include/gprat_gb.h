@@ -183,6 +183,46 @@ int64_t gp_launch_count(gp_t h);
  * predictive mean (Eq. 3: mean = K_{Z*,Z} alpha).  Factors first if needed. */
 gp_status gp_get_alpha(gp_t h, double* alpha_out);
 
+/* ------------------------------------------------------------------------
+ * Learned hyperparameter initialiser (no counterpart in the paper).  A
+ * 64-dimensional summary of a data set feeds a 64 -> 256 -> 256 -> 3 ReLU
+ * MLP whose outputs are initial (log l, log nu, log sigma^2).  All buffers
+ * below are DEVICE memory; calls are stream-ordered on `stream`.
+ *
+ * Model blob (GP_MLP_MODEL_FLOATS floats): W1[256][64] b1[256] W2[256][256]
+ * b2[256] W3[3][256] b3[3] (the GP_MLP_NPARAM trained values), then the
+ * feature mean[64] and standard deviation[64] that standardise summaries. */
+#define GP_MLP_NPARAM 83203
+#define GP_MLP_MODEL_FLOATS (GP_MLP_NPARAM + 128)
+#define GP_LEARNED_INIT_SCRATCH 72
+
+/* s (64 doubles) = summary of (X n x d, y n): the 32 largest per-regressor
+ * standard deviations (descending, zero-padded), the autocorrelation of y at
+ * lags 1..16, and the means of cos(omega_q y) and sin(omega_q y) for the 8
+ * frequencies omega (doubles).  Requires n >= 2, 1 <= d <= 1024. */
+gp_status gp_summary(const double* X, const double* y, int64_t n, int64_t d, const double* omega,
+                     double* s, void* stream);
+/* Feature mean and standard deviation over B summaries (B x 64 doubles) into
+ * the model blob's standardisation slots. */
+gp_status gp_mlp_feature_stats(const double* S, int64_t B, float* model, void* stream);
+/* Floats of workspace gp_mlp_loss_grad needs for a batch of B. */
+int64_t gp_mlp_workspace_floats(int64_t B);
+/* out (B x 3 floats) = network outputs for B summaries S (B x 64 doubles). */
+gp_status gp_mlp_forward(const float* model, const double* S, int64_t B, float* out, void* stream);
+/* Mean-squared error 1/(3B) sum (out - target)^2 into *loss (device float,
+ * may be NULL) and its gradient in the GP_MLP_NPARAM weights into gW. */
+gp_status gp_mlp_loss_grad(const float* model, const double* S, const float* target, int64_t B,
+                           float* gW, float* loss, float* workspace, void* stream);
+/* One Adam step (t >= 1) on the model's GP_MLP_NPARAM weights; m and v are
+ * GP_MLP_NPARAM-float moment buffers owned by the caller. */
+gp_status gp_mlp_adam(float* model, const float* gW, float* m, float* v, int64_t t, double lr,
+                      double beta1, double beta2, double eps, void* stream);
+/* Initial hyperparameters for a data set: summary -> network -> exp, written
+ * to *out (host) on their natural scale; scratch holds GP_LEARNED_INIT_SCRATCH
+ * doubles.  Synchronises.  GP_ERR_STATE if the network output is not finite. */
+gp_status gp_learned_init(const double* X, const double* y, int64_t n, int64_t d, const float* model,
+                          const double* omega, double* scratch, gp_hyper* out, void* stream);
+
 /* Testing aid for the persistent scheduler's bounded waits: until called
  * again with i < 0, every persistent factorisation treats the update counter
  * of tile (i, j) as never complete, so the waits on it expire after

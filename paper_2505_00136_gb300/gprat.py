@@ -26,6 +26,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 GP_OK, GP_ERR_ARG, GP_ERR_NOT_PD, GP_ERR_CUDA, GP_ERR_OOM, GP_ERR_TIMEOUT, GP_ERR_STATE = range(7)
 GP_FP64, GP_MIXED = 0, 1
 GP_SCHED_STREAM, GP_SCHED_PERSISTENT = 0, 1
+GP_MLP_NPARAM = 83203
+GP_MLP_MODEL_FLOATS = GP_MLP_NPARAM + 128
+GP_LEARNED_INIT_SCRATCH = 72
 PHASES = ["assemble", "potrf", "trsm", "update", "solve", "cross", "vsolve", "reduce", "cov",
           "trtri", "lauum", "adjoint", "adam", "refine", "other"]
 
@@ -84,6 +87,14 @@ _SIGS = {
     "gp_launch_count": (_i64, [_H]),
     "gp_predict_mean_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, ctypes.c_double,
                                                ctypes.c_double, _vp, _vp]),
+    "gp_summary": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
+    "gp_mlp_feature_stats": (ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    "gp_mlp_workspace_floats": (_i64, [_i64]),
+    "gp_mlp_forward": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "gp_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "gp_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, _vp]),
+    "gp_learned_init": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, ctypes.POINTER(gp_hyper), _vp]),
     "gp_last_error_info": (_i64, [_H]),
     "gp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "gp_destroy": (None, [_H]),
