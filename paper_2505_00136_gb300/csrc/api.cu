@@ -253,6 +253,19 @@ void launch_factor(gp_t h)
     launch_factor_body(h, true);
 }
 
+// Reads the device word that a tensor-core kernel sets when one of its
+// bounded waits runs out (synchronises the stream).
+gp_status tc_status(gp_t h)
+{
+    if (!h->tc_pending) return GP_OK;
+    int flag = 0;
+    gp_status s = cuda_status(h, gpk::tc_error_fetch(h, &flag));
+    if (s == GP_OK) s = sync(h);
+    if (s != GP_OK) return s;
+    h->tc_pending = false;
+    return flag ? GP_ERR_TIMEOUT : GP_OK;
+}
+
 gp_status read_info(gp_t h)
 {
     unsigned long long info = 0;
@@ -263,6 +276,10 @@ gp_status read_info(gp_t h)
                                                           h->st))) != GP_OK)
         return s;
     if ((s = sync(h)) != GP_OK) return s;
+    if ((s = tc_status(h)) != GP_OK) {
+        h->factored = false;
+        return s;
+    }
     if (ctl[1] == 1) {
         h->last_info = 0;
         h->factored = false;
@@ -340,7 +357,9 @@ gp_status finish_outputs(gp_t h, bool any_host)
 {
     gp_status s = check_launch(h);
     if (s != GP_OK) return s;
-    return any_host ? sync(h) : GP_OK;
+    if (!any_host) return GP_OK;
+    if ((s = sync(h)) != GP_OK) return s;
+    return tc_status(h);
 }
 
 }  // namespace
@@ -599,7 +618,8 @@ gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* 
     }
     if (var && h->opt.prec == GP_MIXED && h->opt.var_correction) {
         if ((s = ensure_kslices(h)) != GP_OK) return s;
-        gpk::var_correction_mixed(h, m, ldm);
+        if (!gpk::var_correction_mixed(h, m, ldm)) return GP_ERR_CUDA;
+        h->tc_pending = true;
     }
     if (mean) {
         if ((s = copy_any(h, mean, h->outm, m)) != GP_OK) return s;

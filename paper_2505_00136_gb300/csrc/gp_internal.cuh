@@ -98,6 +98,7 @@ struct gp_handle {
     double* vpart2;           // (Np/128) x m_cap partial sums of ||L~^{-1} r0||^2
     bool ks_valid;            // KS matches the current K
     int oz_lmax;              // digit pairs (s, u) with s + u <= oz_lmax enter the exact product
+    bool tc_pending;          // a tensor-core kernel ran since its timeout word was last read
     __nv_bfloat16* ZP;        // T(T+1)/2 tiles x 3 planes of (L^{-1})^T tiles (gradient)
     float* U32;               // T(T+1)/2 tiles: TRTRI accumulators (gradient)
     float* Kinv32;            // T(T+1)/2 tiles: K^{-1} lower (gradient)
@@ -170,7 +171,10 @@ void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var);
 void copy_factor_dense_mixed(gp_t h, double* out);
 void full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov);  // cov (prefilled prior) -= W W^T
 void inverse_mixed(gp_t h);                                    // Kinv32 = (L~ L~^T)^{-1}
-void var_correction_mixed(gp_t h, int64_t m, int64_t ldm);     // FP64-level variances into outv
+bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm);     // FP64-level variances into outv
+// kernels_tc.cu
+bool ozaki_tc(gp_t h, int64_t m, int64_t ldm);                  // C = Y K digit-pair product + fused epilogue
+cudaError_t tc_error_fetch(gp_t h, int* out);                   // read and clear the tensor-core timeout word
 constexpr int GP_OZ_SLICES = 6;                                // digit slices per operand (kernels_mixed.cu)
 }  // namespace gpk
 

@@ -611,10 +611,6 @@ __global__ __launch_bounds__(NTH) void k_mbupd(float* R32, int64_t ldr, const __
 }
 
 constexpr int OZ_S = GP_OZ_SLICES;   // digit slices per operand (7 bits each)
-constexpr int OZ_LMAX_DEFAULT = 7;  // keep digit pairs (s, u), 1-based, with s + u <= lmax
-constexpr int OZ_CHUNK = 1024; // k-terms summed exactly in FP32 before a flush
-constexpr int OZ_STAGES = 6;
-constexpr int OZ_SMEM_BYTES = OZ_STAGES * 2 * BG_PLANE * 2;   // stages x {A, B} single planes
 
 __device__ __forceinline__ double pow2_ceil(double x)   // smallest power of two >= x (x > 0)
 {
@@ -673,184 +669,6 @@ __global__ void k_kslices(const double* K64, int64_t b, int64_t Np, const GpHype
     }
 }
 
-// p-th kept digit pair (s, u), 1-based, enumerated s-major with s + u <= lmax.
-__device__ __forceinline__ void oz_pair(int p, int lmax, int& s, int& u)
-{
-    s = 1;
-    while (true) {
-        const int cnt = max(0, min(OZ_S, lmax - s));
-        if (p < cnt) break;
-        p -= cnt;
-        ++s;
-    }
-    u = p + 1;
-}
-
-__device__ __forceinline__ void oz_stage_load(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t Np,
-                                              int64_t k0, __nv_bfloat16* s)
-{
-    // A and B: 128 rows x 4 chunks each = 1024 chunks; 4 per thread
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        int idx = threadIdx.x + q * 256;
-        int which = idx >> 9, rem = idx & 511;
-        int r = rem >> 2, ch = rem & 3;
-        const __nv_bfloat16* src = (which ? B : A) + (int64_t)r * Np + k0 + ch * 8;
-        cp_async16(s + which * BG_PLANE + r * BG_LD + ch * 8, src, true);
-    }
-}
-
-// C = Y K for a 128 x 128 block (rows: test points, cols: training points) from
-// the digit pairs, then the fused epilogue: r0 = Kc - C (FP32 into Rr32) and
-// per-row partial sums of Kc Y and Y r0 into qpart[0|1][col block][row].
-__global__ __launch_bounds__(NTH, 1) void k_ozaki_q(const __nv_bfloat16* YS, int64_t yps, const __nv_bfloat16* KS,
-                                                    int64_t kps, int64_t Np, const double* mu,
-                                                    const double* kappa_p, const double* R64, const float* Y,
-                                                    float* Rr32, double* qpart, int64_t ldm, int64_t m,
-                                                    int64_t n_valid, int lmax)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double rs[2][4][MB];
-    __nv_bfloat16* smem = (__nv_bfloat16*)smem_raw;
-    // grouped raster: 8 row blocks share each column block in flight
-    const int64_t nbn = Np / MB, nbm = ldm / MB;
-    const int64_t g = blockIdx.x, G = 8;
-    const int64_t grp = g / (G * nbn), first = grp * G;
-    const int64_t gsz = (nbm - first) < G ? (nbm - first) : G;
-    const int64_t mb = first + (g % (G * nbn)) % gsz, nb = (g % (G * nbn)) / gsz;
-    const int64_t m0 = mb * MB, n0 = nb * MB;
-
-    float acc[4][4][4], hi[4][4][4], lo[4][4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[a][c][e] = hi[a][c][e] = lo[a][c][e] = 0.f;
-
-    int np = 0;
-    for (int s = 1; s <= OZ_S; ++s) np += max(0, min(OZ_S, lmax - s));
-    const int kst = (int)(Np / BG_KS);
-    const int64_t total = (int64_t)np * kst;
-    const int stage_elems = 2 * BG_PLANE;
-    auto issue = [&](int64_t gs) {
-        if (gs < total) {
-            int p = (int)(gs / kst), k = (int)(gs % kst), ps_, pu_;
-            oz_pair(p, lmax, ps_, pu_);
-            const __nv_bfloat16* A = YS + (ps_ - 1) * yps + m0 * Np;
-            const __nv_bfloat16* B = KS + (pu_ - 1) * kps + n0 * Np;
-            oz_stage_load(A, B, Np, (int64_t)k * BG_KS, smem + (gs % OZ_STAGES) * stage_elems);
-        }
-        cp_async_commit();
-    };
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wm = warp >> 2, wn = warp & 3;
-    const int lq = lane >> 3, lr = lane & 7;
-    for (int q = 0; q < OZ_STAGES - 1; ++q) issue(q);
-    for (int64_t gs = 0; gs < total; ++gs) {
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(OZ_STAGES - 2));
-        __syncthreads();
-        issue(gs + OZ_STAGES - 1);
-        const __nv_bfloat16* As = smem + (gs % OZ_STAGES) * stage_elems;
-        const __nv_bfloat16* Bs = As + BG_PLANE;
-#pragma unroll
-        for (int kk = 0; kk < BG_KS; kk += 16) {
-            uint32_t bf[4][2];
-#pragma unroll
-            for (int npr = 0; npr < 2; ++npr) {
-                uint32_t d[4];
-                const int c0 = wn * 32 + npr * 16;
-                ldsm_x4(d, Bs + (c0 + lr + (lq >> 1) * 8) * BG_LD + kk + (lq & 1) * 8);
-                bf[npr * 2][0] = d[0];
-                bf[npr * 2][1] = d[1];
-                bf[npr * 2 + 1][0] = d[2];
-                bf[npr * 2 + 1][1] = d[3];
-            }
-#pragma unroll
-            for (int mt = 0; mt < 4; ++mt) {
-                uint32_t af[4];
-                ldsm_x4(af, As + (wm * 64 + mt * 16 + lr + (lq & 1) * 8) * BG_LD + kk + (lq >> 1) * 8);
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af, bf[nt][0], bf[nt][1]);
-            }
-        }
-        const int k = (int)(gs % kst);
-        if ((k + 1) % (OZ_CHUNK / BG_KS) == 0 || k + 1 == kst) {
-            int ps_, pu_;
-            oz_pair((int)(gs / kst), lmax, ps_, pu_);
-            const float scale = ldexpf(1.f, -7 * (ps_ + pu_));
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        // double-FP32 accumulation (Knuth TwoSum) of an exact term
-                        const float v = acc[a][c][e] * scale;
-                        const float s = hi[a][c][e] + v;
-                        const float bv = s - hi[a][c][e];
-                        const float er = (hi[a][c][e] - (s - bv)) + (v - bv);
-                        hi[a][c][e] = s;
-                        lo[a][c][e] += er;
-                        acc[a][c][e] = 0.f;
-                    }
-        }
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::);
-    __syncthreads();
-
-    const double kappa = *kappa_p;
-    const int gq = lane >> 2, t = lane & 3;
-    double s1[4][2], s2[4][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) s1[a][0] = s1[a][1] = s2[a][0] = s2[a][1] = 0.0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int64_t gm = m0 + wm * 64 + a * 16 + gq + hh * 8;
-            const double scale = (gm < m) ? mu[gm] * kappa : 0.0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int64_t gn = n0 + wn * 32 + c * 8 + 2 * t + e;
-                    const int fe = hh * 2 + e;
-                    const int64_t o = gm * Np + gn;
-                    if (gm < m && gn < n_valid) {
-                        const double Cv = ((double)hi[a][c][fe] + (double)lo[a][c][fe]) * scale;
-                        const double kc = R64[o], x = (double)Y[o];
-                        const double r = kc - Cv;
-                        Rr32[o] = (float)r;
-                        s1[a][hh] = fma(kc, x, s1[a][hh]);
-                        s2[a][hh] = fma(x, r, s2[a][hh]);
-                    } else if (gm < ldm) {
-                        Rr32[o] = 0.f;
-                    }
-                }
-        }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-#pragma unroll
-            for (int o = 1; o < 4; o <<= 1) {
-                s1[a][hh] += __shfl_xor_sync(0xffffffffu, s1[a][hh], o);
-                s2[a][hh] += __shfl_xor_sync(0xffffffffu, s2[a][hh], o);
-            }
-            if (t == 0) {
-                const int rr = wm * 64 + a * 16 + gq + hh * 8;
-                rs[0][wn][rr] = s1[a][hh];
-                rs[1][wn][rr] = s2[a][hh];
-            }
-        }
-    __syncthreads();
-    if (threadIdx.x < 2 * MB) {
-        const int w = threadIdx.x / MB, r = threadIdx.x % MB;
-        qpart[((int64_t)w * nbn + nb) * ldm + m0 + r] = rs[w][0][r] + rs[w][1][r] + rs[w][2][r] + rs[w][3][r];
-    }
-}
-
 // var = k** - (sum k*^T x0 + sum x0^T r0 + ||L~^{-1} r0||^2), mean untouched.
 __global__ void k_var_finish(const double* qpart, int64_t nqb, const double* vpart2, int64_t nvp, int64_t ldm,
                              int64_t m, const GpHyperDev* hyp, int noisy, double* var)
@@ -901,7 +719,6 @@ static void ensure_attrs_mixed()
     cudaFuncSetAttribute(k_mlauum, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
     cudaFuncSetAttribute(k_mbdiag, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
     cudaFuncSetAttribute(k_mbupd, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
-    cudaFuncSetAttribute(k_ozaki_q, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
     done_dev = dev;
 }
 
@@ -1023,7 +840,7 @@ void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
 
 // Corrected variances into h->outv (needs predict_mixed's forward solve: R32
 // holds W, R64 holds K_{Z*,Z}).  Overwrites the W planes (run after full_cov_mixed).
-void var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
+bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 {
     ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, Np = h->Np;
@@ -1046,14 +863,12 @@ void var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
         h->ks_valid = true;
     }
     const int64_t nbn = Np / MB;
-    GPK_LAUNCH(h, GP_PH_REFINE, k_ozaki_q, (unsigned)(nbn * (ldm / MB)), NTH, OZ_SMEM_BYTES,
-               (const __nv_bfloat16*)h->YS, ldm * Np, (const __nv_bfloat16*)h->KS, Np * Np, Np,
-               (const double*)h->mu, (const double*)h->kappa, (const double*)h->R64, (const float*)h->R32,
-               h->Rr32, h->qpart, ldm, m, h->n, h->oz_lmax);
+    if (!ozaki_tc(h, m, ldm)) return false;
     forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_REFINE);
     GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, nbn,
                (const double*)h->vpart2, Np / MB, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
                h->outv);
+    return true;
 }
 
 void full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)
