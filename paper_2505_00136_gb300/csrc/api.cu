@@ -299,7 +299,7 @@ gp_status factor_mixed_refined(gp_t h)
 {
     gpk::set_info_none(h);
     gpk::assemble_train(h);
-    gpk::factor_mixed(h);
+    if (!gpk::factor_mixed(h)) return GP_ERR_CUDA;
     gp_status s = check_launch(h);
     if (s != GP_OK) return s;
     if ((s = read_info(h)) != GP_OK) return s;
@@ -595,7 +595,7 @@ gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* 
     if (s != GP_OK) return s;
     bool any_host = false;
     if (h->opt.prec == GP_MIXED) {
-        gpk::predict_mixed(h, m, ldm, var != nullptr || cov != nullptr);
+        if (!gpk::predict_mixed(h, m, ldm, var != nullptr || cov != nullptr)) return GP_ERR_CUDA;
     } else if (!var && !cov) {  // Eq. 3 alone: one pass K_{Z*,Z} alpha, no solve
         gpk::predict_mean_only(h, m, ldm);
     } else {
@@ -609,8 +609,8 @@ gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* 
             if ((s = ensure_cov_space(h, m)) != GP_OK) return s;
             target = h->cov;
         }
-        if (h->opt.prec == GP_MIXED) gpk::full_cov_mixed(h, m, ldm, target);
-        else gpk::full_cov(h, m, ldm, target);
+        if (h->opt.prec != GP_MIXED) gpk::full_cov(h, m, ldm, target);
+        else if (!gpk::full_cov_mixed(h, m, ldm, target)) return GP_ERR_CUDA;
         if (!cov_dev) {
             if ((s = copy_any(h, cov, target, m * m)) != GP_OK) return s;
             any_host = true;
@@ -665,14 +665,15 @@ gp_status gp_nlml_grad(gp_t h, double* nlml, double grad[3])
     gp_status s = ensure_factored(h);
     if (s != GP_OK) return s;
     if ((s = ensure_grad_buffers(h)) != GP_OK) return s;
-    if (h->opt.prec == GP_MIXED) gpk::inverse_mixed(h);
-    else gpk::inverse_tiles(h);
+    if (h->opt.prec != GP_MIXED) gpk::inverse_tiles(h);
+    else if (!gpk::inverse_mixed(h)) return GP_ERR_CUDA;
     gpk::adjoint_grad(h);
     if ((s = check_launch(h)) != GP_OK) return s;
     double tmp[4];
     if ((s = cuda_status(h, cudaMemcpyAsync(tmp, h->scal, sizeof(tmp), cudaMemcpyDeviceToHost, h->st))) != GP_OK)
         return s;
     if ((s = sync(h)) != GP_OK) return s;
+    if ((s = tc_status(h)) != GP_OK) return s;
     if (nlml) *nlml = tmp[0];
     grad[0] = tmp[1];
     grad[1] = tmp[2];
@@ -709,8 +710,12 @@ gp_status gp_optimize(gp_t h, int steps, double lr, double* nlml_hist)
                 launch_factor_body(h, it == 0);
             }
         }
-        if (mixed) gpk::inverse_mixed(h);
-        else gpk::inverse_tiles(h);
+        if (!mixed) {
+            gpk::inverse_tiles(h);
+        } else if (!gpk::inverse_mixed(h)) {
+            s = GP_ERR_CUDA;
+            break;
+        }
         gpk::adjoint_grad(h);
         gpk::adam_step(h, lr, hist ? hist + it : nullptr);
     }

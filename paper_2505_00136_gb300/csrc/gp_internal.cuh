@@ -162,19 +162,29 @@ void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, do
 void factor_dag(gp_t h, bool reset_err);                       // persistent tile-DAG factor (FP64)
 
 // kernels_mixed.cu
-void factor_mixed(gp_t h);                                     // mixed factor of h->A32
+bool factor_mixed(gp_t h);                                     // mixed factor of h->A32
 void refine_start(gp_t h, const double* rhs, double* x);       // x = L~^{-T} L~^{-1} rhs
 void refine_step(gp_t h, const double* rhs, double* x, double* r, double* norms);  // r = rhs - K x; x += correction
 void residual64(gp_t h, const double* x, const double* y, double* r);              // r = y - K x (FP64)
 void nlml_mixed(gp_t h);                                       // scal[0] from y^T alpha and log|K|
-void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var);
+bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var);
 void copy_factor_dense_mixed(gp_t h, double* out);
-void full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov);  // cov (prefilled prior) -= W W^T
-void inverse_mixed(gp_t h);                                    // Kinv32 = (L~ L~^T)^{-1}
+bool full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov);  // cov (prefilled prior) -= W W^T
+bool inverse_mixed(gp_t h);                                    // Kinv32 = (L~ L~^T)^{-1}
 bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm);     // FP64-level variances into outv
 // kernels_tc.cu
 bool ozaki_tc(gp_t h, int64_t m, int64_t ldm);                  // C = Y K digit-pair product + fused epilogue
 cudaError_t tc_error_fetch(gp_t h, int* out);                   // read and clear the tensor-core timeout word
+int* tc_error_dev();                                            // device address of that word
+// kernels_tgemm.cu: split-BF16 block products on tcgen05 (false: tensor map not encodable)
+bool tg_panel(gp_t h, int64_t k);
+bool tg_update(gp_t h, int64_t k);
+bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j);
+bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int64_t j);
+bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov);
+bool tg_trtri_fin(gp_t h, int64_t t);
+bool tg_trtri_acc(gp_t h, int64_t t);
+bool tg_lauum(gp_t h);
 constexpr int GP_OZ_SLICES = 6;                                // digit slices per operand (kernels_mixed.cu)
 }  // namespace gpk
 

@@ -70,58 +70,6 @@ __global__ void k_split_panel(const float* A32, __nv_bfloat16* PA, int64_t b, in
     }
 }
 
-// ---------------------------------------------------------------- mixed Cholesky steps
-// Panel: L_ik = A_ik Linv_kk^T (128-blocks; Linv lower so k runs to (cb+1)*128).
-// Writes L_ik in FP32 and its planes into LP.
-__global__ __launch_bounds__(NTH) void k_mpanel(float* A32, __nv_bfloat16* LP, const __nv_bfloat16* PA,
-                                                const __nv_bfloat16* LinvP, int64_t b, int64_t k,
-                                                const unsigned long long* info)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (failed(info)) return;
-    const int Q = (int)(b / MB);
-    const int rb = blockIdx.x / Q, cb = blockIdx.x % Q;
-    const int64_t i = k + 1 + blockIdx.y, bb = b * b;
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{PA + (int64_t)blockIdx.y * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
-    BView vb{LinvP + k * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
-    bgemm_acc(acc, va, vb, 0, (int64_t)(cb + 1) * MB, (__nv_bfloat16*)smem_raw);
-    const int64_t off = (int64_t)rb * MB * b + cb * MB;
-    float* dst = A32 + tri_index(i, k) * bb + off;
-    __nv_bfloat16* lp = LP + tri_index(i, k) * 3 * bb + off;
-    bacc_for_each(acc, [&](int r, int c, float v) {
-        int64_t o = (int64_t)r * b + c;
-        dst[o] = v;
-        __nv_bfloat16 hi, mid, lo;
-        split3(v, hi, mid, lo);
-        lp[o] = hi;
-        lp[bb + o] = mid;
-        lp[2 * bb + o] = lo;
-    });
-}
-
-// Trailing update: A_ij -= L_ik L_jk^T for k < j <= i.
-__global__ __launch_bounds__(NTH) void k_mupdate(float* A32, const __nv_bfloat16* LP, int64_t b, int64_t k,
-                                                 const unsigned long long* info)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (failed(info)) return;
-    const int Q = (int)(b / MB);
-    int64_t ii, jj;
-    tri_decode(blockIdx.x, ii, jj);
-    const int64_t i = k + 1 + ii, j = k + 1 + jj, bb = b * b;
-    const int rb = blockIdx.y / Q, cb = blockIdx.y % Q;
-    if (i == j && cb > rb) return;
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{LP + tri_index(i, k) * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
-    BView vb{LP + tri_index(j, k) * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
-    bgemm_acc(acc, va, vb, 0, b, (__nv_bfloat16*)smem_raw);
-    float* dst = A32 + tri_index(i, j) * bb + (int64_t)rb * MB * b + cb * MB;
-    bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * b + c] -= v; });
-}
-
 // ---------------------------------------------------------------- FP32 single-RHS solves
 __global__ __launch_bounds__(NTH) void k_tri_apply32(const float* Linv, int64_t b, int64_t j, const float* w,
                                                      float* out, int upper)
@@ -333,86 +281,6 @@ __global__ void k_split_cols(const float* R32, int64_t ldr, int64_t j, int64_t b
     }
 }
 
-// W_j = R_j Linv_jj^T (128 x 128 blocks); planes of W_j into WP and FP64 row
-// sums of W_j^2 into vpart[(j*Q + cb)][row].
-__global__ __launch_bounds__(NTH) void k_mdiagW(const __nv_bfloat16* RP, const __nv_bfloat16* LinvP,
-                                                __nv_bfloat16* WP, int64_t ldw, double* vpart, int64_t ldm,
-                                                int64_t b, int64_t j, float* Wout)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double rs[4][MB];
-    const int Q = (int)(b / MB);
-    const int cb = blockIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.y * MB, bb = b * b, ps = ldm * b;
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{RP + m0 * b, b, ps, MB};
-    BView vb{LinvP + j * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
-    bgemm_acc(acc, va, vb, 0, (int64_t)(cb + 1) * MB, (__nv_bfloat16*)smem_raw);
-    __nv_bfloat16* wp = WP + m0 * ldw + j * b + cb * MB;
-    const int64_t psw = ldm * ldw;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wn = warp & 3, wm = warp >> 2;
-    double rowsq[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    float* wout = Wout + m0 * ldw + j * b + cb * MB;   // W_j in FP32 over R_j (same layout as WP)
-    bacc_for_each(acc, [&](int r, int c, float v) {
-        int64_t o = (int64_t)r * ldw + c;
-        __nv_bfloat16 hi, mid, lo;
-        split3(v, hi, mid, lo);
-        wp[o] = hi;
-        wp[psw + o] = mid;
-        wp[2 * psw + o] = lo;
-        wout[o] = v;
-    });
-#pragma unroll
-    for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const float* f = acc.c[mt][nt];
-            rowsq[mt][0] += (double)f[0] * f[0] + (double)f[1] * f[1];
-            rowsq[mt][1] += (double)f[2] * f[2] + (double)f[3] * f[3];
-        }
-#pragma unroll
-    for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            double v = rowsq[mt][h];
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            rowsq[mt][h] = v;
-        }
-    if ((lane & 3) == 0) {
-        const int g = lane >> 2;
-#pragma unroll
-        for (int mt = 0; mt < 4; ++mt) {
-            rs[wn][wm * 64 + mt * 16 + g] = rowsq[mt][0];
-            rs[wn][wm * 64 + mt * 16 + g + 8] = rowsq[mt][1];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < MB) {
-        int r = threadIdx.x;
-        vpart[(j * Q + cb) * ldm + m0 + r] = rs[0][r] + rs[1][r] + rs[2][r] + rs[3][r];
-    }
-}
-
-// R_i -= W_j L_ij^T for all tiles i > j.
-__global__ __launch_bounds__(NTH) void k_mupdW(float* R32, int64_t ldr, const __nv_bfloat16* WP,
-                                               const __nv_bfloat16* LP, int64_t ldm, int64_t b, int64_t j)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Q = (int)(b / MB);
-    const int64_t i = j + 1 + blockIdx.x / Q;
-    const int cb = blockIdx.x % Q;
-    const int64_t m0 = (int64_t)blockIdx.y * MB, bb = b * b;
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{WP + m0 * ldr + j * b, ldr, ldm * ldr, MB};
-    BView vb{LP + tri_index(i, j) * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
-    bgemm_acc(acc, va, vb, 0, b, (__nv_bfloat16*)smem_raw);
-    float* dst = R32 + m0 * ldr + i * b + cb * MB;
-    bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * ldr + c] -= v; });
-}
-
 // mean = sum of the mean partials, var = k** - sum of the variance partials.
 __global__ void k_mixed_finish(const double* mpart, int64_t nmp, const double* vpart, int64_t nvp, int64_t ldm,
                                int64_t m, const GpHyperDev* hyp, int noisy, double* mean, double* var)
@@ -424,28 +292,6 @@ __global__ void k_mixed_finish(const double* mpart, int64_t nmp, const double* v
     for (int64_t q = 0; q < nvp; ++q) sv += vpart[q * ldm + c];
     if (mean) mean[c] = sm;
     if (var) var[c] = hyp->nu + (noisy ? hyp->s2 : 0.0) - sv;
-}
-
-// ---------------------------------------------------------------- mixed full covariance
-// cov (m x m, FP64, prefilled with K_{Z*,Z*}) -= W W^T on lower 128-blocks, mirrored.
-__global__ __launch_bounds__(NTH) void k_msyrk_cov(const __nv_bfloat16* WP, int64_t ldw, int64_t ps,
-                                                   int64_t kdim, int64_t m, double* cov)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    int64_t a, c;
-    tri_decode(blockIdx.x, a, c);
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{WP + a * MB * ldw, ldw, ps, MB};
-    BView vb{WP + c * MB * ldw, ldw, ps, MB};
-    bgemm_acc(acc, va, vb, 0, kdim, (__nv_bfloat16*)smem_raw);
-    bacc_for_each(acc, [&](int r, int cc, float v) {
-        int64_t R = a * MB + r, C = c * MB + cc;
-        if (R >= m || C >= m || (a == c && cc > r)) return;
-        double x = cov[R * m + C] - (double)v;
-        cov[R * m + C] = x;
-        cov[C * m + R] = x;
-    });
 }
 
 // ---------------------------------------------------------------- mixed inverse for the gradient
@@ -485,72 +331,6 @@ __global__ void k_split_row(const float* U32, __nv_bfloat16* PA, int64_t b, int6
         dst[bb + e] = mid;
         dst[2 * bb + e] = lo;
     }
-}
-
-// Z_tj = -U_tj Linv_tt^T for j < t (grid.y = j), planes into ZP.
-__global__ __launch_bounds__(NTH) void k_mtrtri_fin(const __nv_bfloat16* PA, const __nv_bfloat16* LinvP,
-                                                    __nv_bfloat16* ZP, int64_t b, int64_t t)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Q = (int)(b / MB);
-    const int rb = blockIdx.x / Q, cb = blockIdx.x % Q;
-    const int64_t j = blockIdx.y, bb = b * b;
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{PA + j * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
-    BView vb{LinvP + t * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
-    bgemm_acc(acc, va, vb, 0, (int64_t)(cb + 1) * MB, (__nv_bfloat16*)smem_raw);
-    __nv_bfloat16* zp = ZP + tri_index(t, j) * 3 * bb + (int64_t)rb * MB * b + cb * MB;
-    bacc_for_each(acc, [&](int r, int c, float v) {
-        int64_t o = (int64_t)r * b + c;
-        __nv_bfloat16 hi, mid, lo;
-        split3(-v, hi, mid, lo);
-        zp[o] = hi;
-        zp[bb + o] = mid;
-        zp[2 * bb + o] = lo;
-    });
-}
-
-// U_ij (+)= Z_tj L_it^T for i > t >= j; the first contribution (t == j) overwrites.
-__global__ __launch_bounds__(NTH) void k_mtrtri_acc(const __nv_bfloat16* ZP, const __nv_bfloat16* LP, float* U32,
-                                                    int64_t b, int64_t t)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Q = (int)(b / MB);
-    const int64_t i = t + 1 + blockIdx.x / (t + 1), j = blockIdx.x % (t + 1), bb = b * b;
-    const int rb = blockIdx.y / Q, cb = blockIdx.y % Q;
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{ZP + tri_index(t, j) * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
-    BView vb{LP + tri_index(i, t) * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
-    bgemm_acc(acc, va, vb, 0, b, (__nv_bfloat16*)smem_raw);
-    float* dst = U32 + tri_index(i, j) * bb + (int64_t)rb * MB * b + cb * MB;
-    const bool first = (t == j);
-    bacc_for_each(acc, [&](int r, int c, float v) {
-        float* p = dst + (int64_t)r * b + c;
-        *p = first ? v : *p + v;
-    });
-}
-
-// K^{-1}_ij = sum_{t >= i} Z_ti Z_tj^T on lower tiles (FP32 out).
-__global__ __launch_bounds__(NTH) void k_mlauum(const __nv_bfloat16* ZP, float* Kinv32, int64_t b, int64_t T)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Q = (int)(b / MB);
-    int64_t i, j;
-    tri_decode(blockIdx.x, i, j);
-    const int rb = blockIdx.y / Q, cb = blockIdx.y % Q;
-    if (i == j && cb > rb) return;
-    const int64_t bb = b * b;
-    BAcc acc;
-    bacc_zero(acc);
-    for (int64_t t = i; t < T; ++t) {
-        BView va{ZP + tri_index(t, i) * 3 * bb + (int64_t)rb * MB * b, b, bb, MB};
-        BView vb{ZP + tri_index(t, j) * 3 * bb + (int64_t)cb * MB * b, b, bb, MB};
-        bgemm_acc(acc, va, vb, (t == i) ? (int64_t)rb * MB : 0, b, (__nv_bfloat16*)smem_raw);
-    }
-    float* dst = Kinv32 + tri_index(i, j) * bb + (int64_t)rb * MB * b + cb * MB;
-    bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * b + c] = v; });
 }
 
 // ---------------------------------------------------------------- variance correction
@@ -709,24 +489,15 @@ static void ensure_attrs_mixed()
     int dev = 0;
     cudaGetDevice(&dev);
     if (done_dev == dev) return;
-    cudaFuncSetAttribute(k_mpanel, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
-    cudaFuncSetAttribute(k_mupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
-    cudaFuncSetAttribute(k_mdiagW, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
-    cudaFuncSetAttribute(k_mupdW, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
-    cudaFuncSetAttribute(k_msyrk_cov, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
-    cudaFuncSetAttribute(k_mtrtri_fin, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
-    cudaFuncSetAttribute(k_mtrtri_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
-    cudaFuncSetAttribute(k_mlauum, cudaFuncAttributeMaxDynamicSharedMemorySize, BG_SMEM_BYTES);
     cudaFuncSetAttribute(k_mbdiag, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
     cudaFuncSetAttribute(k_mbupd, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
     done_dev = dev;
 }
 
-void factor_mixed(gp_t h)
+bool factor_mixed(gp_t h)
 {
     ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, bb = b * b;
-    const int Q = (int)(b / MB);
     for (int64_t k = 0; k < T; ++k) {
         float* Akk = h->A32 + tri_index(k, k) * bb;
         GPK_LAUNCH(h, GP_PH_POTRF, k_tile_up64, grid_for(bb), NTH, 0, (const float*)Akk, h->D64, bb);
@@ -737,14 +508,10 @@ void factor_mixed(gp_t h)
             const unsigned tt = (unsigned)(T - k - 1);
             GPK_LAUNCH(h, GP_PH_TRSM, k_split_panel, dim3((unsigned)grid_for(bb) / 4 + 1, tt), NTH, 0,
                        (const float*)h->A32, h->PA, b, k);
-            GPK_LAUNCH(h, GP_PH_TRSM, k_mpanel, dim3((unsigned)(Q * Q), tt), NTH, BG_SMEM_BYTES, h->A32, h->LP,
-                       (const __nv_bfloat16*)h->PA, (const __nv_bfloat16*)h->LinvP, b, k,
-                       (const unsigned long long*)h->info);
-            GPK_LAUNCH(h, GP_PH_UPDATE, k_mupdate, dim3(tt * (tt + 1) / 2, (unsigned)(Q * Q)), NTH,
-                       BG_SMEM_BYTES, h->A32, (const __nv_bfloat16*)h->LP, b, k,
-                       (const unsigned long long*)h->info);
+            if (!tg_panel(h, k) || !tg_update(h, k)) return false;
         }
     }
+    return true;
 }
 
 // out32 = L~^{-1} in32 (lower) or L~^{-T} in32 (upper), FP32 throughout.
@@ -810,21 +577,18 @@ void nlml_mixed(gp_t h)
 
 // Forward multi-RHS solve W = R L~^{-T} in place over R (ldm x Np, FP32): W
 // planes into WP, FP32 W over R, FP64 row sums of W^2 into vpart.
-static void forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase)
+static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase)
 {
     const int64_t T = h->T, b = h->b, Np = h->Np;
-    const int Q = (int)(b / MB);
     for (int64_t j = 0; j < T; ++j) {
         GPK_LAUNCH(h, phase, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)R, Np, j, b, ldm, h->RP);
-        GPK_LAUNCH(h, phase, k_mdiagW, dim3((unsigned)Q, (unsigned)(ldm / MB)), NTH, BG_SMEM_BYTES,
-                   (const __nv_bfloat16*)h->RP, (const __nv_bfloat16*)h->LinvP, h->WP, Np, vpart, ldm, b, j, R);
-        if (j + 1 < T)
-            GPK_LAUNCH(h, phase, k_mupdW, dim3((unsigned)((T - j - 1) * Q), (unsigned)(ldm / MB)), NTH,
-                       BG_SMEM_BYTES, R, Np, (const __nv_bfloat16*)h->WP, (const __nv_bfloat16*)h->LP, ldm, b, j);
+        if (!tg_diag_w(h, phase, R, ldm, vpart, j)) return false;
+        if (j + 1 < T && !tg_upd_w(h, phase, R, ldm, j)) return false;
     }
+    return true;
 }
 
-void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
+bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
 {
     ensure_attrs_mixed();
     const int64_t Np = h->Np;
@@ -832,10 +596,11 @@ void predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
     GPK_LAUNCH(h, GP_PH_CROSS, k_cross_mixed, dim3((unsigned)(Np / 64), (unsigned)(ldm / 64)), NTH, 0,
                (const double*)h->Xs, m, (const double*)h->X, h->n, h->d, (const double*)h->alpha,
                (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm, h->R64);
-    if (want_var) forward_w(h, h->R32, ldm, h->vpart, GP_PH_VSOLVE);
+    if (want_var && !forward_w(h, h->R32, ldm, h->vpart, GP_PH_VSOLVE)) return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_mixed_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->mpart,
                nmp, (const double*)h->vpart, want_var ? nvp : (int64_t)0, ldm, m, (const GpHyperDev*)h->hyp,
                h->opt.noisy_test_var, h->outm, want_var ? h->outv : (double*)nullptr);
+    return true;
 }
 
 // Corrected variances into h->outv (needs predict_mixed's forward solve: R32
@@ -864,42 +629,35 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
     }
     const int64_t nbn = Np / MB;
     if (!ozaki_tc(h, m, ldm)) return false;
-    forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_REFINE);
+    if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_REFINE)) return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, nbn,
                (const double*)h->vpart2, Np / MB, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
                h->outv);
     return true;
 }
 
-void full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)
+bool full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)
 {
     ensure_attrs_mixed();
     assemble_test_prior(h, m, cov);
-    const int64_t nb = (m + MB - 1) / MB;
-    GPK_LAUNCH(h, GP_PH_COV, k_msyrk_cov, (unsigned)(nb * (nb + 1) / 2), NTH, BG_SMEM_BYTES,
-               (const __nv_bfloat16*)h->WP, h->Np, ldm * h->Np, h->Np, m, cov);
+    return tg_syrk_cov(h, m, ldm, cov);
 }
 
-void inverse_mixed(gp_t h)
+bool inverse_mixed(gp_t h)
 {
     ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, bb = b * b;
-    const int Q = (int)(b / MB);
     GPK_LAUNCH(h, GP_PH_TRTRI, k_zdiag, dim3((unsigned)grid_for(bb) / 4 + 1, (unsigned)T), NTH, 0,
                (const float*)h->Linv32, h->ZP, b);
     for (int64_t t = 0; t < T; ++t) {
         if (t > 0) {
             GPK_LAUNCH(h, GP_PH_TRTRI, k_split_row, dim3((unsigned)grid_for(bb) / 4 + 1, (unsigned)t), NTH, 0,
                        (const float*)h->U32, h->PA, b, t);
-            GPK_LAUNCH(h, GP_PH_TRTRI, k_mtrtri_fin, dim3((unsigned)(Q * Q), (unsigned)t), NTH, BG_SMEM_BYTES,
-                       (const __nv_bfloat16*)h->PA, (const __nv_bfloat16*)h->LinvP, h->ZP, b, t);
+            if (!tg_trtri_fin(h, t)) return false;
         }
-        if (t + 1 < T)
-            GPK_LAUNCH(h, GP_PH_TRTRI, k_mtrtri_acc, dim3((unsigned)((T - t - 1) * (t + 1)), (unsigned)(Q * Q)),
-                       NTH, BG_SMEM_BYTES, (const __nv_bfloat16*)h->ZP, (const __nv_bfloat16*)h->LP, h->U32, b, t);
+        if (t + 1 < T && !tg_trtri_acc(h, t)) return false;
     }
-    GPK_LAUNCH(h, GP_PH_LAUUM, k_mlauum, dim3((unsigned)(T * (T + 1) / 2), (unsigned)(Q * Q)), NTH, BG_SMEM_BYTES,
-               (const __nv_bfloat16*)h->ZP, h->Kinv32, b, T);
+    return tg_lauum(h);
 }
 
 void copy_factor_dense_mixed(gp_t h, double* out)

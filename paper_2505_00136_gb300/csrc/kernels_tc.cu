@@ -293,14 +293,14 @@ bool map_bf16_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int* tc_error_ptr()
+}  // namespace
+
+int* tc_error_dev()
 {
     void* p = nullptr;
-    cudaGetSymbolAddress(&p, g_tc_error);
+    if (cudaGetSymbolAddress(&p, g_tc_error) != cudaSuccess) return nullptr;
     return (int*)p;
 }
-
-}  // namespace
 
 bool ozaki_tc(gp_t h, int64_t m, int64_t ldm)
 {
@@ -315,7 +315,7 @@ bool ozaki_tc(gp_t h, int64_t m, int64_t ldm)
     CUtensorMap mY, mK;
     if (!map_bf16_tiles(&mY, h->YS, GP_OZ_SLICES * ldm, Np) || !map_bf16_tiles(&mK, h->KS, GP_OZ_SLICES * Np, Np))
         return false;
-    int* err = tc_error_ptr();
+    int* err = tc_error_dev();
     if (!err) return false;
     const int64_t nbn = Np / 128;
     GPK_LAUNCH(h, GP_PH_REFINE, k_ozaki_tc, (unsigned)(nbn * (ldm / 128)), OZT_THREADS, OZT_SMEM, mY, mK, ldm, Np,
@@ -328,7 +328,7 @@ bool ozaki_tc(gp_t h, int64_t m, int64_t ldm)
 // stream synchronisation) into *out and clears it on the device.
 cudaError_t tc_error_fetch(gp_t h, int* out)
 {
-    int* err = tc_error_ptr();
+    int* err = tc_error_dev();
     if (!err) return cudaErrorInvalidSymbol;
     cudaError_t e = cudaMemcpyAsync(out, err, sizeof(int), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), h->st);
