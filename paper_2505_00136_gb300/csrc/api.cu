@@ -120,7 +120,7 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     dev_free(h, &h->RP, 3 * old * h->b);
     dev_free(h, &h->WP, 3 * old * h->Np);
     dev_free(h, &h->mpart, old * (h->Np / TB));
-    dev_free(h, &h->vpart, old * (h->Np / (2 * TB)));
+    dev_free(h, &h->vpart, old * (h->Np / 64));
     dev_free(h, &h->outm, old);
     dev_free(h, &h->outv, old);
     dev_free(h, &h->R64, old * h->Np);
@@ -129,7 +129,7 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     dev_free(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * old * h->Np);
     dev_free(h, &h->mu, old);
     dev_free(h, &h->qpart, 2 * old * (h->Np / (2 * TB)));
-    dev_free(h, &h->vpart2, old * (h->Np / (2 * TB)));
+    dev_free(h, &h->vpart2, old * (h->Np / 64));
     h->m_cap = 0;
     gp_status s;
     if ((s = dev_alloc(h, &h->Xs, ldm * h->d)) != GP_OK) return s;
@@ -141,12 +141,12 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
         if ((s = dev_alloc(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * ldm * h->Np)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->mu, ldm)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->qpart, 2 * ldm * (h->Np / (2 * TB)))) != GP_OK) return s;
-        if ((s = dev_alloc(h, &h->vpart2, ldm * (h->Np / (2 * TB)))) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->vpart2, ldm * (h->Np / 64))) != GP_OK) return s;   // one slot per 64 columns
     }
     if ((s = dev_alloc(h, &h->RP, 3 * ldm * h->b)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->WP, 3 * ldm * h->Np)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->mpart, ldm * (h->Np / TB))) != GP_OK) return s;
-    if ((s = dev_alloc(h, &h->vpart, ldm * (h->Np / (2 * TB)))) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->vpart, ldm * (h->Np / 64))) != GP_OK) return s;     // one slot per 64 columns
     if ((s = dev_alloc(h, &h->outm, ldm)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->outv, ldm)) != GP_OK) return s;
     h->m_cap = ldm;

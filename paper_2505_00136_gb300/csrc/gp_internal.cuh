@@ -85,7 +85,7 @@ struct gp_handle {
     float* R32;               // m_cap x Np: K_{Z*,Z}, overwritten by the W solve
     __nv_bfloat16 *RP, *WP;   // planes: RP 3 x m_cap x b (scratch), WP 3 x m_cap x Np (all of W)
     double* mpart;            // (Np/64) x m_cap mean partial sums
-    double* vpart;            // (Np/128) x m_cap variance partial sums
+    double* vpart;            // (Np/64) x m_cap variance partial sums (one per 64 columns)
     // variance correction (GP_MIXED)
     double* R64;              // m_cap x Np: FP64 K_{Z*,Z}
     float* Rr32;              // m_cap x Np: r0 = K_{Z*,Z} - x0^T K
@@ -95,7 +95,7 @@ struct gp_handle {
     double* mu;               // m_cap row scales of x0^T
     double* kappa;            // scale of K
     double* qpart;            // 2 x (Np/128) x m_cap partial sums
-    double* vpart2;           // (Np/128) x m_cap partial sums of ||L~^{-1} r0||^2
+    double* vpart2;           // (Np/64) x m_cap partial sums of ||L~^{-1} r0||^2
     bool ks_valid;            // KS matches the current K
     int oz_lmax;              // digit pairs (s, u) with s + u <= oz_lmax enter the exact product
     bool tc_pending;          // a tensor-core kernel ran since its timeout word was last read

@@ -592,7 +592,7 @@ bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
 {
     ensure_attrs_mixed();
     const int64_t Np = h->Np;
-    const int64_t nmp = Np / 64, nvp = Np / MB;
+    const int64_t nmp = Np / 64, nvp = Np / 64;   // variance partials: one slot per 64 columns
     GPK_LAUNCH(h, GP_PH_CROSS, k_cross_mixed, dim3((unsigned)(Np / 64), (unsigned)(ldm / 64)), NTH, 0,
                (const double*)h->Xs, m, (const double*)h->X, h->n, h->d, (const double*)h->alpha,
                (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm, h->R64);
@@ -631,7 +631,7 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
     if (!ozaki_tc(h, m, ldm)) return false;
     if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_REFINE)) return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, nbn,
-               (const double*)h->vpart2, Np / MB, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
+               (const double*)h->vpart2, Np / 64, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
                h->outv);
     return true;
 }

@@ -8,12 +8,14 @@
 // one or more k-segments; Op names the operand tiles, the units and the
 // epilogue.
 //
-// Roles (192 threads, one CTA per SM, grid = min(units, SMs)): warp 0 issues
+// Roles (320 threads, one CTA per SM, grid = min(units, SMs)): warp 0 issues
 // the TMA loads of a 64-k stage (three A planes and three B planes, six
 // 128 x 64 tiles, 96 KB) into a two-stage ring; warp 1 owns 256 TMEM columns
 // (two 128-column accumulators, alternating between units) and issues the
-// six plane MMAs per 16-k step; warps 2-5 run the epilogue of unit c while
-// the MMAs of unit c+1 proceed, one output row per thread.  Waits are bounded
+// six plane MMAs per 16-k step; warps 2-9 run the epilogue of unit c while
+// the MMAs of unit c+1 proceed: two warps per TMEM lane quarter, each thread
+// one output row and 64 columns, its read-modify-write loads issued before it
+// waits for the accumulator.  Waits are bounded
 // (see tc_common.cuh); a timeout sets the device error word and the CTA
 // leaves without touching its outputs.
 #include <cuda.h>
@@ -29,7 +31,8 @@
 namespace gpk {
 namespace {
 
-constexpr int TG_THREADS = 192;
+constexpr int TG_THREADS = 320;
+constexpr int TG_EPI_WARPS = 8;
 constexpr int TG_STAGES = 2;
 constexpr int TG_STAGE_BYTES = 6 * tc::TILE_BYTES;
 constexpr int TG_BAR_OFF = TG_STAGES * TG_STAGE_BYTES;
@@ -76,8 +79,8 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
         }
         tc::mbar_init(accf(0), 1);
         tc::mbar_init(accf(1), 1);
-        tc::mbar_init(acce(0), 4);
-        tc::mbar_init(acce(1), 4);
+        tc::mbar_init(acce(0), TG_EPI_WARPS);
+        tc::mbar_init(acce(1), TG_EPI_WARPS);
         tc::mbar_init(drain, 1);
         *abort = 0;
         tc::mbar_init_fence();
@@ -169,16 +172,18 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
             }
         }
     } else {
-        const int wq = warp & 3, row = wq * 32 + lane;
+        const int wq = warp & 3, row = wq * 32 + lane, c0 = ((warp - 2) >> 2) * 64;
         const uint32_t lrow = (uint32_t)(wq * 32) << 16;
         int c = 0;
         for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
             if (!op.active(u)) continue;
             const int a = c & 1;
-            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(accf(a), (uint32_t)((c >> 1) & 1), abort, err));
-            if (!ok) break;
-            tc::fence_after();
-            op.epilogue(u, row, tmem + lrow + (uint32_t)(a * 128));
+            auto wait = [&]() {
+                const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(accf(a), (uint32_t)((c >> 1) & 1), abort, err));
+                if (ok) tc::fence_after();
+                return ok;
+            };
+            if (!op.epilogue(u, row, c0, tmem + lrow + (uint32_t)(a * 128), wait)) break;
             tc::fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(acce(a));
@@ -195,49 +200,47 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
 }
 
 // ---------------------------------------------------------------- epilogue helpers
-__device__ __forceinline__ void st_f16x(float* p, const float (&v)[16])
+// 64 FP32 values of one row: p must be 16-byte aligned.
+struct Row64 {
+    float4 x[16];
+};
+
+__device__ __forceinline__ void row_load(Row64& r, const float* p)
 {
 #pragma unroll
-    for (int q = 0; q < 16; q += 4) *(float4*)(p + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+    for (int q = 0; q < 16; ++q) r.x[q] = __ldcg((const float4*)p + q);
 }
 
-__device__ __forceinline__ void sub_f16x(float* p, const float (&v)[16])
+__device__ __forceinline__ void row_store(float* p, const float (&v)[32], int h)
 {
 #pragma unroll
-    for (int q = 0; q < 16; q += 4) {
-        float4 x = __ldcg((const float4*)(p + q));
-        x.x -= v[q];
-        x.y -= v[q + 1];
-        x.z -= v[q + 2];
-        x.w -= v[q + 3];
-        *(float4*)(p + q) = x;
+    for (int q = 0; q < 8; ++q) ((float4*)p)[8 * h + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// p[32h + e] = base[32h + e] + sign * v[e] for the 32 values of half h.
+__device__ __forceinline__ void row_axpy(float* p, const Row64& base, const float (&v)[32], int h, float sign)
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float4 x = base.x[8 * h + q];
+        x.x += sign * v[4 * q];
+        x.y += sign * v[4 * q + 1];
+        x.z += sign * v[4 * q + 2];
+        x.w += sign * v[4 * q + 3];
+        ((float4*)p)[8 * h + q] = x;
     }
 }
 
-__device__ __forceinline__ void add_f16x(float* p, const float (&v)[16])
+// Three BF16 planes of 32 values at p, p + ps, p + 2 ps (16-byte aligned).
+__device__ __forceinline__ void planes32(__nv_bfloat16* p, int64_t ps, const float (&v)[32], float sign = 1.f)
 {
 #pragma unroll
-    for (int q = 0; q < 16; q += 4) {
-        float4 x = __ldcg((const float4*)(p + q));
-        x.x += v[q];
-        x.y += v[q + 1];
-        x.z += v[q + 2];
-        x.w += v[q + 3];
-        *(float4*)(p + q) = x;
-    }
-}
-
-// Three BF16 planes of 16 values at p, p + ps, p + 2 ps (16-byte aligned).
-__device__ __forceinline__ void planes_f16x(__nv_bfloat16* p, int64_t ps, const float (&v)[16], float sign = 1.f)
-{
-    __align__(16) __nv_bfloat16 h[3][16];
+    for (int g = 0; g < 4; ++g) {
+        __align__(16) __nv_bfloat16 hb[3][8];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) split3(sign * v[q], h[0][q], h[1][q], h[2][q]);
+        for (int q = 0; q < 8; ++q) split3(sign * v[8 * g + q], hb[0][q], hb[1][q], hb[2][q]);
 #pragma unroll
-    for (int pl = 0; pl < 3; ++pl) {
-        uint4* d = (uint4*)(p + pl * ps);
-        d[0] = *(const uint4*)&h[pl][0];
-        d[1] = *(const uint4*)&h[pl][8];
+        for (int pl = 0; pl < 3; ++pl) *(uint4*)(p + pl * ps + 8 * g) = *(const uint4*)&hb[pl][0];
     }
 }
 
@@ -263,20 +266,23 @@ struct OpPanel {
         const int y = u / (Q * Q), r = u % (Q * Q), rb = r / Q, cb = r % Q;
         return Seg{y * 3 * b + rb * 128, 0, k * 3 * b + cb * 128, 0, 0, (cb + 1) * 128};
     }
-    __device__ void epilogue(int u, int row, uint32_t t) const
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
         const int y = u / (Q * Q), r = u % (Q * Q), rb = r / Q, cb = r % Q;
         const int64_t i = k + 1 + y, bb = (int64_t)b * b;
-        const int64_t off = (int64_t)(rb * 128 + row) * b + cb * 128;
+        const int64_t off = (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
         float* dst = A32 + tri_index(i, k) * bb + off;
         __nv_bfloat16* lp = LP + 3 * tri_index(i, k) * bb + off;
+        if (!wait()) return false;
 #pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
-            float v[16];
-            tc::tmem_ld16(t + col, v);
-            st_f16x(dst + col, v);
-            planes_f16x(lp + col, bb, v);
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(t + c0 + 32 * h, v);
+            row_store(dst, v, h);
+            planes32(lp + 32 * h, bb, v);
         }
+        return true;
     }
 };
 
@@ -312,18 +318,23 @@ struct OpUpdate {
         decode(u, i, j, rb, cb);
         return Seg{(int)(tri_index(i, k) * 3 * b) + rb * 128, 0, (int)(tri_index(j, k) * 3 * b) + cb * 128, 0, 0, b};
     }
-    __device__ void epilogue(int u, int row, uint32_t t) const
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
         int64_t i, j;
         int rb, cb;
         decode(u, i, j, rb, cb);
-        float* dst = A32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128;
-#pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
-            float v[16];
-            tc::tmem_ld16(t + col, v);
-            sub_f16x(dst + col, v);
+        float* dst = A32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
+        Row64 cur;
+        row_load(cur, dst);
+        if (!wait()) return false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(t + c0 + 32 * h, v);
+            row_axpy(dst, cur, v, h, -1.f);
         }
+        return true;
     }
 };
 
@@ -345,22 +356,25 @@ struct OpDiagW {
         const int cb = u % Q, mb = u / Q;
         return Seg{mb * 128, 0, j * 3 * b + cb * 128, 0, 0, (cb + 1) * 128};
     }
-    __device__ void epilogue(int u, int row, uint32_t t) const
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
         const int cb = u % Q, mb = u / Q;
         const int64_t r = (int64_t)mb * 128 + row;
-        const int64_t o = r * ldw + (int64_t)j * b + cb * 128;
+        const int64_t o = r * ldw + (int64_t)j * b + cb * 128 + c0;
+        if (!wait()) return false;
         double sq = 0.0;
 #pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
-            float v[16];
-            tc::tmem_ld16(t + col, v);
-            planes_f16x(WP + o + col, ldm * ldw, v);
-            st_f16x(Wout + o + col, v);
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(t + c0 + 32 * h, v);
+            planes32(WP + o + 32 * h, ldm * ldw, v);
+            row_store(Wout + o, v, h);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) sq += (double)v[q] * v[q];
+            for (int q = 0; q < 32; ++q) sq += (double)v[q] * v[q];
         }
-        vpart[((int64_t)j * Q + cb) * ldm + r] = sq;
+        vpart[(((int64_t)j * b + cb * 128 + c0) / 64) * ldm + r] = sq;   // one slot per 64 columns
+        return true;
     }
 };
 
@@ -381,18 +395,23 @@ struct OpUpdW {
         const int cb = x % Q;
         return Seg{mb * 128, j * b, (int)(tri_index(i, j) * 3 * b) + cb * 128, 0, 0, b};
     }
-    __device__ void epilogue(int u, int row, uint32_t t) const
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
         const int nx = (T - j - 1) * Q, x = u % nx, mb = u / nx;
         const int64_t i = j + 1 + x / Q;
         const int cb = x % Q;
-        float* dst = R32 + ((int64_t)mb * 128 + row) * ldr + i * b + cb * 128;
-#pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
-            float v[16];
-            tc::tmem_ld16(t + col, v);
-            sub_f16x(dst + col, v);
+        float* dst = R32 + ((int64_t)mb * 128 + row) * ldr + i * b + cb * 128 + c0;
+        Row64 cur;
+        row_load(cur, dst);
+        if (!wait()) return false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(t + c0 + 32 * h, v);
+            row_axpy(dst, cur, v, h, -1.f);
         }
+        return true;
     }
 };
 
@@ -412,24 +431,28 @@ struct OpSyrkCov {
         tri_decode(u, a, c);
         return Seg{(int)a * 128, 0, (int)c * 128, 0, 0, kdim};
     }
-    __device__ void epilogue(int u, int row, uint32_t t) const
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
         int64_t a, c;
         tri_decode(u, a, c);
         const int64_t R = a * 128 + row;
+        if (!wait()) return false;
 #pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
-            float v[16];
-            tc::tmem_ld16(t + col, v);
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(t + c0 + 32 * h, v);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int64_t C = c * 128 + col + q;
-                if (R >= m || C >= m || (a == c && col + q > row)) continue;
+            for (int q = 0; q < 32; ++q) {
+                const int cc = c0 + 32 * h + q;
+                const int64_t C = c * 128 + cc;
+                if (R >= m || C >= m || (a == c && cc > row)) continue;
                 const double x = cov[R * m + C] - (double)v[q];
                 cov[R * m + C] = x;
                 cov[C * m + R] = x;
             }
         }
+        return true;
     }
 };
 
@@ -447,17 +470,20 @@ struct OpTrtriFin {
         const int j = u / (Q * Q), r = u % (Q * Q), rb = r / Q, cb = r % Q;
         return Seg{j * 3 * b + rb * 128, 0, t * 3 * b + cb * 128, 0, 0, (cb + 1) * 128};
     }
-    __device__ void epilogue(int u, int row, uint32_t tm) const
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t tm, W&& wait) const
     {
         const int j = u / (Q * Q), r = u % (Q * Q), rb = r / Q, cb = r % Q;
         const int64_t bb = (int64_t)b * b;
-        __nv_bfloat16* zp = ZP + tri_index(t, j) * 3 * bb + (int64_t)(rb * 128 + row) * b + cb * 128;
+        __nv_bfloat16* zp = ZP + tri_index(t, j) * 3 * bb + (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
+        if (!wait()) return false;
 #pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
-            float v[16];
-            tc::tmem_ld16(tm + col, v);
-            planes_f16x(zp + col, bb, v, -1.f);
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(tm + c0 + 32 * h, v);
+            planes32(zp + 32 * h, bb, v, -1.f);
         }
+        return true;
     }
 };
 
@@ -485,20 +511,25 @@ struct OpTrtriAcc {
         decode(u, i, j, rb, cb);
         return Seg{(int)(tri_index(t, j) * 3 * b) + rb * 128, 0, (int)(tri_index(i, t) * 3 * b) + cb * 128, 0, 0, b};
     }
-    __device__ void epilogue(int u, int row, uint32_t tm) const
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t tm, W&& wait) const
     {
         int64_t i, j;
         int rb, cb;
         decode(u, i, j, rb, cb);
-        float* dst = U32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128;
+        float* dst = U32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
         const bool first = (t == j);
-#pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
-            float v[16];
-            tc::tmem_ld16(tm + col, v);
-            if (first) st_f16x(dst + col, v);
-            else add_f16x(dst + col, v);
+        Row64 cur;
+        if (!first) row_load(cur, dst);
+        if (!wait()) return false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(tm + c0 + 32 * h, v);
+            if (first) row_store(dst, v, h);
+            else row_axpy(dst, cur, v, h, 1.f);
         }
+        return true;
     }
 };
 
@@ -538,18 +569,21 @@ struct OpLauum {
         return Seg{(int)(tri_index(t, i) * 3 * b) + rb * 128, 0, (int)(tri_index(t, j) * 3 * b) + cb * 128, 0,
                    q == 0 ? rb * 128 : 0, b};
     }
-    __device__ void epilogue(int u, int row, uint32_t tm) const
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t tm, W&& wait) const
     {
         int64_t i, j;
         int rb, cb;
         decode(u, i, j, rb, cb);
-        float* dst = Kinv32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128;
-#pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
-            float v[16];
-            tc::tmem_ld16(tm + col, v);
-            st_f16x(dst + col, v);
+        float* dst = Kinv32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
+        if (!wait()) return false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(tm + c0 + 32 * h, v);
+            row_store(dst, v, h);
         }
+        return true;
     }
 };
 
