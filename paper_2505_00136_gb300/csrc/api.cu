@@ -486,7 +486,7 @@ void gp_destroy(gp_t h)
     void* ptrs[] = {h->X, h->y, h->hyp, h->adam, h->L, h->Linv, h->beta, h->alpha, h->work,
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
-                    h->PA, h->D64, h->X64, h->r32, h->t32, h->w32, h->res, h->norms, h->R32, h->RP,
+                    h->PA, h->r32, h->t32, h->w32, h->res, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32, h->YP,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
                     h->dag_upd, h->dag_fin};
@@ -560,8 +560,6 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(dev_alloc(h, &h->Linv32, h->T * bb));
         TRY(dev_alloc(h, &h->LinvP, 3 * h->T * bb));
         TRY(dev_alloc(h, &h->PA, 3 * (h->T > 1 ? h->T - 1 : 1) * bb));
-        TRY(dev_alloc(h, &h->D64, bb));
-        TRY(dev_alloc(h, &h->X64, bb));
         TRY(dev_alloc(h, &h->r32, h->Np));
         TRY(dev_alloc(h, &h->t32, h->Np));
         TRY(dev_alloc(h, &h->w32, h->Np));

@@ -77,8 +77,6 @@ struct gp_handle {
     float* Linv32;            // T tiles: inverses of the diagonal factor tiles
     __nv_bfloat16* LinvP;     // T tiles x 3 planes of Linv32
     __nv_bfloat16* PA;        // (T-1) tiles x 3 planes: panel operand scratch
-    double* D64;              // b x b FP64 diagonal tile scratch
-    double* X64;              // b x b FP64 inverse scratch
     float *r32, *t32, *w32;   // Np FP32 vectors of the refinement solves
     double* res;              // Np FP64 residual
     double* norms;            // 2 FP64 norms

@@ -3,11 +3,12 @@
 //
 //  - K is assembled once in FP64 (kept for residuals) and in FP32 (working copy).
 //  - Tiled right-looking Cholesky (Fig. 1) on the FP32 copy: each diagonal tile
-//    is factored and inverted in FP64 (same kernel as the FP64 path), the panel
-//    TRSM (L_ik = A_ik Linv_kk^T) and the trailing SYRK/GEMM run as bf16x6
-//    products with FP32 accumulation.  Every finished off-diagonal tile of L is
-//    also kept as three BF16 planes, the operand format of later products.
-//  - log|K| comes from the FP64 diagonal factors.
+//    is factored and inverted in FP32 by one CTA (k_potrf32), the panel TRSM
+//    (L_ik = A_ik Linv_kk^T) and the trailing SYRK/GEMM run as bf16x6 products
+//    with FP32 accumulation on the tensor cores.  Every finished off-diagonal
+//    tile of L is also kept as three BF16 planes, the operand format of later
+//    products.
+//  - log|K| = 2 sum log L_jj, the logarithms taken and summed in FP64.
 //  - alpha = K^{-1} y by iterative refinement: FP32 triangular solves with the
 //    mixed factor, residual y - K alpha in FP64 against the FP64 K.
 //  - Prediction: the mean is K_{Z*,Z} alpha in FP64 (fused into the cross-
@@ -25,32 +26,213 @@ namespace gpk {
 constexpr int MB = 128;   // block edge of the split-BF16 products
 constexpr int NTH = 256;
 
-// ---------------------------------------------------------------- conversions
-__global__ void k_tile_up64(const float* src, double* dst, int64_t count)
+// ---------------------------------------------------------------- FP32 diagonal-tile factor
+// 64 x 64 FP32 block product for the diagonal tile: acc(r, c) += sum over k in
+// [kb, ke) of A(r, k) B(c, k), element (row, k) of a view at p[row*sr + k*sk].
+// 256 threads as 16 x 16, thread (tr, tc) owns rows tr + 16 i, columns tc + 16 j.
+struct SView {
+    const float* p;
+    int64_t sr, sk;
+};
+
+constexpr int SG_KC = 32;                     // k per shared-memory chunk
+constexpr int SG_FLOATS = 2 * SG_KC * 65;     // A and B chunks, k-major, padded
+
+__device__ __forceinline__ void sg_stage(const SView& v, int64_t k0, int64_t ke, float* dst)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
-         e += (int64_t)gridDim.x * blockDim.x)
-        dst[e] = (double)src[e];
+    for (int e = threadIdx.x; e < 64 * SG_KC; e += NTH) {
+        int r, kk;
+        if (v.sk == 1) { r = e / SG_KC; kk = e % SG_KC; }
+        else           { kk = e / 64;   r = e % 64; }
+        dst[kk * 65 + r] = (k0 + kk < ke) ? __ldcg(v.p + (int64_t)r * v.sr + (k0 + kk) * v.sk) : 0.f;
+    }
 }
 
-// FP64 factor tile and its inverse back to FP32 (zero upper triangle) and to
-// the three-plane operand format of the inverse.
-__global__ void k_tile_down(const double* D, const double* X, float* A32, float* Linv32,
-                            __nv_bfloat16* LinvP, int64_t b)
+__device__ void sgemm64(float (&acc)[4][4], const SView& A, const SView& B, int64_t kb, int64_t ke, float* sm)
 {
-    const int64_t bb = b * b;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < bb;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e / b, c = e % b;
-        A32[e] = (c <= r) ? (float)D[e] : 0.f;
-        float xv = (c <= r) ? (float)X[e] : 0.f;
-        Linv32[e] = xv;
-        __nv_bfloat16 hi, mid, lo;
-        split3(xv, hi, mid, lo);
-        LinvP[e] = hi;
-        LinvP[bb + e] = mid;
-        LinvP[2 * bb + e] = lo;
+    float* As = sm;
+    float* Bs = sm + SG_KC * 65;
+    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+    for (int64_t k0 = kb; k0 < ke; k0 += SG_KC) {
+        __syncthreads();
+        sg_stage(A, k0, ke, As);
+        sg_stage(B, k0, ke, Bs);
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < SG_KC; ++kk) {
+            float a[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk * 65 + tr + 16 * i];
+                bv[i] = Bs[kk * 65 + tc + 16 * i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+        }
     }
+    __syncthreads();
+}
+
+template <class F>
+__device__ __forceinline__ void sacc_for_each(const float (&acc)[4][4], F&& f)
+{
+    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) f(tr + 16 * i, tc + 16 * j, acc[i][j]);
+}
+
+__device__ __forceinline__ void sacc_zero(float (&acc)[4][4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+}
+
+constexpr int POTRF32_SMEM = (2 * 64 * 65 + SG_FLOATS) * 4;
+
+// Cholesky factor and inverse of one b x b diagonal tile in FP32 (one CTA):
+// A (lower tile, in place) = L_kk with a zero upper triangle, X = L_kk^{-1},
+// XP = the three BF16 planes of X, *logdet_slot = sum of log L_jj in FP64.
+// 64-blocks inside the tile, left-looking: A_pp -= A_p,<p A_p,<p^T, unblocked
+// factor and inverse of the 64-block, panel A_rp = (A_rp - A_r,<p A_p,<p^T)
+// L_pp^{-T}; then X_rq = -X_rr sum_{t=q}^{r-1} L_rt X_tq.  A non-positive
+// pivot records its global row in *info.
+__global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat16* XP, int64_t b, int64_t row0,
+                                                 double* logdet_slot, unsigned long long* info)
+{
+    extern __shared__ float fsm[];
+    float* S = fsm;
+    float* Iv = S + 64 * 65;
+    float* gsm = Iv + 64 * 65;
+    __shared__ double logacc;
+    __shared__ float rcp;
+    __shared__ int fail;
+    if (failed(info)) return;
+    const int tid = threadIdx.x;
+    const int P = (int)(b / 64);
+    if (tid == 0) { logacc = 0.0; fail = 0; }
+    for (int p = 0; p < P; ++p) {
+        float* App = A + (int64_t)p * 64 * b + p * 64;
+        if (p > 0) {
+            float acc[4][4];
+            sacc_zero(acc);
+            const SView va{A + (int64_t)p * 64 * b, b, 1};
+            sgemm64(acc, va, va, 0, (int64_t)p * 64, gsm);
+            sacc_for_each(acc, [&](int r, int c, float v) {
+                float* q = App + (int64_t)r * b + c;
+                *q = __ldcg(q) - v;
+            });
+        }
+        __syncthreads();
+        for (int e = tid; e < 64 * 64; e += NTH) {
+            const int r = e >> 6, c = e & 63;
+            S[r * 65 + c] = (c <= r) ? __ldcg(App + (int64_t)r * b + c) : 0.f;
+            Iv[r * 65 + c] = 0.f;
+        }
+        __syncthreads();
+        for (int j = 0; j < 64; ++j) {
+            if (tid == 0) {
+                const float piv = S[j * 65 + j];
+                if (piv > 0.f) {
+                    const float sq = sqrtf(piv);
+                    S[j * 65 + j] = sq;
+                    rcp = 1.f / sq;
+                } else {
+                    fail = 1;
+                    atomicMin(info, (unsigned long long)(row0 + p * 64 + j));
+                }
+            }
+            __syncthreads();
+            if (fail) return;
+            const float dinv = rcp;
+            for (int r = j + 1 + tid; r < 64; r += NTH) S[r * 65 + j] *= dinv;
+            __syncthreads();
+            const int ty = tid >> 4, tx = tid & 15;
+            for (int r = j + 1 + ty; r < 64; r += 16) {
+                const float lr = S[r * 65 + j];
+                for (int c = j + 1 + tx; c <= r; c += 16) S[r * 65 + c] -= lr * S[c * 65 + j];
+            }
+            __syncthreads();
+        }
+        if (tid < 32) {
+            double lg = log((double)S[tid * 65 + tid]) + log((double)S[(tid + 32) * 65 + tid + 32]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
+            if (tid == 0) logacc += lg;
+        }
+        {   // inverse of the 64-block factor, row by row, 4 threads per column
+            const int c = tid >> 2, q = tid & 3;
+            for (int r = 0; r < 64; ++r) {
+                float sum = 0.f;
+                if (c < r)
+                    for (int t = c + q; t < r; t += 4) sum = fmaf(S[r * 65 + t], Iv[t * 65 + c], sum);
+                sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+                sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+                if (q == 0 && c <= r) Iv[r * 65 + c] = ((r == c) ? 1.f : -sum) / S[r * 65 + r];
+                __syncthreads();
+            }
+        }
+        float* Xpp = X + (int64_t)p * 64 * b + p * 64;
+        for (int e = tid; e < 64 * 64; e += NTH) {
+            const int r = e >> 6, c = e & 63;
+            App[(int64_t)r * b + c] = S[r * 65 + c];
+            Xpp[(int64_t)r * b + c] = Iv[r * 65 + c];
+        }
+        __syncthreads();
+        for (int r = p + 1; r < P; ++r) {
+            float* Arp = A + (int64_t)r * 64 * b + p * 64;
+            if (p > 0) {
+                float acc[4][4];
+                sacc_zero(acc);
+                sgemm64(acc, SView{A + (int64_t)r * 64 * b, b, 1}, SView{A + (int64_t)p * 64 * b, b, 1}, 0,
+                        (int64_t)p * 64, gsm);
+                sacc_for_each(acc, [&](int rr, int c, float v) {
+                    float* q = Arp + (int64_t)rr * b + c;
+                    *q = __ldcg(q) - v;
+                });
+            }
+            float acc[4][4];
+            sacc_zero(acc);
+            sgemm64(acc, SView{Arp, b, 1}, SView{Xpp, b, 1}, 0, 64, gsm);
+            sacc_for_each(acc, [&](int rr, int c, float v) { Arp[(int64_t)rr * b + c] = v; });
+        }
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < b * b; e += NTH) {
+        const int64_t r = e / b, c = e % b;
+        if (c > r) {
+            A[e] = 0.f;
+            X[e] = 0.f;
+        }
+    }
+    for (int r = 1; r < P; ++r) {
+        for (int q = 0; q < r; ++q) {
+            float* Xrq = X + (int64_t)r * 64 * b + q * 64;
+            float acc[4][4];
+            sacc_zero(acc);
+            sgemm64(acc, SView{A + (int64_t)r * 64 * b, b, 1}, SView{X + q * 64, 1, b}, (int64_t)q * 64,
+                    (int64_t)r * 64, gsm);
+            sacc_for_each(acc, [&](int rr, int c, float v) { Xrq[(int64_t)rr * b + c] = v; });
+            sacc_zero(acc);
+            sgemm64(acc, SView{X + (int64_t)r * 64 * b + r * 64, b, 1}, SView{Xrq, 1, b}, 0, 64, gsm);
+            sacc_for_each(acc, [&](int rr, int c, float v) { Xrq[(int64_t)rr * b + c] = -v; });
+        }
+    }
+    __syncthreads();
+    const int64_t bb = b * b;
+    for (int64_t e = tid; e < bb; e += NTH) {
+        __nv_bfloat16 hi, mid, lo;
+        split3(__ldcg(X + e), hi, mid, lo);
+        XP[e] = hi;
+        XP[bb + e] = mid;
+        XP[2 * bb + e] = lo;
+    }
+    if (tid == 0) *logdet_slot = logacc;
 }
 
 // Planes of the panel tiles A32_(i,k), i = k+1..T-1, into PA (one slot per tile).
@@ -490,6 +672,7 @@ static void ensure_attrs_mixed()
     cudaGetDevice(&dev);
     if (done_dev == dev) return;
     cudaFuncSetAttribute(k_mbdiag, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
+    cudaFuncSetAttribute(k_potrf32, cudaFuncAttributeMaxDynamicSharedMemorySize, POTRF32_SMEM);
     cudaFuncSetAttribute(k_mbupd, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
     done_dev = dev;
 }
@@ -499,11 +682,8 @@ bool factor_mixed(gp_t h)
     ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, bb = b * b;
     for (int64_t k = 0; k < T; ++k) {
-        float* Akk = h->A32 + tri_index(k, k) * bb;
-        GPK_LAUNCH(h, GP_PH_POTRF, k_tile_up64, grid_for(bb), NTH, 0, (const float*)Akk, h->D64, bb);
-        potrf_diag_launch(h, h->D64, h->X64, b, k * b, h->logdet_part + k);
-        GPK_LAUNCH(h, GP_PH_POTRF, k_tile_down, grid_for(bb), NTH, 0, (const double*)h->D64,
-                   (const double*)h->X64, Akk, h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b);
+        GPK_LAUNCH(h, GP_PH_POTRF, k_potrf32, 1, NTH, POTRF32_SMEM, h->A32 + tri_index(k, k) * bb,
+                   h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b, k * b, h->logdet_part + k, h->info);
         if (k + 1 < T) {
             const unsigned tt = (unsigned)(T - k - 1);
             GPK_LAUNCH(h, GP_PH_TRSM, k_split_panel, dim3((unsigned)grid_for(bb) / 4 + 1, tt), NTH, 0,
