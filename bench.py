@@ -257,8 +257,9 @@ def run_ours(args):
     K = args.steps
     ph = {k: v[0] / K for k, v in prof.items()}
     factor_ms = ph["assemble"] + ph["potrf"] + ph["trsm"] + ph["update"] + ph["solve"] + ph["refine"]
-    # predict+variance = factor + cross-covariance + multi-RHS solve + reductions of the predict call
-    predict_var_ms = factor_ms + ph["cross"] + ph["vsolve"]
+    # predict+variance = factor + cross-covariance + multi-RHS solve (+ the variance correction's
+    # backward solve, exact product and second forward solve on the mixed path)
+    predict_var_ms = factor_ms + ph["cross"] + ph["vsolve"] + ph["bsolve"] + ph["ozaki"] + ph["rsolve"]
     grad_ms = factor_ms + ph["trtri"] + ph["lauum"] + ph["adjoint"] + ph["adam"]
     ms_per_step = total_ms / K
     vals = torch.tensor([predict_var_ms, grad_ms, ms_per_step], dtype=torch.float64, device=dev)
@@ -275,7 +276,7 @@ def run_ours(args):
         peak_note = "of measured bf16 burst" if "bf16_tflops" in pk else "of fallback bf16"
         tensor_flops = 6.0 * upd_flops_per_launch      # six BF16 plane products per FP32-accurate product
         achieved = tensor_flops / (upd_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": "k_mupdate (trailing SYRK/GEMM, split-BF16 x6, mma.sync bf16)",
+        roof = {"bound": "tensor", "kernel": "k_tgemm<OpUpdate> (trailing SYRK/GEMM, split-BF16 x6, tcgen05)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_note": peak_note, "traffic": None,
                 "algorithmic_flops_per_launch": upd_flops_per_launch,

@@ -166,7 +166,10 @@ typedef enum {
     GP_PH_LAUUM,        /* K^{-1} = L^{-T} L^{-1} tiles */
     GP_PH_ADJOINT,      /* fused dK/dtheta reduction */
     GP_PH_ADAM,
-    GP_PH_REFINE,       /* mixed path: FP64 residuals and corrections */
+    GP_PH_REFINE,       /* mixed path: FP64 residuals and corrections of alpha */
+    GP_PH_BSOLVE,       /* mixed variance correction: x0^T = W L~^{-1} (backward multi-RHS solve) */
+    GP_PH_OZAKI,        /* mixed variance correction: digit slices and the exact product K x0 */
+    GP_PH_RSOLVE,       /* mixed variance correction: L~^{-1} r0 (forward multi-RHS solve) */
     GP_PH_OTHER,
     GP_NPHASE
 } gp_phase;

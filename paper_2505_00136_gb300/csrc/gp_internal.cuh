@@ -183,6 +183,8 @@ bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov);
 bool tg_trtri_fin(gp_t h, int64_t t);
 bool tg_trtri_acc(gp_t h, int64_t t);
 bool tg_lauum(gp_t h);
+bool tg_bdiag(gp_t h, int64_t ldm, int64_t i);                  // Y_i = S_i Linv_ii (NN form)
+bool tg_bupd(gp_t h, int64_t ldm, int64_t i);                   // S_j -= Y_i L_ij, j < i (NN form)
 constexpr int GP_OZ_SLICES = 6;                                // digit slices per operand (kernels_mixed.cu)
 }  // namespace gpk
 

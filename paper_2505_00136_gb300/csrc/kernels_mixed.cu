@@ -17,7 +17,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
-#include "bgemm_block.cuh"
+#include "split_bf16.cuh"
 #include "gp_internal.cuh"
 #include "se_common.cuh"
 
@@ -526,51 +526,6 @@ __global__ void k_split_row(const float* U32, __nv_bfloat16* PA, int64_t b, int6
 // at most 1024 of them are exact in FP32, and the partial sums are carried in
 // double-FP32.
 
-// Backward solve, diagonal step: Y_i = S_i Linv_ii (NN form: Linv_ii[t][c],
-// nonzero for t >= c).  Writes Y_i in FP32 over S_i (column block i of R32)
-// and its planes into YP (3 x ldm x b).
-__global__ __launch_bounds__(NTH) void k_mbdiag(const __nv_bfloat16* RP, const __nv_bfloat16* LinvP,
-                                                __nv_bfloat16* YP, float* R32, int64_t ldr, int64_t ldm,
-                                                int64_t b, int64_t i)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int cb = blockIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.y * MB, bb = b * b, ps = ldm * b;
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{RP + m0 * b, b, ps, MB};
-    BView vb{LinvP + i * 3 * bb + (int64_t)cb * MB, b, bb, MB};
-    bgemm_acc_nn(acc, va, vb, (int64_t)cb * MB, b, (__nv_bfloat16*)smem_raw);
-    __nv_bfloat16* yp = YP + m0 * b + cb * MB;
-    float* dst = R32 + m0 * ldr + i * b + cb * MB;
-    bacc_for_each(acc, [&](int r, int c, float v) {
-        dst[(int64_t)r * ldr + c] = v;
-        int64_t o = (int64_t)r * b + c;
-        __nv_bfloat16 hi, mid, lo;
-        split3(v, hi, mid, lo);
-        yp[o] = hi;
-        yp[ps + o] = mid;
-        yp[2 * ps + o] = lo;
-    });
-}
-
-// Backward solve, update: S_j -= Y_i L_ij for j < i (NN form: L_ij[t][c]).
-__global__ __launch_bounds__(NTH) void k_mbupd(float* R32, int64_t ldr, const __nv_bfloat16* YP,
-                                               const __nv_bfloat16* LP, int64_t ldm, int64_t b, int64_t i)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Q = (int)(b / MB);
-    const int64_t j = blockIdx.x / Q;
-    const int cb = blockIdx.x % Q;
-    const int64_t m0 = (int64_t)blockIdx.y * MB, bb = b * b, ps = ldm * b;
-    BAcc acc;
-    bacc_zero(acc);
-    BView va{YP + m0 * b, b, ps, MB};
-    BView vb{LP + tri_index(i, j) * 3 * bb + (int64_t)cb * MB, b, bb, MB};
-    bgemm_acc_nn(acc, va, vb, 0, b, (__nv_bfloat16*)smem_raw);
-    float* dst = R32 + m0 * ldr + j * b + cb * MB;
-    bacc_for_each(acc, [&](int r, int c, float v) { dst[(int64_t)r * ldr + c] -= v; });
-}
 
 constexpr int OZ_S = GP_OZ_SLICES;   // digit slices per operand (7 bits each)
 
@@ -671,9 +626,7 @@ static void ensure_attrs_mixed()
     int dev = 0;
     cudaGetDevice(&dev);
     if (done_dev == dev) return;
-    cudaFuncSetAttribute(k_mbdiag, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
     cudaFuncSetAttribute(k_potrf32, cudaFuncAttributeMaxDynamicSharedMemorySize, POTRF32_SMEM);
-    cudaFuncSetAttribute(k_mbupd, cudaFuncAttributeMaxDynamicSharedMemorySize, BN_SMEM_BYTES);
     done_dev = dev;
 }
 
@@ -789,27 +742,22 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 {
     ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, Np = h->Np;
-    const int Q = (int)(b / MB);
-    const unsigned gm = (unsigned)(ldm / MB);
     // x0^T = W L~^{-1}: backward sweep over tile columns, in place over R32
     for (int64_t i = T - 1; i >= 0; --i) {
-        GPK_LAUNCH(h, GP_PH_REFINE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np, i, b, ldm,
+        GPK_LAUNCH(h, GP_PH_BSOLVE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np, i, b, ldm,
                    h->RP);
-        GPK_LAUNCH(h, GP_PH_REFINE, k_mbdiag, dim3((unsigned)Q, gm), NTH, BN_SMEM_BYTES, (const __nv_bfloat16*)h->RP,
-                   (const __nv_bfloat16*)h->LinvP, h->YP, h->R32, Np, ldm, b, i);
-        if (i > 0)
-            GPK_LAUNCH(h, GP_PH_REFINE, k_mbupd, dim3((unsigned)(i * Q), gm), NTH, BN_SMEM_BYTES, h->R32, Np,
-                       (const __nv_bfloat16*)h->YP, (const __nv_bfloat16*)h->LP, ldm, b, i);
+        if (!tg_bdiag(h, ldm, i)) return false;
+        if (i > 0 && !tg_bupd(h, ldm, i)) return false;
     }
-    GPK_LAUNCH(h, GP_PH_REFINE, k_yslices, (unsigned)ldm, NTH, 0, (const float*)h->R32, Np, h->YS, ldm * Np, h->mu);
+    GPK_LAUNCH(h, GP_PH_OZAKI, k_yslices, (unsigned)ldm, NTH, 0, (const float*)h->R32, Np, h->YS, ldm * Np, h->mu);
     if (!h->ks_valid) {
-        GPK_LAUNCH(h, GP_PH_REFINE, k_kslices, grid_for(Np * Np), NTH, 0, (const double*)h->L, b, Np,
+        GPK_LAUNCH(h, GP_PH_OZAKI, k_kslices, grid_for(Np * Np), NTH, 0, (const double*)h->L, b, Np,
                    (const GpHyperDev*)h->hyp, h->KS, Np * Np, h->kappa);
         h->ks_valid = true;
     }
     const int64_t nbn = Np / MB;
     if (!ozaki_tc(h, m, ldm)) return false;
-    if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_REFINE)) return false;
+    if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_RSOLVE)) return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, nbn,
                (const double*)h->vpart2, Np / 64, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
                h->outv);

@@ -318,7 +318,7 @@ bool ozaki_tc(gp_t h, int64_t m, int64_t ldm)
     int* err = tc_error_dev();
     if (!err) return false;
     const int64_t nbn = Np / 128;
-    GPK_LAUNCH(h, GP_PH_REFINE, k_ozaki_tc, (unsigned)(nbn * (ldm / 128)), OZT_THREADS, OZT_SMEM, mY, mK, ldm, Np,
+    GPK_LAUNCH(h, GP_PH_OZAKI, k_ozaki_tc, (unsigned)(nbn * (ldm / 128)), OZT_THREADS, OZT_SMEM, mY, mK, ldm, Np,
                (const double*)h->mu, (const double*)h->kappa, (const double*)h->R64, (const float*)h->R32, h->Rr32,
                h->qpart, m, h->n, h->oz_lmax, err);
     return true;

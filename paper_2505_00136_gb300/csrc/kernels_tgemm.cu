@@ -23,7 +23,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
-#include "bgemm_block.cuh"
+#include "split_bf16.cuh"
 #include "gp_internal.cuh"
 #include "se_common.cuh"
 #include "tc_common.cuh"
@@ -38,9 +38,13 @@ constexpr int TG_STAGE_BYTES = 6 * tc::TILE_BYTES;
 constexpr int TG_BAR_OFF = TG_STAGES * TG_STAGE_BYTES;
 constexpr int TG_SMEM = 1024 + TG_BAR_OFF + 256;
 constexpr uint32_t TG_IDESC = tc::idesc_bf16(128, 128);
+constexpr uint32_t TG_IDESC_BMN = tc::idesc_bf16_bmn(128, 128);
 
 // Operand coordinates of one k-segment: plane p of A is the 128-row box at
-// map row a_row + p * a_ps, k-columns a_x + [k0, k1); likewise B.
+// map row a_row + p * a_ps, k-columns a_x + [k0, k1); likewise B when B is
+// K-major.  An Op with kBMN set gives B as K x N with n contiguous (the NN
+// form): plane p holds k rows b_row + p * b_ps + [k0, k1), n columns b_x +
+// [0, 128), loaded as two 64 x 64 boxes.
 struct Seg {
     int a_row, a_x, b_row, b_x, k0, k1;
 };
@@ -113,8 +117,15 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                         for (int p = 0; p < 3; ++p) {
                             tc::tma_load_2d(dst + p * tc::TILE_BYTES, &mapA, sg.a_x + k, sg.a_row + p * op.a_ps,
                                             full(st));
-                            tc::tma_load_2d(dst + (3 + p) * tc::TILE_BYTES, &mapB, sg.b_x + k,
-                                            sg.b_row + p * op.b_ps, full(st));
+                            if (Op::kBMN) {
+                                const uint32_t db = dst + (3 + p) * tc::TILE_BYTES;
+                                tc::tma_load_2d(db, &mapB, sg.b_x, sg.b_row + p * op.b_ps + k, full(st));
+                                tc::tma_load_2d(db + tc::TILE_BYTES / 2, &mapB, sg.b_x + 64, sg.b_row + p * op.b_ps + k,
+                                                full(st));
+                            } else {
+                                tc::tma_load_2d(dst + (3 + p) * tc::TILE_BYTES, &mapB, sg.b_x + k,
+                                                sg.b_row + p * op.b_ps, full(st));
+                            }
                         }
                     }
                 }
@@ -154,9 +165,10 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                             for (int qa = 0; qa < 3; ++qa)
 #pragma unroll
                                 for (int qb = 0; qa + qb < 3; ++qb) {
+                                    const uint32_t sb = s0 + (3 + qb) * tc::TILE_BYTES;
                                     tc::mma_bf16(d, tc::desc_sw128(s0 + qa * tc::TILE_BYTES + kk * 32),
-                                                 tc::desc_sw128(s0 + (3 + qb) * tc::TILE_BYTES + kk * 32), TG_IDESC,
-                                                 first ? 0u : 1u);
+                                                 Op::kBMN ? tc::desc_mn_sw128(sb + kk * 2048) : tc::desc_sw128(sb + kk * 32),
+                                                 Op::kBMN ? TG_IDESC_BMN : TG_IDESC, first ? 0u : 1u);
                                     first = false;
                                 }
                         tc::mma_commit(empty(st));
@@ -252,6 +264,7 @@ __device__ __forceinline__ void planes32(__nv_bfloat16* p, int64_t ps, const flo
 // Cholesky panel: L_ik = A_ik Linv_kk^T, k-range of Linv_kk's lower 128-block
 // column; FP32 L_ik over A_ik and its planes into LP.
 struct OpPanel {
+    static constexpr bool kBMN = false;
     float* A32;
     __nv_bfloat16* LP;
     int b, k, tt, Q;
@@ -288,6 +301,7 @@ struct OpPanel {
 
 // Trailing update: A_ij -= L_ik L_jk^T for k < j <= i (lower 128-blocks of diagonal tiles).
 struct OpUpdate {
+    static constexpr bool kBMN = false;
     float* A32;
     int b, k, tt, Q;
     int a_ps, b_ps;
@@ -341,6 +355,7 @@ struct OpUpdate {
 // Forward multi-RHS solve, diagonal step: W_j = R_j Linv_jj^T; planes of W_j
 // into WP, FP32 W_j over R_j, FP64 row sums of W_j^2 into vpart.
 struct OpDiagW {
+    static constexpr bool kBMN = false;
     __nv_bfloat16* WP;
     float* Wout;
     double* vpart;
@@ -380,6 +395,7 @@ struct OpDiagW {
 
 // Forward multi-RHS solve, update: R_i -= W_j L_ij^T for all tiles i > j.
 struct OpUpdW {
+    static constexpr bool kBMN = false;
     float* R32;
     int64_t ldr;
     int b, j, T, Q, nmb;
@@ -417,6 +433,7 @@ struct OpUpdW {
 
 // Full covariance: cov (m x m, FP64, holding K_{Z*,Z*}) -= W W^T on lower 128-blocks, mirrored.
 struct OpSyrkCov {
+    static constexpr bool kBMN = false;
     double* cov;
     int64_t m;
     int kdim, nb;
@@ -458,6 +475,7 @@ struct OpSyrkCov {
 
 // Inverse for the gradient, finishing step: Z_tj = -U_tj Linv_tt^T (j < t), planes into ZP.
 struct OpTrtriFin {
+    static constexpr bool kBMN = false;
     __nv_bfloat16* ZP;
     int b, t, Q;
     int a_ps, b_ps;
@@ -489,6 +507,7 @@ struct OpTrtriFin {
 
 // Inverse, accumulation step: U_ij (+)= Z_tj L_it^T for i > t >= j; t == j overwrites.
 struct OpTrtriAcc {
+    static constexpr bool kBMN = false;
     float* U32;
     int b, t, T, Q;
     int a_ps, b_ps;
@@ -535,6 +554,7 @@ struct OpTrtriAcc {
 
 // Inverse, K^{-1}_ij = sum_{t >= i} Z_ti Z_tj^T on lower tiles (FP32 out).
 struct OpLauum {
+    static constexpr bool kBMN = false;
     float* Kinv32;
     int b, T, Q;
     int a_ps, b_ps;
@@ -587,6 +607,83 @@ struct OpLauum {
     }
 };
 
+// Backward multi-RHS solve of the variance correction (x0^T = W L~^{-1}, NN form).
+// Diagonal step: Y_i = S_i Linv_ii, Linv_ii[t][c] nonzero for t >= c, so the
+// k-range of output column block cb starts at cb * 128.  FP32 Y_i over S_i
+// (column block i of R32) and its planes into YP (3 x ldm x b).
+struct OpBDiag {
+    static constexpr bool kBMN = true;
+    float* R32;
+    __nv_bfloat16* YP;
+    int64_t ldr, ldm;
+    int b, i, Q, nmb;
+    int a_ps, b_ps;
+    __device__ bool skip_all() const { return false; }
+    __device__ int units() const { return Q * nmb; }
+    __device__ bool active(int) const { return true; }
+    __device__ int nseg(int) const { return 1; }
+    __device__ Seg seg(int u, int) const
+    {
+        const int cb = u % Q, mb = u / Q;
+        return Seg{mb * 128, 0, i * 3 * b, cb * 128, cb * 128, b};
+    }
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
+    {
+        const int cb = u % Q, mb = u / Q;
+        const int64_t r = (int64_t)mb * 128 + row;
+        float* dst = R32 + r * ldr + (int64_t)i * b + cb * 128 + c0;
+        __nv_bfloat16* yp = YP + r * b + cb * 128 + c0;
+        if (!wait()) return false;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(t + c0 + 32 * h, v);
+            row_store(dst, v, h);
+            planes32(yp + 32 * h, ldm * b, v);
+        }
+        return true;
+    }
+};
+
+// Backward solve, update: S_j -= Y_i L_ij for all j < i (NN form, L_ij[t][c]).
+struct OpBUpd {
+    static constexpr bool kBMN = true;
+    float* R32;
+    int64_t ldr;
+    int b, i, Q, nmb;
+    int a_ps, b_ps;
+    __device__ bool skip_all() const { return false; }
+    __device__ int units() const { return i * Q * nmb; }
+    __device__ bool active(int) const { return true; }
+    __device__ int nseg(int) const { return 1; }
+    __device__ Seg seg(int u, int) const
+    {
+        const int nx = i * Q, x = u % nx, mb = u / nx;
+        const int64_t j = x / Q;
+        const int cb = x % Q;
+        return Seg{mb * 128, 0, (int)(tri_index(i, j) * 3 * b), cb * 128, 0, b};
+    }
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
+    {
+        const int nx = i * Q, x = u % nx, mb = u / nx;
+        const int64_t j = x / Q;
+        const int cb = x % Q;
+        float* dst = R32 + ((int64_t)mb * 128 + row) * ldr + j * b + cb * 128 + c0;
+        Row64 cur;
+        row_load(cur, dst);
+        if (!wait()) return false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(t + c0 + 32 * h, v);
+            row_axpy(dst, cur, v, h, -1.f);
+        }
+        return true;
+    }
+};
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn_tg()
 {
@@ -602,13 +699,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn_tg()
     return fn;
 }
 
-bool map_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols)
+// Row-major BF16 matrix (rows x cols, row stride cols) as 64-column boxes of
+// box_rows rows, 128-byte swizzle: 128 rows for K-major operands, 64 k rows
+// for an MN-major B.
+bool map_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols, int box_rows = 128)
 {
     auto enc = encode_fn_tg();
     if (!enc || ((uintptr_t)p & 15) || (cols * 2) % 16 || rows >= (1ll << 31)) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {64, 128}, es[2] = {1, 1};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows}, es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(p), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -714,6 +814,25 @@ bool tg_lauum(gp_t h)
     if (!map_tiles(&mA, h->ZP, 3 * (int64_t)T * (T + 1) / 2 * b, b)) return false;
     OpLauum op{h->Kinv32, b, T, Q, b, b};
     return launch(h, GP_PH_LAUUM, mA, mA, op, T * (T + 1) / 2 * Q * Q);
+}
+
+bool tg_bdiag(gp_t h, int64_t ldm, int64_t i)
+{
+    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->RP, 3 * ldm, b) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, 64)) return false;
+    OpBDiag op{h->R32, h->YP, h->Np, ldm, b, (int)i, Q, (int)(ldm / 128), (int)ldm, b};
+    return launch(h, GP_PH_BSOLVE, mA, mB, op, Q * (int)(ldm / 128));
+}
+
+bool tg_bupd(gp_t h, int64_t ldm, int64_t i)
+{
+    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->YP, 3 * ldm, b) || !map_tiles(&mB, h->LP, 3 * (int64_t)T * (T + 1) / 2 * b, b, 64))
+        return false;
+    OpBUpd op{h->R32, h->Np, b, (int)i, Q, (int)(ldm / 128), (int)ldm, b};
+    return launch(h, GP_PH_BSOLVE, mA, mB, op, (int)i * Q * (int)(ldm / 128));
 }
 
 }  // namespace gpk

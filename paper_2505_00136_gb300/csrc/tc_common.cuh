@@ -86,11 +86,28 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
     return d;
 }
 
+// Shared-memory matrix descriptor for an MN-major operand (n contiguous):
+// 64-element n groups of 128 bytes per k row, 128-byte swizzle, loaded as
+// 64 x 64 TMA boxes; 8-k-row groups 1024 B apart, 64-column groups 8 KB apart.
+// A 16-element k step advances the start address by 16 rows (2048 bytes).
+__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(8192 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+// As idesc_bf16 with B MN-major (n contiguous in shared memory).
+__host__ __device__ constexpr uint32_t idesc_bf16_bmn(int M, int N) { return idesc_bf16(M, N) | (1u << 16); }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum)
 {
