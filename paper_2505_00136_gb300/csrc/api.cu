@@ -128,7 +128,7 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     dev_free(h, &h->YP, 3 * old * h->b);
     dev_free(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * old * h->Np);
     dev_free(h, &h->mu, old);
-    dev_free(h, &h->qpart, 2 * old * (h->Np / (2 * TB)));
+    dev_free(h, &h->qpart, 2 * old * (h->Np / 64));
     dev_free(h, &h->vpart2, old * (h->Np / 64));
     h->m_cap = 0;
     gp_status s;
@@ -140,7 +140,7 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
         if ((s = dev_alloc(h, &h->YP, 3 * ldm * h->b)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * ldm * h->Np)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->mu, ldm)) != GP_OK) return s;
-        if ((s = dev_alloc(h, &h->qpart, 2 * ldm * (h->Np / (2 * TB)))) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->qpart, 2 * ldm * (h->Np / 64))) != GP_OK) return s;   // one slot per 64 columns
         if ((s = dev_alloc(h, &h->vpart2, ldm * (h->Np / 64))) != GP_OK) return s;   // one slot per 64 columns
     }
     if ((s = dev_alloc(h, &h->RP, 3 * ldm * h->b)) != GP_OK) return s;
@@ -522,7 +522,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     h->d = d;
     h->oz_lmax = 7;
     h->dag_stall = -1;
-    if (const char* e = getenv("GPRAT_OZAKI_LMAX")) {   // accuracy/speed study knob: 6 or 7
+    if (const char* e = getenv("GPRAT_OZAKI_LMAX")) {   // accuracy/speed study knob: 5, 6 or 7
         int v = atoi(e);
         if (v >= 4 && v <= 2 * gpk::GP_OZ_SLICES) h->oz_lmax = v;
     }

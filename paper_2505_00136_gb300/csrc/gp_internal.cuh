@@ -92,7 +92,7 @@ struct gp_handle {
     __nv_bfloat16* KS;        // digit slices of K, OZ_S x Np x Np (allocated on first use)
     double* mu;               // m_cap row scales of x0^T
     double* kappa;            // scale of K
-    double* qpart;            // 2 x (Np/128) x m_cap partial sums
+    double* qpart;            // 2 x (Np/64) x m_cap partial sums (one per 64 columns)
     double* vpart2;           // (Np/64) x m_cap partial sums of ||L~^{-1} r0||^2
     bool ks_valid;            // KS matches the current K
     int oz_lmax;              // digit pairs (s, u) with s + u <= oz_lmax enter the exact product
@@ -186,6 +186,7 @@ bool tg_lauum(gp_t h);
 bool tg_bdiag(gp_t h, int64_t ldm, int64_t i);                  // Y_i = S_i Linv_ii (NN form)
 bool tg_bupd(gp_t h, int64_t ldm, int64_t i);                   // S_j -= Y_i L_ij, j < i (NN form)
 constexpr int GP_OZ_SLICES = 6;                                // digit slices per operand (kernels_mixed.cu)
+constexpr int GP_OZ_BITS = 7;                                   // bits per signed digit: |d| <= 2^7, exact in BF16
 }  // namespace gpk
 
 #define GP_CUDA_OK(call)                                                   \

@@ -23,7 +23,6 @@
 
 namespace gpk {
 
-constexpr int MB = 128;   // block edge of the split-BF16 products
 constexpr int NTH = 256;
 
 // ---------------------------------------------------------------- FP32 diagonal-tile factor
@@ -522,12 +521,14 @@ __global__ void k_split_row(const float* U32, __nv_bfloat16* PA, int64_t b, int6
 // error is third order in the factor's error).  Only K x0 must be accurate to
 // FP64 level; it is formed from exactly-accumulated BF16 digit slices (Ozaki
 // et al. 2012): each row of Y = x0^T and all of K are scaled by a power of two
-// and split into 7-bit integer digits, every digit product is exact, sums of
-// at most 1024 of them are exact in FP32, and the partial sums are carried in
+// and split into 7-bit signed integer digits (|d| <= 128, exact in BF16),
+// every digit product is exact (|d e| <= 2^14), sums of at most 1024 of them
+// are exact in FP32 (<= 2^24), and the partial sums are carried in
 // double-FP32.
 
 
-constexpr int OZ_S = GP_OZ_SLICES;   // digit slices per operand (7 bits each)
+constexpr int OZ_S = GP_OZ_SLICES;   // digit slices per operand
+constexpr int OZ_B = GP_OZ_BITS;     // bits per digit
 
 __device__ __forceinline__ double pow2_ceil(double x)   // smallest power of two >= x (x > 0)
 {
@@ -536,8 +537,25 @@ __device__ __forceinline__ double pow2_ceil(double x)   // smallest power of two
     return (f == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
 }
 
+// Balanced base-2^OZ_B digits of a in [-1, 1]: q = rint(a 2^(OZ_B OZ_S))
+// (exact in a 64-bit integer), d_s = q rounded to a multiple of
+// 2^(OZ_B (OZ_S - s)) and removed from q, most significant first, so that
+// a ~ sum_s d_s 2^{-OZ_B s} with |d_1| <= 2^OZ_B, |d_s| <= 2^(OZ_B - 1) for
+// s > 1, the error at most 2^{-OZ_B OZ_S - 1}.
+__device__ __forceinline__ void oz_digits(double a, __nv_bfloat16 (&d)[OZ_S])
+{
+    long long q = llrint(ldexp(a, OZ_B * OZ_S));
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+        const int sh = OZ_B * (OZ_S - 1 - s);
+        const long long dg = sh > 0 ? ((q + (1ll << (sh - 1))) >> sh) : q;
+        q -= dg * (1ll << sh);
+        d[s] = __float2bfloat16_rn((float)dg);
+    }
+}
+
 // Digits of each row of Y (R32, ldm x Np): mu[row] = power of two >= max |Y|,
-// YS[s][row][col] = s-th 7-bit rounded digit of Y / mu.  One CTA per row.
+// YS[s][row][col] = s-th digit of Y / mu.  One CTA per row.
 __global__ void k_yslices(const float* Y, int64_t Np, __nv_bfloat16* YS, int64_t ps, double* mu)
 {
     __shared__ float red[NTH];
@@ -555,34 +573,45 @@ __global__ void k_yslices(const float* Y, int64_t Np, __nv_bfloat16* YS, int64_t
     if (threadIdx.x == 0) mu[row] = m;
     const double inv = 1.0 / m;
     for (int64_t c = threadIdx.x; c < Np; c += NTH) {
-        double a = (double)y[c] * inv;
-        for (int s = 0; s < OZ_S; ++s) {
-            double dgt = rint(a * 128.0);
-            YS[s * ps + row * Np + c] = __float2bfloat16_rn((float)dgt);
-            a = a * 128.0 - dgt;
-        }
+        __nv_bfloat16 d[OZ_S];
+        oz_digits((double)y[c] * inv, d);
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) YS[s * ps + row * Np + c] = d[s];
     }
 }
 
 // Digits of the full symmetric K (from the lower FP64 tiles) scaled by
-// kappa = power of two >= max(nu + sigma^2, 1).
+// kappa = power of two >= max(nu + sigma^2, 1).  One CTA per 64 x 64 block of
+// K: the block at (max, min) of its block indices is read row-wise from the
+// lower tiles into shared memory and written out directly or transposed, so
+// both the reads and the digit writes are coalesced.
 __global__ void k_kslices(const double* K64, int64_t b, int64_t Np, const GpHyperDev* hyp, __nv_bfloat16* KS,
                           int64_t ps, double* kappa_out)
 {
+    __shared__ double tile[64][65];
     const double kappa = pow2_ceil(fmax(hyp->nu + hyp->s2, 1.0));
-    if (blockIdx.x == 0 && threadIdx.x == 0) *kappa_out = kappa;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *kappa_out = kappa;
     const double inv = 1.0 / kappa;
-    const int64_t total = Np * Np;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e / Np, c = e % Np;
-        int64_t rr = r >= c ? r : c, cc = r >= c ? c : r;
-        double a = K64[tri_index(rr / b, cc / b) * b * b + (rr % b) * b + (cc % b)] * inv;
-        for (int s = 0; s < OZ_S; ++s) {
-            double dgt = rint(a * 128.0);
-            KS[s * ps + e] = __float2bfloat16_rn((float)dgt);
-            a = a * 128.0 - dgt;
-        }
+    const int64_t R0 = (int64_t)blockIdx.y * 64, C0 = (int64_t)blockIdx.x * 64;
+    const int64_t LR = R0 >= C0 ? R0 : C0, LC = R0 >= C0 ? C0 : R0;   // lower block
+    const double* src = K64 + tri_index(LR / b, LC / b) * b * b + (LR % b) * b + (LC % b);
+    for (int e = threadIdx.x; e < 64 * 64; e += NTH) {
+        const int r = e >> 6, c = e & 63;
+        tile[r][c] = src[(int64_t)r * b + c];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * 64; e += NTH) {
+        const int r = e >> 6, c = e & 63;
+        // element (R0 + r, C0 + c) of the symmetric K, from the lower triangle
+        double v;
+        if (R0 > C0) v = tile[r][c];
+        else if (R0 < C0) v = tile[c][r];
+        else v = (c <= r) ? tile[r][c] : tile[c][r];
+        __nv_bfloat16 d[OZ_S];
+        oz_digits(v * inv, d);
+        const int64_t o = (R0 + r) * Np + C0 + c;
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) KS[s * ps + o] = d[s];
     }
 }
 
@@ -751,14 +780,13 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
     }
     GPK_LAUNCH(h, GP_PH_OZAKI, k_yslices, (unsigned)ldm, NTH, 0, (const float*)h->R32, Np, h->YS, ldm * Np, h->mu);
     if (!h->ks_valid) {
-        GPK_LAUNCH(h, GP_PH_OZAKI, k_kslices, grid_for(Np * Np), NTH, 0, (const double*)h->L, b, Np,
+        GPK_LAUNCH(h, GP_PH_OZAKI, k_kslices, dim3((unsigned)(Np / 64), (unsigned)(Np / 64)), NTH, 0, (const double*)h->L, b, Np,
                    (const GpHyperDev*)h->hyp, h->KS, Np * Np, h->kappa);
         h->ks_valid = true;
     }
-    const int64_t nbn = Np / MB;
     if (!ozaki_tc(h, m, ldm)) return false;
     if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_RSOLVE)) return false;
-    GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, nbn,
+    GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, Np / 64,
                (const double*)h->vpart2, Np / 64, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
                h->outv);
     return true;

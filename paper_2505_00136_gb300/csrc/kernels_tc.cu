@@ -2,21 +2,23 @@
 // accumulators in tensor memory, operands staged by TMA).
 //
 // k_ozaki_tc: C = Y K for the third-order variance correction, Y (test rows x
-// Np) and K (Np x Np, symmetric) each given as six BF16 digit slices of 7
-// bits, C = sum over kept digit pairs (s, u) of 2^{-7(s+u)} Y_s K_u.  Each
-// pair's product is summed exactly in FP32 over chunks of 1024 k (digit
-// products are below 2^14 in magnitude, so a chunk sum stays below 2^24), and
-// each chunk sum is added into a double-FP32 (hi + lo) running sum, which
-// carries about 48 bits.  The fused epilogue forms r0 = Kc - C and the row
-// sums of Kc Y and Y r0 (the terms k*^T x0 and x0^T r0 of the corrected
-// variance).
+// Np) and K (Np x Np, symmetric) each given as BF16 slices of signed
+// GP_OZ_BITS-bit digits (|d| <= 2^GP_OZ_BITS), C = sum over kept digit pairs
+// (s, u) of 2^{-GP_OZ_BITS (s+u)} Y_s K_u.  Each pair's product is summed
+// exactly in FP32 over chunks of 2^(24 - 2 GP_OZ_BITS) k (1024 for 7-bit
+// digits: a product is at most 2^(2 GP_OZ_BITS), so a chunk sum stays within
+// 2^24), and each chunk sum is added into a double-FP32
+// (hi + lo) running sum, which carries about 48 bits.  The fused epilogue
+// forms r0 = Kc - C and the partial row sums of Kc Y and Y r0 (the terms
+// k*^T x0 and x0^T r0 of the corrected variance).
 //
-// Roles (192 threads, one CTA per SM): warp 0 issues TMA loads into a
+// Roles (320 threads, one CTA per SM): warp 0 issues TMA loads into a
 // 6-stage ring of {Y tile, K tile} (32 KB per stage); warp 1 owns the 512
-// TMEM columns and issues the MMAs; warps 2-5 (one per TMEM lane quarter,
-// one output row per thread) flush chunk sums and run the epilogue.  TMEM
-// columns: two 128-column accumulators used alternately per chunk (the MMAs
-// of chunk c+1 run while chunk c is flushed), hi at 256, lo at 384.
+// TMEM columns and issues the MMAs; warps 2-9 (two per TMEM lane quarter,
+// one output row and 64 columns per thread) flush chunk sums and run the
+// epilogue.  TMEM columns: two 128-column accumulators used alternately per
+// chunk (the MMAs of chunk c+1 run while chunk c is flushed), hi at 256, lo
+// at 384.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -33,14 +35,15 @@ __device__ int g_tc_error;
 namespace {
 
 constexpr int OZT_STAGES = 6;
-constexpr int OZT_KCH = 16;                              // 64-k stages per exact chunk
-constexpr int OZT_THREADS = 192;
+constexpr int OZT_KCH = (1 << (24 - 2 * GP_OZ_BITS)) / 64;  // 64-k stages per exact chunk
+constexpr int OZT_THREADS = 320;
+constexpr int OZT_EPI_WARPS = 8;
 constexpr int OZT_STAGE_BYTES = 2 * tc::TILE_BYTES;
 constexpr int OZT_BAR_OFF = OZT_STAGES * OZT_STAGE_BYTES;
 constexpr int OZT_SMEM = 1024 + OZT_BAR_OFF + 256;
 constexpr uint32_t OZT_IDESC = tc::idesc_bf16(128, 128);
 
-// p-th kept digit pair (s, u), 1-based, s-major, s + u <= lmax, s, u <= 6.
+// p-th kept digit pair (s, u), 1-based, s-major, s + u <= lmax, s, u <= GP_OZ_SLICES.
 __device__ __forceinline__ void oz_pair_tc(int p, int lmax, int& s, int& u)
 {
     s = 1;
@@ -94,8 +97,8 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
         }
         tc::mbar_init(accf(0), 1);
         tc::mbar_init(accf(1), 1);
-        tc::mbar_init(acce(0), 4);
-        tc::mbar_init(acce(1), 4);
+        tc::mbar_init(acce(0), OZT_EPI_WARPS);
+        tc::mbar_init(acce(1), OZT_EPI_WARPS);
         tc::mbar_init(drain, 1);
         *abort = 0;
         tc::mbar_init_fence();
@@ -172,7 +175,7 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
             }
         }
     } else {
-        const int wq = warp & 3, row = wq * 32 + lane;
+        const int wq = warp & 3, row = wq * 32 + lane, c0 = ((warp - 2) >> 2) * 64;
         const uint32_t lrow = (uint32_t)(wq * 32) << 16;
         const uint32_t t_hi = tmem + lrow + 256, t_lo = tmem + lrow + 384;
         bool ok = true;
@@ -180,7 +183,7 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
         for (int p = 0; p < np && ok; ++p) {
             int s, u;
             oz_pair_tc(p, lmax, s, u);
-            const float scale = ldexpf(1.f, -7 * (s + u));
+            const float scale = ldexpf(1.f, -GP_OZ_BITS * (s + u));
             for (int k0 = 0; k0 < kst; k0 += OZT_KCH, ++c) {
                 const int a = c & 1;
                 ok = __all_sync(0xffffffffu, tc::mbar_wait(accf(a), (uint32_t)((c >> 1) & 1), abort, err));
@@ -188,7 +191,7 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
                 tc::fence_after();
                 const uint32_t t_acc = tmem + lrow + (uint32_t)(a * 128);
 #pragma unroll 1
-                for (int col = 0; col < 128; col += 16) {
+                for (int col = c0; col < c0 + 64; col += 16) {
                     float v[16], hi[16], lo[16];
                     tc::tmem_ld16(t_acc + col, v);
                     if (c == 0) {
@@ -219,7 +222,7 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
                 if (lane == 0) tc::mbar_arrive(acce(a));
             }
         }
-        // fused epilogue, one output row per thread
+        // fused epilogue, one output row and 64 columns per thread
         const int64_t gm = m0 + row;
         const bool live = ok && gm < m;
         const double sc = live ? mu[gm] * (*kappa_p) : 0.0;
@@ -228,7 +231,7 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
         const float* yrow = Y + gm * Np + n0;
         float* rr = Rr32 + gm * Np + n0;
 #pragma unroll 1
-        for (int col = 0; col < 128; col += 16) {
+        for (int col = c0; col < c0 + 64; col += 16) {
             float hi[16], lo[16];
             if (ok) {
                 tc::tmem_ld16(t_hi + col, hi);
@@ -252,8 +255,9 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
             }
         }
         if (!ok) s1 = s2 = __longlong_as_double(0x7ff8000000000000ll);
-        qpart[nb * ldm + gm] = s1;
-        qpart[(nbn + nb) * ldm + gm] = s2;
+        const int64_t nslot = Np / 64, slot = (n0 + c0) / 64;
+        qpart[slot * ldm + gm] = s1;
+        qpart[(nslot + slot) * ldm + gm] = s2;
     }
     tc::fence_before();
     __syncthreads();
