@@ -158,18 +158,26 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                             break;
                         }
                         tc::fence_after();
+                        // stage descriptors once; planes are TILE_BYTES apart (TILE_BYTES >> 4 in the address
+                        // field), a 16-k step adds 32 bytes (K-major) or 2048 bytes (MN-major B)
                         const uint32_t s0 = sbase + st * TG_STAGE_BYTES;
+                        const uint64_t da = tc::desc_sw128(s0);
+                        const uint64_t db = Op::kBMN ? tc::desc_mn_sw128(s0 + 3 * tc::TILE_BYTES)
+                                                     : tc::desc_sw128(s0 + 3 * tc::TILE_BYTES);
+                        constexpr uint64_t pl = (uint64_t)(tc::TILE_BYTES >> 4);
+                        constexpr uint64_t bstep = Op::kBMN ? (2048 >> 4) : 2;
+                        constexpr uint32_t idesc = Op::kBMN ? TG_IDESC_BMN : TG_IDESC;
+                        if (first) tc::mma_bf16(d, da, db, idesc, 0u);
+                        else tc::mma_bf16_acc(d, da, db, idesc);
+                        first = false;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
                             for (int qa = 0; qa < 3; ++qa)
 #pragma unroll
                                 for (int qb = 0; qa + qb < 3; ++qb) {
-                                    const uint32_t sb = s0 + (3 + qb) * tc::TILE_BYTES;
-                                    tc::mma_bf16(d, tc::desc_sw128(s0 + qa * tc::TILE_BYTES + kk * 32),
-                                                 Op::kBMN ? tc::desc_mn_sw128(sb + kk * 2048) : tc::desc_sw128(sb + kk * 32),
-                                                 Op::kBMN ? TG_IDESC_BMN : TG_IDESC, first ? 0u : 1u);
-                                    first = false;
+                                    if (kk == 0 && qa == 0 && qb == 0) continue;
+                                    tc::mma_bf16_acc(d, da + qa * pl + 2 * kk, db + qb * pl + bstep * kk, idesc);
                                 }
                         tc::mma_commit(empty(st));
                     }

@@ -75,6 +75,32 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y) : "memory");
 }
 
+// As tma_load_2d, the box written to the same shared-memory offset in every
+// CTA of the cluster named in mask, each of whose mbarrier at offset mbar
+// receives the completed bytes.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar,
+                                               uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;\n"
+        ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "h"(mask) : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+
+// All threads of all CTAs in the cluster; orders earlier shared-memory writes
+// (barrier initialisation included) before everything after it.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
 {
@@ -116,11 +142,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db
                  ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(accum));
 }
 
+// As mma_bf16 with the accumulator always read (enable-input-d true): no
+// predicate set-up on the issue path.
+__device__ __forceinline__ void mma_bf16_acc(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc)
+{
+    asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(da), "l"(db), "r"(idesc));
+}
+
 // The mbarrier completes a phase once all earlier MMAs of this thread are done.
 __device__ __forceinline__ void mma_commit(uint32_t mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                  ::"r"(mbar) : "memory");
+}
+
+// As mma_commit, arriving on the mbarrier at offset mbar in every CTA of the cluster named in mask.
+__device__ __forceinline__ void mma_commit_mc(uint32_t mbar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n"
+                 ::"r"(mbar), "h"(mask) : "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
