@@ -138,6 +138,7 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
         if (lane == 0) {
             int gs = 0;
             bool ok = true;
+            const uint64_t pol = tc::policy_evict_last();
             for (int kc = 0; kc < nkc && ok; ++kc)
             for (int p = 0; p < np && ok; ++p) {
                 int s, u;
@@ -154,10 +155,10 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
                         const int kx = k * OZT_KS + 64 * j;
-                        tc::tma_load_2d_mc(dst + j * tc::TILE_BYTES + cn * (tc::TILE_BYTES / 2), &mapY, kx,
-                                           ya + 64 * cn, full(st), mask_y);
-                        tc::tma_load_2d_mc(dst + (2 + j) * tc::TILE_BYTES + cm * (tc::TILE_BYTES / 2), &mapK, kx,
-                                           kb + 64 * cm, full(st), mask_k);
+                        tc::tma_load_2d_mc_hint(dst + j * tc::TILE_BYTES + cn * (tc::TILE_BYTES / 2), &mapY, kx,
+                                                ya + 64 * cn, full(st), mask_y, pol);
+                        tc::tma_load_2d_mc_hint(dst + (2 + j) * tc::TILE_BYTES + cm * (tc::TILE_BYTES / 2), &mapK, kx,
+                                                kb + 64 * cm, full(st), mask_k, pol);
                     }
                 }
             }

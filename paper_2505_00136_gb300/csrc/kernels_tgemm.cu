@@ -9,8 +9,9 @@
 // epilogue.
 //
 // Roles (320 threads, one CTA per SM, grid = min(units, SMs)): warp 0 issues
-// the TMA loads of a 64-k stage (three A planes and three B planes, six
-// 128 x 64 tiles, 96 KB) into a two-stage ring; warp 1 owns 256 TMEM columns
+// the TMA loads of a 32-k stage (three A planes and three B planes, six
+// 128 x 32 tiles with 64-byte swizzle, 48 KB) into a four-stage ring; warp 1
+// owns 256 TMEM columns
 // (two 128-column accumulators, alternating between units) and issues the
 // six plane MMAs per 16-k step; warps 2-9 run the epilogue of unit c while
 // the MMAs of unit c+1 proceed: two warps per TMEM lane quarter, each thread
@@ -33,8 +34,10 @@ namespace {
 
 constexpr int TG_THREADS = 320;
 constexpr int TG_EPI_WARPS = 8;
-constexpr int TG_STAGES = 2;
-constexpr int TG_STAGE_BYTES = 6 * tc::TILE_BYTES;
+constexpr int TG_STAGES = 4;
+constexpr int TG_KS = 32;                          // k per stage
+constexpr int TG_PLANE = 128 * TG_KS * 2;          // bytes of one 128-row plane tile
+constexpr int TG_STAGE_BYTES = 6 * TG_PLANE;
 constexpr int TG_BAR_OFF = TG_STAGES * TG_STAGE_BYTES;
 constexpr int TG_SMEM = 1024 + TG_BAR_OFF + 256;
 constexpr uint32_t TG_IDESC = tc::idesc_bf16(128, 128);
@@ -44,7 +47,8 @@ constexpr uint32_t TG_IDESC_BMN = tc::idesc_bf16_bmn(128, 128);
 // map row a_row + p * a_ps, k-columns a_x + [k0, k1); likewise B when B is
 // K-major.  An Op with kBMN set gives B as K x N with n contiguous (the NN
 // form): plane p holds k rows b_row + p * b_ps + [k0, k1), n columns b_x +
-// [0, 128), loaded as two 64 x 64 boxes.
+// [0, 128), loaded as two 64-column boxes per stage.  k0 and k1 are
+// multiples of 32.
 struct Seg {
     int a_row, a_x, b_row, b_x, k0, k1;
 };
@@ -100,12 +104,13 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
         if (lane == 0) {
             int it = 0;
             bool ok = true;
+            const uint64_t pol = tc::policy_evict_last();
             for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
                 if (!op.active(u)) continue;
                 const int ns = op.nseg(u);
                 for (int q = 0; q < ns && ok; ++q) {
                     const Seg sg = op.seg(u, q);
-                    for (int k = sg.k0; k < sg.k1; k += 64, ++it) {
+                    for (int k = sg.k0; k < sg.k1; k += TG_KS, ++it) {
                         const int st = it % TG_STAGES, use = it / TG_STAGES;
                         if (use > 0 && !tc::mbar_wait(empty(st), (uint32_t)((use - 1) & 1), abort, err)) {
                             ok = false;
@@ -115,16 +120,16 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                         tc::mbar_expect_tx(full(st), TG_STAGE_BYTES);
 #pragma unroll
                         for (int p = 0; p < 3; ++p) {
-                            tc::tma_load_2d(dst + p * tc::TILE_BYTES, &mapA, sg.a_x + k, sg.a_row + p * op.a_ps,
-                                            full(st));
+                            tc::tma_load_2d_hint(dst + p * TG_PLANE, &mapA, sg.a_x + k, sg.a_row + p * op.a_ps, full(st),
+                                                 pol);
                             if (Op::kBMN) {
-                                const uint32_t db = dst + (3 + p) * tc::TILE_BYTES;
-                                tc::tma_load_2d(db, &mapB, sg.b_x, sg.b_row + p * op.b_ps + k, full(st));
-                                tc::tma_load_2d(db + tc::TILE_BYTES / 2, &mapB, sg.b_x + 64, sg.b_row + p * op.b_ps + k,
-                                                full(st));
+                                const uint32_t db = dst + (3 + p) * TG_PLANE;
+                                tc::tma_load_2d_hint(db, &mapB, sg.b_x, sg.b_row + p * op.b_ps + k, full(st), pol);
+                                tc::tma_load_2d_hint(db + TG_PLANE / 2, &mapB, sg.b_x + 64, sg.b_row + p * op.b_ps + k,
+                                                     full(st), pol);
                             } else {
-                                tc::tma_load_2d(dst + (3 + p) * tc::TILE_BYTES, &mapB, sg.b_x + k,
-                                                sg.b_row + p * op.b_ps, full(st));
+                                tc::tma_load_2d_hint(dst + (3 + p) * TG_PLANE, &mapB, sg.b_x + k,
+                                                     sg.b_row + p * op.b_ps, full(st), pol);
                             }
                         }
                     }
@@ -151,27 +156,27 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                 const int ns = op.nseg(u);
                 for (int q = 0; q < ns && ok; ++q) {
                     const Seg sg = op.seg(u, q);
-                    for (int k = sg.k0; k < sg.k1; k += 64, ++it) {
+                    for (int k = sg.k0; k < sg.k1; k += TG_KS, ++it) {
                         const int st = it % TG_STAGES;
                         if (!tc::mbar_wait(full(st), (uint32_t)((it / TG_STAGES) & 1), abort, err)) {
                             ok = false;
                             break;
                         }
                         tc::fence_after();
-                        // stage descriptors once; planes are TILE_BYTES apart (TILE_BYTES >> 4 in the address
+                        // stage descriptors once; planes are TG_PLANE apart (TG_PLANE >> 4 in the address
                         // field), a 16-k step adds 32 bytes (K-major) or 2048 bytes (MN-major B)
                         const uint32_t s0 = sbase + st * TG_STAGE_BYTES;
-                        const uint64_t da = tc::desc_sw128(s0);
-                        const uint64_t db = Op::kBMN ? tc::desc_mn_sw128(s0 + 3 * tc::TILE_BYTES)
-                                                     : tc::desc_sw128(s0 + 3 * tc::TILE_BYTES);
-                        constexpr uint64_t pl = (uint64_t)(tc::TILE_BYTES >> 4);
+                        const uint64_t da = tc::desc_sw64(s0);
+                        const uint64_t db = Op::kBMN ? tc::desc_mn32_sw128(s0 + 3 * TG_PLANE)
+                                                     : tc::desc_sw64(s0 + 3 * TG_PLANE);
+                        constexpr uint64_t pl = (uint64_t)(TG_PLANE >> 4);
                         constexpr uint64_t bstep = Op::kBMN ? (2048 >> 4) : 2;
                         constexpr uint32_t idesc = Op::kBMN ? TG_IDESC_BMN : TG_IDESC;
                         if (first) tc::mma_bf16(d, da, db, idesc, 0u);
                         else tc::mma_bf16_acc(d, da, db, idesc);
                         first = false;
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
+                        for (int kk = 0; kk < TG_KS / 16; ++kk)
 #pragma unroll
                             for (int qa = 0; qa < 3; ++qa)
 #pragma unroll
@@ -225,16 +230,19 @@ struct Row64 {
     float4 x[16];
 };
 
+// Epilogue traffic is read or written once: streaming (evict-first) accesses
+// keep it from displacing the operand tiles in L2.
 __device__ __forceinline__ void row_load(Row64& r, const float* p)
 {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) r.x[q] = __ldcg((const float4*)p + q);
+    for (int q = 0; q < 16; ++q) r.x[q] = __ldcs((const float4*)p + q);
 }
 
 __device__ __forceinline__ void row_store(float* p, const float (&v)[32], int h)
 {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) ((float4*)p)[8 * h + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int q = 0; q < 8; ++q)
+        __stcs((float4*)p + 8 * h + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
 }
 
 // p[32h + e] = base[32h + e] + sign * v[e] for the 32 values of half h.
@@ -247,7 +255,7 @@ __device__ __forceinline__ void row_axpy(float* p, const Row64& base, const floa
         x.y += sign * v[4 * q + 1];
         x.z += sign * v[4 * q + 2];
         x.w += sign * v[4 * q + 3];
-        ((float4*)p)[8 * h + q] = x;
+        __stcs((float4*)p + 8 * h + q, x);
     }
 }
 
@@ -707,19 +715,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn_tg()
     return fn;
 }
 
-// Row-major BF16 matrix (rows x cols, row stride cols) as 64-column boxes of
-// box_rows rows, 128-byte swizzle: 128 rows for K-major operands, 64 k rows
-// for an MN-major B.
-bool map_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols, int box_rows = 128)
+// Row-major BF16 matrix (rows x cols, row stride cols) as TMA boxes: K-major
+// operands as {32 k, 128 rows} with 64-byte swizzle (mn = false), an MN-major
+// B as {64 n, 32 k rows} with 128-byte swizzle (mn = true).
+bool map_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols, bool mn = false)
 {
     auto enc = encode_fn_tg();
     if (!enc || ((uintptr_t)p & 15) || (cols * 2) % 16 || rows >= (1ll << 31)) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)box_rows}, es[2] = {1, 1};
+    cuuint32_t box[2] = {mn ? 64u : (cuuint32_t)TG_KS, mn ? (cuuint32_t)TG_KS : 128u}, es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(p), dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_INTERLEAVE_NONE, mn ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int g_num_sms = 0;
@@ -828,7 +836,7 @@ bool tg_bdiag(gp_t h, int64_t ldm, int64_t i)
 {
     const int b = (int)h->b, T = (int)h->T, Q = b / 128;
     CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->RP, 3 * ldm, b) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, 64)) return false;
+    if (!map_tiles(&mA, h->RP, 3 * ldm, b) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, true)) return false;
     OpBDiag op{h->R32, h->YP, h->Np, ldm, b, (int)i, Q, (int)(ldm / 128), (int)ldm, b};
     return launch(h, GP_PH_BSOLVE, mA, mB, op, Q * (int)(ldm / 128));
 }
@@ -837,7 +845,7 @@ bool tg_bupd(gp_t h, int64_t ldm, int64_t i)
 {
     const int b = (int)h->b, T = (int)h->T, Q = b / 128;
     CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->YP, 3 * ldm, b) || !map_tiles(&mB, h->LP, 3 * (int64_t)T * (T + 1) / 2 * b, b, 64))
+    if (!map_tiles(&mA, h->YP, 3 * ldm, b) || !map_tiles(&mB, h->LP, 3 * (int64_t)T * (T + 1) / 2 * b, b, true))
         return false;
     OpBUpd op{h->R32, h->Np, b, (int)i, Q, (int)(ldm / 128), (int)ldm, b};
     return launch(h, GP_PH_BSOLVE, mA, mB, op, (int)i * Q * (int)(ldm / 128));

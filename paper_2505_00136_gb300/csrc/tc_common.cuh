@@ -75,6 +75,25 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y) : "memory");
 }
 
+// L2 policy that keeps lines resident in preference to others (operand tiles
+// reused by many CTAs, while epilogue traffic streams through).
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+
+// As tma_load_2d with an L2 cache policy.
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar,
+                                                 uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4}], [%2], %5;\n"
+        ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "l"(policy) : "memory");
+}
+
 // As tma_load_2d, the box written to the same shared-memory offset in every
 // CTA of the cluster named in mask, each of whose mbarrier at offset mbar
 // receives the completed bytes.
@@ -85,6 +104,16 @@ __device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* 
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
         " [%0], [%1, {%3, %4}], [%2], %5;\n"
         ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "h"(mask) : "memory");
+}
+
+// As tma_load_2d_mc with an L2 cache policy.
+__device__ __forceinline__ void tma_load_2d_mc_hint(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar,
+                                                    uint16_t mask, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint"
+        " [%0], [%1, {%3, %4}], [%2], %5, %6;\n"
+        ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "h"(mask), "l"(policy) : "memory");
 }
 
 __device__ __forceinline__ uint32_t cluster_rank()
@@ -120,6 +149,30 @@ __device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr)
 {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
     d |= (uint64_t)(8192 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// K-major, 64-byte swizzle (32-element k rows of 64 bytes, 8-row groups 512 B
+// apart), as loaded by a {32, rows} TMA box; a 16-k step adds 32 bytes.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+// MN-major operand of 32 k rows per 64-column box (4 KB boxes, the second
+// 64 columns 4 KB on), 128-byte swizzle; a 16-k step adds 2048 bytes.
+__device__ __forceinline__ uint64_t desc_mn32_sw128(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(4096 >> 4) << 16;
     d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
