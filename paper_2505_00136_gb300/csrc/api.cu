@@ -304,11 +304,13 @@ gp_status factor_mixed_refined(gp_t h)
     if (s != GP_OK) return s;
     if ((s = read_info(h)) != GP_OK) return s;
     gpk::refine_start(h, h->y, h->alpha);
+    if ((s = check_launch(h)) != GP_OK) return s;
     double prev = INFINITY, nrm[2];
     int it = 0;
     while (it < h->opt.refine_max_iter) {
         gpk::refine_step(h, h->y, h->alpha, h->res, h->norms);
         ++it;
+        if ((s = check_launch(h)) != GP_OK) return s;
         if ((s = cuda_status(h, cudaMemcpyAsync(nrm, h->norms, sizeof(nrm), cudaMemcpyDeviceToHost, h->st))) != GP_OK)
             return s;
         if ((s = sync(h)) != GP_OK) return s;
@@ -318,6 +320,7 @@ gp_status factor_mixed_refined(gp_t h)
         prev = rel;
     }
     h->refine_iters = it;
+    if ((s = tc_status(h)) != GP_OK) return s;   // bounded waits of the persistent solves
     gpk::nlml_mixed(h);
     return check_launch(h);
 }
@@ -486,7 +489,7 @@ void gp_destroy(gp_t h)
     void* ptrs[] = {h->X, h->y, h->hyp, h->adam, h->L, h->Linv, h->beta, h->alpha, h->work,
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
-                    h->PA, h->r32, h->t32, h->w32, h->res, h->norms, h->R32, h->RP,
+                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32, h->YP,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
                     h->dag_upd, h->dag_fin};
@@ -563,6 +566,8 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(dev_alloc(h, &h->r32, h->Np));
         TRY(dev_alloc(h, &h->t32, h->Np));
         TRY(dev_alloc(h, &h->w32, h->Np));
+        TRY(dev_alloc(h, &h->solve_flags, 2));
+        TRY(cuda_status(h, cudaMemset(h->solve_flags, 0, 2 * sizeof(int))));
         TRY(dev_alloc(h, &h->res, h->Np));
         TRY(dev_alloc(h, &h->norms, 2));
         TRY(dev_alloc(h, &h->kappa, 1));

@@ -97,6 +97,7 @@ struct gp_handle {
     bool ks_valid;            // KS matches the current K
     int oz_lmax;              // digit pairs (s, u) with s + u <= oz_lmax enter the exact product
     bool tc_pending;          // a tensor-core kernel ran since its timeout word was last read
+    int* solve_flags;         // grid barrier of the persistent FP32 solve: arrival count, generation
     __nv_bfloat16* ZP;        // T(T+1)/2 tiles x 3 planes of (L^{-1})^T tiles (gradient)
     float* U32;               // T(T+1)/2 tiles: TRTRI accumulators (gradient)
     float* Kinv32;            // T(T+1)/2 tiles: K^{-1} lower (gradient)

@@ -251,65 +251,149 @@ __global__ void k_split_panel(const float* A32, __nv_bfloat16* PA, int64_t b, in
     }
 }
 
-// ---------------------------------------------------------------- FP32 single-RHS solves
-__global__ __launch_bounds__(NTH) void k_tri_apply32(const float* Linv, int64_t b, int64_t j, const float* w,
-                                                     float* out, int upper)
+// One cooperative launch per solve, every CTA on every step: out = L~^{-1} in
+// (upper = 0) or out = L~^{-T} in (upper = 1), FP32 throughout.  Lower, for
+// t = 0 .. T-1: (A) out_t = Linv_tt (in_t - s_t), the rows of the b x b
+// product spread over all warps; (B) s_i += L_it out_t for every i > t, each
+// of the (T-t-1) b rows owned by one warp (deterministic).  Upper, for
+// t = T-1 .. 0: (A) out_t = Linv_tt^T (in_t - s_t) by four-column groups;
+// (B) s_j += L_tj^T out_t for every j < t, four-column groups over warps.
+// s (Np floats) holds the partial sums; in_t - s_t is formed inside (A).
+// Phases are separated by a grid barrier (arrival counter and generation
+// word, bounded wait); a timeout sets *err and the kernel leaves, the caller
+// reports it.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err,
+                                             int* okb)
 {
-    const float* Xj = Linv + j * b * b;
-    const float* wj = w + j * b;
-    float* oj = out + j * b;
-    if (!upper) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < b; r += (int64_t)gridDim.x * 8) {
-            float s = 0.f;
-            for (int64_t t = lane; t <= r; t += 32) s = fmaf(Xj[r * b + t], wj[t], s);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) oj[r] = s;
-        }
-    } else {
-        for (int64_t c = (int64_t)blockIdx.x * NTH + threadIdx.x; c < b; c += (int64_t)gridDim.x * NTH) {
-            float s = 0.f;
-            for (int64_t t = c; t < b; ++t) s = fmaf(Xj[t * b + c], wj[t], s);
-            oj[c] = s;
-        }
-    }
-}
-
-__global__ __launch_bounds__(NTH) void k_gemv_lower32(const float* Lt, int64_t b, int64_t j, int64_t T,
-                                                      const float* x, float* w)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t rows = (T - j - 1) * b;
-    const float* xj = x + j * b;
-    for (int64_t R = (int64_t)blockIdx.x * 8 + warp; R < rows; R += (int64_t)gridDim.x * 8) {
-        int64_t i = j + 1 + R / b, r = R % b;
-        const float* row = Lt + tri_index(i, j) * b * b + r * b;
-        float s = 0.f;
-        for (int64_t t = lane; t < b; t += 32) s = fmaf(row[t], xj[t], s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) w[i * b + r] -= s;
-    }
-}
-
-__global__ __launch_bounds__(NTH) void k_gemv_upper32(const float* Lt, int64_t b, int64_t j, const float* x,
-                                                      float* w)
-{
-    __shared__ float red[4][64];
-    const int c = threadIdx.x & 63, q = threadIdx.x >> 6;
-    const int64_t cols = j * b;
-    const int64_t C = (int64_t)blockIdx.x * 64 + c;
-    const float* xj = x + j * b;
-    float s = 0.f;
-    if (C < cols) {
-        int64_t i = C / b, cc = C % b;
-        const float* tile = Lt + tri_index(j, i) * b * b;
-        for (int64_t r = q; r < b; r += 4) s = fmaf(tile[r * b + cc], xj[r], s);
-    }
-    red[q][c] = s;
+    __threadfence();
     __syncthreads();
-    if (q == 0 && C < cols) w[C] -= red[0][c] + red[1][c] + red[2][c] + red[3][c];
+    if (threadIdx.x == 0) {
+        unsigned g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(g) : "l"(gen) : "memory");
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            *count = 0;
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(gen), "r"(g + 1) : "memory");
+        } else {
+            const long long t0 = clock64();
+            while (true) {
+                unsigned v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(gen) : "memory");
+                if (v != g) break;
+                if (clock64() - t0 > 4000000000ll) {
+                    atomicExch(err, 1);
+                    *okb = 0;
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return *okb != 0;
+}
+
+// Dot product of a row (b floats, 16-byte aligned) with x - z (z may be
+// null) over one warp.
+__device__ __forceinline__ float warp_row_dot(const float* row, const float* x, const float* z, int64_t b, int lane)
+{
+    float sum = 0.f;
+    for (int64_t c = 4 * lane; c < b; c += 128) {
+        const float4 v = __ldcs((const float4*)(row + c));
+        float4 w = __ldcg((const float4*)(x + c));
+        if (z) {
+            const float4 u = __ldcg((const float4*)(z + c));
+            w.x -= u.x;
+            w.y -= u.y;
+            w.z -= u.z;
+            w.w -= u.w;
+        }
+        sum += v.x * w.x + v.y * w.y + v.z * w.z + v.w * w.w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    return sum;
+}
+
+// Four columns c4 .. c4+3 of M^T (x - z) (M b x b row-major, z may be null)
+// over one warp: lanes take rows lane, lane + 32, ...
+__device__ __forceinline__ float4 warp_col4_dot(const float* M, const float* x, const float* z, int64_t b, int64_t c4,
+                                                int lane)
+{
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+    for (int64_t r = lane; r < b; r += 32) {
+        const float4 v = __ldcs((const float4*)(M + r * b + c4));
+        const float xr = __ldcg(x + r) - (z ? __ldcg(z + r) : 0.f);
+        s.x = fmaf(v.x, xr, s.x);
+        s.y = fmaf(v.y, xr, s.y);
+        s.z = fmaf(v.z, xr, s.z);
+        s.w = fmaf(v.w, xr, s.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+        s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
+    }
+    return s;
+}
+
+__global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* Linv, int64_t b, int64_t T,
+                                                  const float* in, float* out, float* sbuf, int upper, unsigned* bar,
+                                                  int* err)
+{
+    __shared__ int okb;
+    if (threadIdx.x == 0) okb = 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (NTH / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (NTH / 32) + (threadIdx.x >> 5);
+    const int64_t Np = T * b;
+    for (int64_t e = (int64_t)blockIdx.x * NTH + threadIdx.x; e < Np; e += (int64_t)gridDim.x * NTH) sbuf[e] = 0.f;
+    if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
+    for (int64_t q = 0; q < T; ++q) {
+        const int64_t t = upper ? T - 1 - q : q;
+        // (A) out_t = Linv_tt (in_t - s_t), or the transpose
+        const float* X = Linv + t * b * b;
+        if (!upper) {
+            for (int64_t r = gw; r < b; r += nw) {
+                const float v = warp_row_dot(X + r * b, in + t * b, sbuf + t * b, b, lane);
+                if (lane == 0) out[t * b + r] = v;
+            }
+        } else {
+            for (int64_t c4 = 4 * gw; c4 < b; c4 += 4 * nw) {
+                const float4 v = warp_col4_dot(X, in + t * b, sbuf + t * b, b, c4, lane);
+                if (lane == 0) *(float4*)(out + t * b + c4) = v;
+            }
+        }
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
+        // (B) partial sums of the blocks still to solve
+        const float* xt = out + t * b;
+        if (!upper) {
+            const int64_t rows = (T - t - 1) * b;
+            for (int64_t R = gw; R < rows; R += nw) {
+                const int64_t i = t + 1 + R / b, r = R % b;
+                const float v = warp_row_dot(Lt + tri_index(i, t) * b * b + r * b, xt, nullptr, b, lane);
+                if (lane == 0) sbuf[i * b + r] += v;
+            }
+        } else {
+            const int64_t quads = t * (b / 4);
+            for (int64_t Q = gw; Q < quads; Q += nw) {
+                const int64_t j = Q / (b / 4), c4 = 4 * (Q % (b / 4));
+                const float4 v = warp_col4_dot(Lt + tri_index(t, j) * b * b, xt, nullptr, b, c4, lane);
+                if (lane == 0) {
+                    float4* p = (float4*)(sbuf + j * b + c4);
+                    float4 o = __ldcg(p);
+                    o.x += v.x;
+                    o.y += v.y;
+                    o.z += v.z;
+                    o.w += v.w;
+                    *p = o;
+                }
+            }
+        }
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
+    }
 }
 
 // ---------------------------------------------------------------- FP64 residual r = y - K x
@@ -679,26 +763,32 @@ bool factor_mixed(gp_t h)
 // out32 = L~^{-1} in32 (lower) or L~^{-T} in32 (upper), FP32 throughout.
 static void solve32(gp_t h, const float* in32, float* out32, bool upper)
 {
-    const int64_t T = h->T, b = h->b;
-    cudaMemcpyAsync(h->w32, in32, h->Np * sizeof(float), cudaMemcpyDeviceToDevice, h->st);
-    if (!upper) {
-        const unsigned g_apply = (unsigned)((b + 7) / 8 < 64 ? (b + 7) / 8 : 64);
-        for (int64_t j = 0; j < T; ++j) {
-            GPK_LAUNCH(h, GP_PH_SOLVE, k_tri_apply32, g_apply, NTH, 0, (const float*)h->Linv32, b, j,
-                       (const float*)h->w32, out32, 0);
-            if (j + 1 < T)
-                GPK_LAUNCH(h, GP_PH_SOLVE, k_gemv_lower32, grid_for((T - j - 1) * b, 8), NTH, 0,
-                           (const float*)h->A32, b, j, T, (const float*)out32, h->w32);
-        }
-    } else {
-        for (int64_t j = T - 1; j >= 0; --j) {
-            GPK_LAUNCH(h, GP_PH_SOLVE, k_tri_apply32, (unsigned)((b + NTH - 1) / NTH), NTH, 0,
-                       (const float*)h->Linv32, b, j, (const float*)h->w32, out32, 1);
-            if (j > 0)
-                GPK_LAUNCH(h, GP_PH_SOLVE, k_gemv_upper32, (unsigned)((j * b + 63) / 64), NTH, 0,
-                           (const float*)h->A32, b, j, (const float*)out32, h->w32);
-        }
+    static int grid_dev = -1, grid_blocks = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (grid_dev != dev) {   // every CTA resident at once: the blocks wait on one another
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve32p, NTH, 0);
+        grid_blocks = sms * (per < 2 ? per : 2);
+        grid_dev = dev;
     }
+    int64_t bb = h->b, TT = h->T;
+    int up = upper ? 1 : 0;
+    const float* Lt = h->A32;
+    const float* Li = h->Linv32;
+    float* sbuf = h->w32;
+    unsigned* bar = (unsigned*)h->solve_flags;
+    int* err = tc_error_dev();
+    void* args[] = {(void*)&Lt, (void*)&Li, (void*)&bb, (void*)&TT, (void*)&in32, (void*)&out32, (void*)&sbuf,
+                    (void*)&up, (void*)&bar, (void*)&err};
+    cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), h->st);   // fresh barrier words, whatever a failed solve left
+    const bool p_ = h->prof_on && prof_begin(h, GP_PH_SOLVE);
+    // a failed launch leaves its error for the caller's check of the last launch error
+    cudaLaunchCooperativeKernel((const void*)k_solve32p, dim3((unsigned)grid_blocks), dim3(NTH), args, 0, h->st);
+    h->launches++;
+    if (p_) prof_end(h);
+    h->tc_pending = true;
 }
 
 // One correction sweep: d = L~^{-T} L~^{-1} r32 (FP32), x += d.
