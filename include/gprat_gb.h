@@ -168,8 +168,9 @@ typedef enum {
     GP_PH_ADAM,
     GP_PH_REFINE,       /* mixed path: FP64 residuals and corrections of alpha */
     GP_PH_BSOLVE,       /* mixed variance correction: x0^T = W L~^{-1} (backward multi-RHS solve) */
-    GP_PH_OZAKI,        /* mixed variance correction: digit slices and the exact product K x0 */
+    GP_PH_OZAKI,        /* mixed variance correction: the exact digit-pair product K x0 */
     GP_PH_RSOLVE,       /* mixed variance correction: L~^{-1} r0 (forward multi-RHS solve) */
+    GP_PH_SLICES,       /* mixed variance correction: digit slices of x0 and K */
     GP_PH_OTHER,
     GP_NPHASE
 } gp_phase;

@@ -125,7 +125,6 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     dev_free(h, &h->outv, old);
     dev_free(h, &h->R64, old * h->Np);
     dev_free(h, &h->Rr32, old * h->Np);
-    dev_free(h, &h->YP, 3 * old * h->b);
     dev_free(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * old * h->Np);
     dev_free(h, &h->mu, old);
     dev_free(h, &h->qpart, 2 * old * (h->Np / 64));
@@ -137,7 +136,6 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     if (h->opt.var_correction) {
         if ((s = dev_alloc(h, &h->R64, ldm * h->Np)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->Rr32, ldm * h->Np)) != GP_OK) return s;
-        if ((s = dev_alloc(h, &h->YP, 3 * ldm * h->b)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * ldm * h->Np)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->mu, ldm)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->qpart, 2 * ldm * (h->Np / 64))) != GP_OK) return s;   // one slot per 64 columns
@@ -490,7 +488,7 @@ void gp_destroy(gp_t h)
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
                     h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->norms, h->R32, h->RP,
-                    h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32, h->YP,
+                    h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
                     h->dag_upd, h->dag_fin};
     for (void* p : ptrs)

@@ -87,7 +87,6 @@ struct gp_handle {
     // variance correction (GP_MIXED)
     double* R64;              // m_cap x Np: FP64 K_{Z*,Z}
     float* Rr32;              // m_cap x Np: r0 = K_{Z*,Z} - x0^T K
-    __nv_bfloat16* YP;        // 3 x m_cap x b planes (backward solve)
     __nv_bfloat16* YS;        // digit slices of x0^T, OZ_S x m_cap x Np
     __nv_bfloat16* KS;        // digit slices of K, OZ_S x Np x Np (allocated on first use)
     double* mu;               // m_cap row scales of x0^T
@@ -179,13 +178,13 @@ int* tc_error_dev();                                            // device addres
 bool tg_panel(gp_t h, int64_t k);
 bool tg_update(gp_t h, int64_t k);
 bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j);
-bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int64_t j);
+bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni);   // R_i -= sum W_j L_ij^T
 bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov);
 bool tg_trtri_fin(gp_t h, int64_t t);
 bool tg_trtri_acc(gp_t h, int64_t t);
 bool tg_lauum(gp_t h);
 bool tg_bdiag(gp_t h, int64_t ldm, int64_t i);                  // Y_i = S_i Linv_ii (NN form)
-bool tg_bupd(gp_t h, int64_t ldm, int64_t i);                   // S_j -= Y_i L_ij, j < i (NN form)
+bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj);   // S_j -= sum Y_i L_ij (NN form)
 constexpr int GP_OZ_SLICES = 6;                                // digit slices per operand (kernels_mixed.cu)
 constexpr int GP_OZ_BITS = 7;                                   // bits per signed digit: |d| <= 2^7, exact in BF16
 }  // namespace gpk

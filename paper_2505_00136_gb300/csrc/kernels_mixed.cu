@@ -829,13 +829,24 @@ void nlml_mixed(gp_t h)
 
 // Forward multi-RHS solve W = R L~^{-T} in place over R (ldm x Np, FP32): W
 // planes into WP, FP32 W over R, FP64 row sums of W^2 into vpart.
+// Multi-RHS sweeps update the trailing right-hand side once per block of
+// SWEEP_BLOCK tile columns (each block step one k-segment per column), so the
+// FP32 right-hand side is read and written T / SWEEP_BLOCK times, not T.
+constexpr int SWEEP_BLOCK = 4;
+
 static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase)
 {
-    const int64_t T = h->T, b = h->b, Np = h->Np;
-    for (int64_t j = 0; j < T; ++j) {
-        GPK_LAUNCH(h, phase, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)R, Np, j, b, ldm, h->RP);
-        if (!tg_diag_w(h, phase, R, ldm, vpart, j)) return false;
-        if (j + 1 < T && !tg_upd_w(h, phase, R, ldm, j)) return false;
+    const int T = (int)h->T;
+    const int64_t b = h->b, Np = h->Np;
+    for (int J = 0; J < T; J += SWEEP_BLOCK) {
+        const int e = J + SWEEP_BLOCK < T ? J + SWEEP_BLOCK : T;
+        for (int j = J; j < e; ++j) {
+            GPK_LAUNCH(h, phase, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)R, Np, (int64_t)j, b, ldm,
+                       h->RP);
+            if (!tg_diag_w(h, phase, R, ldm, vpart, j)) return false;
+            if (j + 1 < e && !tg_upd_w(h, phase, R, ldm, j, 1, j + 1, e - j - 1)) return false;
+        }
+        if (e < T && !tg_upd_w(h, phase, R, ldm, J, e - J, e, T - e)) return false;
     }
     return true;
 }
@@ -861,16 +872,21 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 {
     ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, Np = h->Np;
-    // x0^T = W L~^{-1}: backward sweep over tile columns, in place over R32
-    for (int64_t i = T - 1; i >= 0; --i) {
-        GPK_LAUNCH(h, GP_PH_BSOLVE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np, i, b, ldm,
-                   h->RP);
-        if (!tg_bdiag(h, ldm, i)) return false;
-        if (i > 0 && !tg_bupd(h, ldm, i)) return false;
+    // x0^T = W L~^{-1}: backward sweep over tile columns, in place over R32, in
+    // blocks of SWEEP_BLOCK columns; Y planes go to the W plane buffer
+    for (int I = (int)T - 1; I >= 0; I -= SWEEP_BLOCK) {
+        const int lo = I - SWEEP_BLOCK + 1 > 0 ? I - SWEEP_BLOCK + 1 : 0;
+        for (int i = I; i >= lo; --i) {
+            GPK_LAUNCH(h, GP_PH_BSOLVE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np,
+                       (int64_t)i, b, ldm, h->RP);
+            if (!tg_bdiag(h, ldm, i)) return false;
+            if (i > lo && !tg_bupd(h, ldm, i, 1, lo, i - lo)) return false;
+        }
+        if (lo > 0 && !tg_bupd(h, ldm, lo, I - lo + 1, 0, lo)) return false;
     }
-    GPK_LAUNCH(h, GP_PH_OZAKI, k_yslices, (unsigned)ldm, NTH, 0, (const float*)h->R32, Np, h->YS, ldm * Np, h->mu);
+    GPK_LAUNCH(h, GP_PH_SLICES, k_yslices, (unsigned)ldm, NTH, 0, (const float*)h->R32, Np, h->YS, ldm * Np, h->mu);
     if (!h->ks_valid) {
-        GPK_LAUNCH(h, GP_PH_OZAKI, k_kslices, dim3((unsigned)(Np / 64), (unsigned)(Np / 64)), NTH, 0, (const double*)h->L, b, Np,
+        GPK_LAUNCH(h, GP_PH_SLICES, k_kslices, dim3((unsigned)(Np / 64), (unsigned)(Np / 64)), NTH, 0, (const double*)h->L, b, Np,
                    (const GpHyperDev*)h->hyp, h->KS, Np * Np, h->kappa);
         h->ks_valid = true;
     }

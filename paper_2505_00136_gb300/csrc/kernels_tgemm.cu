@@ -4,19 +4,23 @@
 // to nearest at each step); a product A B^T is taken as the six plane
 // products Aa Bb^T with a + b <= 2, accumulated in FP32, which reproduces the
 // FP32 product to about FP32 rounding.  One persistent kernel template,
-// k_tgemm<Op>, runs all of them: a work unit is a 128 x 128 output block with
-// one or more k-segments; Op names the operand tiles, the units and the
-// epilogue.
+// k_tgemm<Op>, runs all of them: a work unit is a 128 x N output block (N =
+// Op::kN, 256 where the tile edge allows it, else 128) with one or more
+// k-segments; Op names the operand tiles, the units and the epilogue.
+//
+// A 128 x 256 x 16 MMA reads 12 KB of operands from shared memory in 128
+// clocks, a 128 x 128 x 16 one 8 KB in 64: the wide tile leaves shared-memory
+// bandwidth for the TMA fill and halves the A traffic per flop.
 //
 // Roles (320 threads, one CTA per SM, grid = min(units, SMs)): warp 0 issues
-// the TMA loads of a 32-k stage (three A planes and three B planes, six
-// 128 x 32 tiles with 64-byte swizzle, 48 KB) into a four-stage ring; warp 1
-// owns 256 TMEM columns
-// (two 128-column accumulators, alternating between units) and issues the
-// six plane MMAs per 16-k step; warps 2-9 run the epilogue of unit c while
-// the MMAs of unit c+1 proceed: two warps per TMEM lane quarter, each thread
-// one output row and 64 columns, its read-modify-write loads issued before it
-// waits for the accumulator.  Waits are bounded
+// the TMA loads of a 32-k stage — the three A planes (128 x 32 each) as one
+// box and the three B planes (N x 32 each) as one box, 64-byte swizzle —
+// into a ring of 3 (N = 256) or 4 (N = 128) stages; warp 1 owns 2N TMEM
+// columns (two 128 x N FP32 accumulators, alternating between units) and
+// issues the six plane MMAs per 16-k step; warps 2-9 run the epilogue of unit
+// c while the MMAs of unit c+1 proceed: two warps per TMEM lane quarter, each
+// thread one output row and N/2 columns in 64-column chunks, each chunk's
+// read-modify-write loads issued before its TMEM reads.  Waits are bounded
 // (see tc_common.cuh); a timeout sets the device error word and the CTA
 // leaves without touching its outputs.
 #include <cuda.h>
@@ -34,21 +38,25 @@ namespace {
 
 constexpr int TG_THREADS = 320;
 constexpr int TG_EPI_WARPS = 8;
-constexpr int TG_STAGES = 4;
 constexpr int TG_KS = 32;                          // k per stage
-constexpr int TG_PLANE = 128 * TG_KS * 2;          // bytes of one 128-row plane tile
-constexpr int TG_STAGE_BYTES = 6 * TG_PLANE;
-constexpr int TG_BAR_OFF = TG_STAGES * TG_STAGE_BYTES;
-constexpr int TG_SMEM = 1024 + TG_BAR_OFF + 256;
-constexpr uint32_t TG_IDESC = tc::idesc_bf16(128, 128);
-constexpr uint32_t TG_IDESC_BMN = tc::idesc_bf16_bmn(128, 128);
+constexpr int TG_APLANE = 128 * TG_KS * 2;         // bytes of one 128-row A plane tile
 
-// Operand coordinates of one k-segment: plane p of A is the 128-row box at
-// map row a_row + p * a_ps, k-columns a_x + [k0, k1); likewise B when B is
-// K-major.  An Op with kBMN set gives B as K x N with n contiguous (the NN
-// form): plane p holds k rows b_row + p * b_ps + [k0, k1), n columns b_x +
-// [0, 128), loaded as two 64-column boxes per stage.  k0 and k1 are
-// multiples of 32.
+template <int N>
+struct TgCfg {
+    static constexpr int BPLANE = N * TG_KS * 2;                 // bytes of one N-row B plane tile
+    static constexpr int STAGE = 3 * TG_APLANE + 3 * BPLANE;     // 48 KB (N = 128) or 72 KB (N = 256)
+    static constexpr int STAGES = N == 256 ? 3 : 4;
+    static constexpr int BAR_OFF = STAGES * STAGE;
+    static constexpr int SMEM = 1024 + BAR_OFF + 256;
+    static constexpr uint32_t IDESC = tc::idesc_bf16(128, N);
+    static constexpr uint32_t IDESC_BMN = tc::idesc_bf16_bmn(128, N);
+};
+
+// Operand coordinates of one k-segment: the A planes are the 128-row box at
+// plane-0 row a_row, k-columns a_x + [k0, k1); likewise the N-row B box when
+// B is K-major.  An Op with kBMN set gives B as K x N with n contiguous (the
+// NN form): its planes hold k rows b_row + [k0, k1), n columns b_x + [0, N).
+// k0 and k1 are multiples of 32.
 struct Seg {
     int a_row, a_x, b_row, b_x, k0, k1;
 };
@@ -66,22 +74,23 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                                                          const __grid_constant__ CUtensorMap mapB, const Op op,
                                                          int* err)
 {
+    using C = TgCfg<Op::kN>;
     extern __shared__ unsigned char dyn[];
     if (op.skip_all()) return;
     unsigned char* base = dyn + ((1024 - (tc::su32(dyn) & 1023)) & 1023);
     const uint32_t sbase = tc::su32(base);
-    const uint32_t bar = sbase + TG_BAR_OFF;   // full[2], empty[2], accf[2], acce[2], drain
+    const uint32_t bar = sbase + C::BAR_OFF;   // full[S], empty[S], accf[2], acce[2], drain
     auto full = [&](int s) { return bar + 8 * s; };
-    auto empty = [&](int s) { return bar + 8 * (TG_STAGES + s); };
-    auto accf = [&](int a) { return bar + 8 * (2 * TG_STAGES + a); };
-    auto acce = [&](int a) { return bar + 8 * (2 * TG_STAGES + 2 + a); };
-    const uint32_t drain = bar + 8 * (2 * TG_STAGES + 4);
-    uint32_t* tmem_slot = (uint32_t*)(base + TG_BAR_OFF + 8 * (2 * TG_STAGES + 5));
+    auto empty = [&](int s) { return bar + 8 * (C::STAGES + s); };
+    auto accf = [&](int a) { return bar + 8 * (2 * C::STAGES + a); };
+    auto acce = [&](int a) { return bar + 8 * (2 * C::STAGES + 2 + a); };
+    const uint32_t drain = bar + 8 * (2 * C::STAGES + 4);
+    uint32_t* tmem_slot = (uint32_t*)(base + C::BAR_OFF + 8 * (2 * C::STAGES + 5));
     volatile int* abort = (volatile int*)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TG_STAGES; ++s) {
+        for (int s = 0; s < C::STAGES; ++s) {
             tc::mbar_init(full(s), 1);
             tc::mbar_init(empty(s), 1);
         }
@@ -93,7 +102,7 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
         *abort = 0;
         tc::mbar_init_fence();
     }
-    if (warp == 1) tc::tmem_alloc(tc::su32(tmem_slot), 256);
+    if (warp == 1) tc::tmem_alloc(tc::su32(tmem_slot), 2 * Op::kN);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -111,33 +120,26 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                 for (int q = 0; q < ns && ok; ++q) {
                     const Seg sg = op.seg(u, q);
                     for (int k = sg.k0; k < sg.k1; k += TG_KS, ++it) {
-                        const int st = it % TG_STAGES, use = it / TG_STAGES;
+                        const int st = it % C::STAGES, use = it / C::STAGES;
                         if (use > 0 && !tc::mbar_wait(empty(st), (uint32_t)((use - 1) & 1), abort, err)) {
                             ok = false;
                             break;
                         }
-                        const uint32_t dst = sbase + st * TG_STAGE_BYTES;
-                        tc::mbar_expect_tx(full(st), TG_STAGE_BYTES);
-#pragma unroll
-                        for (int p = 0; p < 3; ++p) {
-                            tc::tma_load_2d_hint(dst + p * TG_PLANE, &mapA, sg.a_x + k, sg.a_row + p * op.a_ps, full(st),
-                                                 pol);
-                            if (Op::kBMN) {
-                                const uint32_t db = dst + (3 + p) * TG_PLANE;
-                                tc::tma_load_2d_hint(db, &mapB, sg.b_x, sg.b_row + p * op.b_ps + k, full(st), pol);
-                                tc::tma_load_2d_hint(db + TG_PLANE / 2, &mapB, sg.b_x + 64, sg.b_row + p * op.b_ps + k,
-                                                     full(st), pol);
-                            } else {
-                                tc::tma_load_2d_hint(dst + (3 + p) * TG_PLANE, &mapB, sg.b_x + k,
-                                                     sg.b_row + p * op.b_ps, full(st), pol);
-                            }
-                        }
+                        const uint32_t dst = sbase + st * C::STAGE;
+                        tc::mbar_expect_tx(full(st), C::STAGE);
+                        // one box per operand: the three planes are the box's last dimension
+                        tc::tma_load_3d_hint(dst, &mapA, sg.a_x + k, sg.a_row, 0, full(st), pol);
+                        if (Op::kBMN)
+                            tc::tma_load_4d_hint(dst + 3 * TG_APLANE, &mapB, 0, sg.b_row + k, sg.b_x / 64, 0,
+                                                 full(st), pol);
+                        else
+                            tc::tma_load_3d_hint(dst + 3 * TG_APLANE, &mapB, sg.b_x + k, sg.b_row, 0, full(st), pol);
                     }
                 }
             }
             if (!ok)
-                for (int q = it - 1; q >= 0 && q >= it - TG_STAGES; --q)
-                    seg_wait_drain(full(q % TG_STAGES), (uint32_t)((q / TG_STAGES) & 1));
+                for (int q = it - 1; q >= 0 && q >= it - C::STAGES; --q)
+                    seg_wait_drain(full(q % C::STAGES), (uint32_t)((q / C::STAGES) & 1));
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -151,27 +153,28 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                     break;
                 }
                 tc::fence_after();
-                const uint32_t d = tmem + (uint32_t)(a * 128);
+                const uint32_t d = tmem + (uint32_t)(a * Op::kN);
                 bool first = true;
                 const int ns = op.nseg(u);
                 for (int q = 0; q < ns && ok; ++q) {
                     const Seg sg = op.seg(u, q);
                     for (int k = sg.k0; k < sg.k1; k += TG_KS, ++it) {
-                        const int st = it % TG_STAGES;
-                        if (!tc::mbar_wait(full(st), (uint32_t)((it / TG_STAGES) & 1), abort, err)) {
+                        const int st = it % C::STAGES;
+                        if (!tc::mbar_wait(full(st), (uint32_t)((it / C::STAGES) & 1), abort, err)) {
                             ok = false;
                             break;
                         }
                         tc::fence_after();
-                        // stage descriptors once; planes are TG_PLANE apart (TG_PLANE >> 4 in the address
-                        // field), a 16-k step adds 32 bytes (K-major) or 2048 bytes (MN-major B)
-                        const uint32_t s0 = sbase + st * TG_STAGE_BYTES;
+                        // stage descriptors once; plane tiles follow each other, a 16-k step adds 32
+                        // bytes (K-major) or 2048 bytes (MN-major B)
+                        const uint32_t s0 = sbase + st * C::STAGE;
                         const uint64_t da = tc::desc_sw64(s0);
-                        const uint64_t db = Op::kBMN ? tc::desc_mn32_sw128(s0 + 3 * TG_PLANE)
-                                                     : tc::desc_sw64(s0 + 3 * TG_PLANE);
-                        constexpr uint64_t pl = (uint64_t)(TG_PLANE >> 4);
+                        const uint64_t db = Op::kBMN ? tc::desc_mn32_sw128(s0 + 3 * TG_APLANE)
+                                                     : tc::desc_sw64(s0 + 3 * TG_APLANE);
+                        constexpr uint64_t apl = (uint64_t)(TG_APLANE >> 4);
+                        constexpr uint64_t bpl = (uint64_t)(C::BPLANE >> 4);
                         constexpr uint64_t bstep = Op::kBMN ? (2048 >> 4) : 2;
-                        constexpr uint32_t idesc = Op::kBMN ? TG_IDESC_BMN : TG_IDESC;
+                        constexpr uint32_t idesc = Op::kBMN ? C::IDESC_BMN : C::IDESC;
                         if (first) tc::mma_bf16(d, da, db, idesc, 0u);
                         else tc::mma_bf16_acc(d, da, db, idesc);
                         first = false;
@@ -182,7 +185,7 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
 #pragma unroll
                                 for (int qb = 0; qa + qb < 3; ++qb) {
                                     if (kk == 0 && qa == 0 && qb == 0) continue;
-                                    tc::mma_bf16_acc(d, da + qa * pl + 2 * kk, db + qb * pl + bstep * kk, idesc);
+                                    tc::mma_bf16_acc(d, da + qa * apl + 2 * kk, db + qb * bpl + bstep * kk, idesc);
                                 }
                         tc::mma_commit(empty(st));
                     }
@@ -197,7 +200,7 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
             }
         }
     } else {
-        const int wq = warp & 3, row = wq * 32 + lane, c0 = ((warp - 2) >> 2) * 64;
+        const int wq = warp & 3, row = wq * 32 + lane, c0 = ((warp - 2) >> 2) * (Op::kN / 2);
         const uint32_t lrow = (uint32_t)(wq * 32) << 16;
         int c = 0;
         for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
@@ -208,7 +211,7 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                 if (ok) tc::fence_after();
                 return ok;
             };
-            if (!op.epilogue(u, row, c0, tmem + lrow + (uint32_t)(a * 128), wait)) break;
+            if (!op.epilogue(u, row, c0, tmem + lrow + (uint32_t)(a * Op::kN), wait)) break;
             tc::fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(acce(a));
@@ -220,7 +223,7 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
     if (warp == 1) {
         __syncwarp();
         tc::fence_after();
-        tc::tmem_dealloc(tmem, 256);
+        tc::tmem_dealloc(tmem, 2 * Op::kN);
     }
 }
 
@@ -272,188 +275,224 @@ __device__ __forceinline__ void planes32(__nv_bfloat16* p, int64_t ps, const flo
     }
 }
 
+// This thread's ncols accumulator columns c0 .. c0 + ncols of one row,
+// folded into the FP32 row dst (column 0 of the unit): dst[col] += sign * v
+// (store = false) or dst[col] = v (store = true), in 64-column chunks whose
+// loads are issued before the chunk's TMEM reads.  Chunks that start at or
+// beyond column limit are left untouched.  Calls wait() once, first.
+template <class W>
+__device__ __forceinline__ bool epi_rows(float* dst, uint32_t t, int c0, int ncols, float sign, bool store,
+                                         int limit, W&& wait)
+{
+    bool waited = false;
+#pragma unroll 1
+    for (int h64 = 0; h64 < ncols; h64 += 64) {
+        const int col = c0 + h64;
+        const bool skip = col >= limit;
+        Row64 cur;
+        if (!store && !skip) row_load(cur, dst + col);
+        if (!waited) {
+            if (!wait()) return false;
+            waited = true;
+        }
+        if (skip) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(t + col + 32 * h, v);
+            if (store) row_store(dst + col, v, h);
+            else row_axpy(dst + col, cur, v, h, sign);
+        }
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------- operations
 // All tile stores are b x b row-major; LP, ZP: three planes per lower tile
-// (tile t at rows 3 t b of the plane map); LinvP: three planes per diagonal
-// tile; PA: three planes per panel slot.
+// (tile t at rows 3 t b of the plane array); LinvP: three planes per diagonal
+// tile; PA: three planes per panel slot.  Q = b / 128 row blocks per tile,
+// Qn = b / N column units per tile.
 
-// Cholesky panel: L_ik = A_ik Linv_kk^T, k-range of Linv_kk's lower 128-block
-// column; FP32 L_ik over A_ik and its planes into LP.
+// Cholesky panel: L_ik = A_ik Linv_kk^T, k-range of Linv_kk's lower rows of
+// the column unit; FP32 L_ik over A_ik and its planes into LP.
+template <int N>
 struct OpPanel {
     static constexpr bool kBMN = false;
+    static constexpr int kN = N;
     float* A32;
     __nv_bfloat16* LP;
-    int b, k, tt, Q;
-    int a_ps, b_ps;
+    int b, k, tt, Q, Qn;
     const unsigned long long* info;
     __device__ bool skip_all() const { return failed(info); }
-    __device__ int units() const { return tt * Q * Q; }
+    __device__ int units() const { return tt * Q * Qn; }
     __device__ bool active(int) const { return true; }
     __device__ int nseg(int) const { return 1; }
     __device__ Seg seg(int u, int) const
     {
-        const int y = u / (Q * Q), r = u % (Q * Q), rb = r / Q, cb = r % Q;
-        return Seg{y * 3 * b + rb * 128, 0, k * 3 * b + cb * 128, 0, 0, (cb + 1) * 128};
+        const int y = u / (Q * Qn), r = u % (Q * Qn), rb = r / Qn, cn = r % Qn;
+        return Seg{y * 3 * b + rb * 128, 0, k * 3 * b + cn * N, 0, 0, (cn + 1) * N};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
-        const int y = u / (Q * Q), r = u % (Q * Q), rb = r / Q, cb = r % Q;
+        const int y = u / (Q * Qn), r = u % (Q * Qn), rb = r / Qn, cn = r % Qn;
         const int64_t i = k + 1 + y, bb = (int64_t)b * b;
-        const int64_t off = (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
+        const int64_t off = (int64_t)(rb * 128 + row) * b + cn * N;
         float* dst = A32 + tri_index(i, k) * bb + off;
         __nv_bfloat16* lp = LP + 3 * tri_index(i, k) * bb + off;
         if (!wait()) return false;
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < N / 2; h += 32) {
             float v[32];
-            tc::tmem_ld32(t + c0 + 32 * h, v);
-            row_store(dst, v, h);
-            planes32(lp + 32 * h, bb, v);
+            tc::tmem_ld32(t + c0 + h, v);
+            row_store(dst + c0 + h, v, 0);
+            planes32(lp + c0 + h, bb, v);
         }
         return true;
     }
 };
 
-// Trailing update: A_ij -= L_ik L_jk^T for k < j <= i (lower 128-blocks of diagonal tiles).
+// Trailing update: A_ij -= L_ik L_jk^T for k < j <= i; in diagonal tiles only
+// the column blocks up to the row's own diagonal 128-block are written.
+template <int N>
 struct OpUpdate {
     static constexpr bool kBMN = false;
+    static constexpr int kN = N;
     float* A32;
-    int b, k, tt, Q;
-    int a_ps, b_ps;
+    int b, k, tt, Q, Qn;
     const unsigned long long* info;
     __device__ bool skip_all() const { return failed(info); }
-    __device__ int units() const { return tt * (tt + 1) / 2 * Q * Q; }
-    __device__ void decode(int u, int64_t& i, int64_t& j, int& rb, int& cb) const
+    __device__ int units() const { return tt * (tt + 1) / 2 * Q * Qn; }
+    __device__ void decode(int u, int64_t& i, int64_t& j, int& rb, int& cn) const
     {
         int64_t ii, jj;
-        tri_decode(u / (Q * Q), ii, jj);
+        tri_decode(u / (Q * Qn), ii, jj);
         i = k + 1 + ii;
         j = k + 1 + jj;
-        rb = (u % (Q * Q)) / Q;
-        cb = u % Q;
+        rb = (u % (Q * Qn)) / Qn;
+        cn = u % Qn;
     }
     __device__ bool active(int u) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
-        return !(i == j && cb > rb);
+        int rb, cn;
+        decode(u, i, j, rb, cn);
+        return !(i == j && cn * N > rb * 128);
     }
     __device__ int nseg(int) const { return 1; }
     __device__ Seg seg(int u, int) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
-        return Seg{(int)(tri_index(i, k) * 3 * b) + rb * 128, 0, (int)(tri_index(j, k) * 3 * b) + cb * 128, 0, 0, b};
+        int rb, cn;
+        decode(u, i, j, rb, cn);
+        return Seg{(int)(tri_index(i, k) * 3 * b) + rb * 128, 0, (int)(tri_index(j, k) * 3 * b) + cn * N, 0, 0, b};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
-        float* dst = A32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
-        Row64 cur;
-        row_load(cur, dst);
-        if (!wait()) return false;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float v[32];
-            tc::tmem_ld32(t + c0 + 32 * h, v);
-            row_axpy(dst, cur, v, h, -1.f);
-        }
-        return true;
+        int rb, cn;
+        decode(u, i, j, rb, cn);
+        float* dst = A32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cn * N;
+        const int limit = (i == j) ? (rb + 1) * 128 - cn * N : N;
+        return epi_rows(dst, t, c0, N / 2, -1.f, false, limit, wait);
     }
 };
 
 // Forward multi-RHS solve, diagonal step: W_j = R_j Linv_jj^T; planes of W_j
-// into WP, FP32 W_j over R_j, FP64 row sums of W_j^2 into vpart.
+// into WP, FP32 W_j over R_j, FP64 row sums of W_j^2 into vpart (one slot per
+// 64 columns).
+template <int N>
 struct OpDiagW {
     static constexpr bool kBMN = false;
+    static constexpr int kN = N;
     __nv_bfloat16* WP;
     float* Wout;
     double* vpart;
     int64_t ldw, ldm;
-    int b, j, Q, nmb;
-    int a_ps, b_ps;
+    int b, j, Qn, nmb;
     __device__ bool skip_all() const { return false; }
-    __device__ int units() const { return Q * nmb; }
+    __device__ int units() const { return Qn * nmb; }
     __device__ bool active(int) const { return true; }
     __device__ int nseg(int) const { return 1; }
     __device__ Seg seg(int u, int) const
     {
-        const int cb = u % Q, mb = u / Q;
-        return Seg{mb * 128, 0, j * 3 * b + cb * 128, 0, 0, (cb + 1) * 128};
+        const int cn = u % Qn, mb = u / Qn;
+        return Seg{mb * 128, 0, j * 3 * b + cn * N, 0, 0, (cn + 1) * N};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
-        const int cb = u % Q, mb = u / Q;
+        const int cn = u % Qn, mb = u / Qn;
         const int64_t r = (int64_t)mb * 128 + row;
-        const int64_t o = r * ldw + (int64_t)j * b + cb * 128 + c0;
+        const int64_t o = r * ldw + (int64_t)j * b + cn * N;
         if (!wait()) return false;
-        double sq = 0.0;
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            float v[32];
-            tc::tmem_ld32(t + c0 + 32 * h, v);
-            planes32(WP + o + 32 * h, ldm * ldw, v);
-            row_store(Wout + o, v, h);
+        for (int h64 = 0; h64 < N / 2; h64 += 64) {
+            double sq = 0.0;
+#pragma unroll 1
+            for (int h = 0; h < 64; h += 32) {
+                float v[32];
+                tc::tmem_ld32(t + c0 + h64 + h, v);
+                planes32(WP + o + c0 + h64 + h, ldm * ldw, v);
+                row_store(Wout + o + c0 + h64 + h, v, 0);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) sq += (double)v[q] * v[q];
+                for (int q = 0; q < 32; ++q) sq += (double)v[q] * v[q];
+            }
+            vpart[(((int64_t)j * b + cn * N + c0 + h64) / 64) * ldm + r] = sq;
         }
-        vpart[(((int64_t)j * b + cb * 128 + c0) / 64) * ldm + r] = sq;   // one slot per 64 columns
         return true;
     }
 };
 
-// Forward multi-RHS solve, update: R_i -= W_j L_ij^T for all tiles i > j.
+// Forward multi-RHS solve, update: R_i -= sum_{j in [j0, j0 + nsrc)} W_j L_ij^T
+// for the target tiles i in [i0, i0 + ni), one k-segment per source column
+// (the block step of the sweep: R_i is read and written once per block).
+template <int N>
 struct OpUpdW {
     static constexpr bool kBMN = false;
+    static constexpr int kN = N;
     float* R32;
     int64_t ldr;
-    int b, j, T, Q, nmb;
-    int a_ps, b_ps;
+    int b, j0, nsrc, i0, ni, Qn, nmb;
     __device__ bool skip_all() const { return false; }
-    __device__ int units() const { return (T - j - 1) * Q * nmb; }
+    __device__ int units() const { return ni * Qn * nmb; }
     __device__ bool active(int) const { return true; }
-    __device__ int nseg(int) const { return 1; }
-    __device__ Seg seg(int u, int) const
+    __device__ int nseg(int) const { return nsrc; }
+    __device__ void decode(int u, int64_t& i, int& cn, int& mb) const
     {
-        const int nx = (T - j - 1) * Q, x = u % nx, mb = u / nx;
-        const int64_t i = j + 1 + x / Q;
-        const int cb = x % Q;
-        return Seg{mb * 128, j * b, (int)(tri_index(i, j) * 3 * b) + cb * 128, 0, 0, b};
+        const int nx = ni * Qn, x = u % nx;
+        mb = u / nx;
+        i = i0 + x / Qn;
+        cn = x % Qn;
+    }
+    __device__ Seg seg(int u, int q) const
+    {
+        int64_t i;
+        int cn, mb;
+        decode(u, i, cn, mb);
+        const int64_t j = j0 + q;
+        return Seg{mb * 128, (int)(j * b), (int)(tri_index(i, j) * 3 * b) + cn * N, 0, 0, b};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
-        const int nx = (T - j - 1) * Q, x = u % nx, mb = u / nx;
-        const int64_t i = j + 1 + x / Q;
-        const int cb = x % Q;
-        float* dst = R32 + ((int64_t)mb * 128 + row) * ldr + i * b + cb * 128 + c0;
-        Row64 cur;
-        row_load(cur, dst);
-        if (!wait()) return false;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float v[32];
-            tc::tmem_ld32(t + c0 + 32 * h, v);
-            row_axpy(dst, cur, v, h, -1.f);
-        }
-        return true;
+        int64_t i;
+        int cn, mb;
+        decode(u, i, cn, mb);
+        float* dst = R32 + ((int64_t)mb * 128 + row) * ldr + i * b + cn * N;
+        return epi_rows(dst, t, c0, N / 2, -1.f, false, N, wait);
     }
 };
 
-// Full covariance: cov (m x m, FP64, holding K_{Z*,Z*}) -= W W^T on lower 128-blocks, mirrored.
+// Full covariance: cov (m x m, FP64, holding K_{Z*,Z*}) -= W W^T on lower
+// 128-blocks, mirrored (128-wide units).
 struct OpSyrkCov {
     static constexpr bool kBMN = false;
+    static constexpr int kN = 128;
     double* cov;
     int64_t m;
     int kdim, nb;
-    int a_ps, b_ps;
     __device__ bool skip_all() const { return false; }
     __device__ int units() const { return nb * (nb + 1) / 2; }
     __device__ bool active(int) const { return true; }
@@ -478,11 +517,11 @@ struct OpSyrkCov {
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int cc = c0 + 32 * h + q;
-                const int64_t C = c * 128 + cc;
-                if (R >= m || C >= m || (a == c && cc > row)) continue;
-                const double x = cov[R * m + C] - (double)v[q];
-                cov[R * m + C] = x;
-                cov[C * m + R] = x;
+                const int64_t Cg = c * 128 + cc;
+                if (R >= m || Cg >= m || (a == c && cc > row)) continue;
+                const double x = cov[R * m + Cg] - (double)v[q];
+                cov[R * m + Cg] = x;
+                cov[Cg * m + R] = x;
             }
         }
         return true;
@@ -490,213 +529,204 @@ struct OpSyrkCov {
 };
 
 // Inverse for the gradient, finishing step: Z_tj = -U_tj Linv_tt^T (j < t), planes into ZP.
+template <int N>
 struct OpTrtriFin {
     static constexpr bool kBMN = false;
+    static constexpr int kN = N;
     __nv_bfloat16* ZP;
-    int b, t, Q;
-    int a_ps, b_ps;
+    int b, t, Q, Qn;
     __device__ bool skip_all() const { return false; }
-    __device__ int units() const { return t * Q * Q; }
+    __device__ int units() const { return t * Q * Qn; }
     __device__ bool active(int) const { return true; }
     __device__ int nseg(int) const { return 1; }
     __device__ Seg seg(int u, int) const
     {
-        const int j = u / (Q * Q), r = u % (Q * Q), rb = r / Q, cb = r % Q;
-        return Seg{j * 3 * b + rb * 128, 0, t * 3 * b + cb * 128, 0, 0, (cb + 1) * 128};
+        const int j = u / (Q * Qn), r = u % (Q * Qn), rb = r / Qn, cn = r % Qn;
+        return Seg{j * 3 * b + rb * 128, 0, t * 3 * b + cn * N, 0, 0, (cn + 1) * N};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t tm, W&& wait) const
     {
-        const int j = u / (Q * Q), r = u % (Q * Q), rb = r / Q, cb = r % Q;
+        const int j = u / (Q * Qn), r = u % (Q * Qn), rb = r / Qn, cn = r % Qn;
         const int64_t bb = (int64_t)b * b;
-        __nv_bfloat16* zp = ZP + tri_index(t, j) * 3 * bb + (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
+        __nv_bfloat16* zp = ZP + tri_index(t, j) * 3 * bb + (int64_t)(rb * 128 + row) * b + cn * N;
         if (!wait()) return false;
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < N / 2; h += 32) {
             float v[32];
-            tc::tmem_ld32(tm + c0 + 32 * h, v);
-            planes32(zp + 32 * h, bb, v, -1.f);
+            tc::tmem_ld32(tm + c0 + h, v);
+            planes32(zp + c0 + h, bb, v, -1.f);
         }
         return true;
     }
 };
 
 // Inverse, accumulation step: U_ij (+)= Z_tj L_it^T for i > t >= j; t == j overwrites.
+template <int N>
 struct OpTrtriAcc {
     static constexpr bool kBMN = false;
+    static constexpr int kN = N;
     float* U32;
-    int b, t, T, Q;
-    int a_ps, b_ps;
+    int b, t, T, Q, Qn;
     __device__ bool skip_all() const { return false; }
-    __device__ int units() const { return (T - t - 1) * (t + 1) * Q * Q; }
+    __device__ int units() const { return (T - t - 1) * (t + 1) * Q * Qn; }
     __device__ bool active(int) const { return true; }
     __device__ int nseg(int) const { return 1; }
-    __device__ void decode(int u, int64_t& i, int64_t& j, int& rb, int& cb) const
+    __device__ void decode(int u, int64_t& i, int64_t& j, int& rb, int& cn) const
     {
-        const int x = u / (Q * Q);
+        const int x = u / (Q * Qn);
         i = t + 1 + x / (t + 1);
         j = x % (t + 1);
-        rb = (u % (Q * Q)) / Q;
-        cb = u % Q;
+        rb = (u % (Q * Qn)) / Qn;
+        cn = u % Qn;
     }
     __device__ Seg seg(int u, int) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
-        return Seg{(int)(tri_index(t, j) * 3 * b) + rb * 128, 0, (int)(tri_index(i, t) * 3 * b) + cb * 128, 0, 0, b};
+        int rb, cn;
+        decode(u, i, j, rb, cn);
+        return Seg{(int)(tri_index(t, j) * 3 * b) + rb * 128, 0, (int)(tri_index(i, t) * 3 * b) + cn * N, 0, 0, b};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t tm, W&& wait) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
-        float* dst = U32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
-        const bool first = (t == j);
-        Row64 cur;
-        if (!first) row_load(cur, dst);
-        if (!wait()) return false;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float v[32];
-            tc::tmem_ld32(tm + c0 + 32 * h, v);
-            if (first) row_store(dst, v, h);
-            else row_axpy(dst, cur, v, h, 1.f);
-        }
-        return true;
+        int rb, cn;
+        decode(u, i, j, rb, cn);
+        float* dst = U32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cn * N;
+        return epi_rows(dst, tm, c0, N / 2, 1.f, t == j, N, wait);
     }
 };
 
-// Inverse, K^{-1}_ij = sum_{t >= i} Z_ti Z_tj^T on lower tiles (FP32 out).
+// Inverse, K^{-1}_ij = sum_{t >= i} Z_ti Z_tj^T on lower tiles (FP32 out);
+// in diagonal tiles only the column blocks up to the row's diagonal block.
+template <int N>
 struct OpLauum {
     static constexpr bool kBMN = false;
+    static constexpr int kN = N;
     float* Kinv32;
-    int b, T, Q;
-    int a_ps, b_ps;
+    int b, T, Q, Qn;
     __device__ bool skip_all() const { return false; }
-    __device__ int units() const { return T * (T + 1) / 2 * Q * Q; }
-    __device__ void decode(int u, int64_t& i, int64_t& j, int& rb, int& cb) const
+    __device__ int units() const { return T * (T + 1) / 2 * Q * Qn; }
+    __device__ void decode(int u, int64_t& i, int64_t& j, int& rb, int& cn) const
     {
-        tri_decode(u / (Q * Q), i, j);
-        rb = (u % (Q * Q)) / Q;
-        cb = u % Q;
+        tri_decode(u / (Q * Qn), i, j);
+        rb = (u % (Q * Qn)) / Qn;
+        cn = u % Qn;
     }
     __device__ bool active(int u) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
-        return !(i == j && cb > rb);
+        int rb, cn;
+        decode(u, i, j, rb, cn);
+        return !(i == j && cn * N > rb * 128);
     }
     __device__ int nseg(int u) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
+        int rb, cn;
+        decode(u, i, j, rb, cn);
         return (int)(T - i);
     }
     __device__ Seg seg(int u, int q) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
+        int rb, cn;
+        decode(u, i, j, rb, cn);
         const int64_t t = i + q;
-        return Seg{(int)(tri_index(t, i) * 3 * b) + rb * 128, 0, (int)(tri_index(t, j) * 3 * b) + cb * 128, 0,
+        return Seg{(int)(tri_index(t, i) * 3 * b) + rb * 128, 0, (int)(tri_index(t, j) * 3 * b) + cn * N, 0,
                    q == 0 ? rb * 128 : 0, b};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t tm, W&& wait) const
     {
         int64_t i, j;
-        int rb, cb;
-        decode(u, i, j, rb, cb);
-        float* dst = Kinv32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cb * 128 + c0;
-        if (!wait()) return false;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float v[32];
-            tc::tmem_ld32(tm + c0 + 32 * h, v);
-            row_store(dst, v, h);
-        }
-        return true;
+        int rb, cn;
+        decode(u, i, j, rb, cn);
+        float* dst = Kinv32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cn * N;
+        const int limit = (i == j) ? (rb + 1) * 128 - cn * N : N;
+        return epi_rows(dst, tm, c0, N / 2, 1.f, true, limit, wait);
     }
 };
 
 // Backward multi-RHS solve of the variance correction (x0^T = W L~^{-1}, NN form).
 // Diagonal step: Y_i = S_i Linv_ii, Linv_ii[t][c] nonzero for t >= c, so the
-// k-range of output column block cb starts at cb * 128.  FP32 Y_i over S_i
-// (column block i of R32) and its planes into YP (3 x ldm x b).
+// k-range of a column unit starts at its first column.  FP32 Y_i over S_i
+// (column block i of R32) and its planes into column block i of planes
+// (three planes of ldm x ldr: the W plane buffer).
+template <int N>
 struct OpBDiag {
     static constexpr bool kBMN = true;
+    static constexpr int kN = N;
     float* R32;
-    __nv_bfloat16* YP;
+    __nv_bfloat16* planes;
     int64_t ldr, ldm;
-    int b, i, Q, nmb;
-    int a_ps, b_ps;
+    int b, i, Qn, nmb;
     __device__ bool skip_all() const { return false; }
-    __device__ int units() const { return Q * nmb; }
+    __device__ int units() const { return Qn * nmb; }
     __device__ bool active(int) const { return true; }
     __device__ int nseg(int) const { return 1; }
     __device__ Seg seg(int u, int) const
     {
-        const int cb = u % Q, mb = u / Q;
-        return Seg{mb * 128, 0, i * 3 * b, cb * 128, cb * 128, b};
+        const int cn = u % Qn, mb = u / Qn;
+        return Seg{mb * 128, 0, i * 3 * b, cn * N, cn * N, b};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
-        const int cb = u % Q, mb = u / Q;
+        const int cn = u % Qn, mb = u / Qn;
         const int64_t r = (int64_t)mb * 128 + row;
-        float* dst = R32 + r * ldr + (int64_t)i * b + cb * 128 + c0;
-        __nv_bfloat16* yp = YP + r * b + cb * 128 + c0;
+        float* dst = R32 + r * ldr + (int64_t)i * b + cn * N;
+        __nv_bfloat16* yp = planes + r * ldr + (int64_t)i * b + cn * N;
         if (!wait()) return false;
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < N / 2; h += 32) {
             float v[32];
-            tc::tmem_ld32(t + c0 + 32 * h, v);
-            row_store(dst, v, h);
-            planes32(yp + 32 * h, ldm * b, v);
+            tc::tmem_ld32(t + c0 + h, v);
+            row_store(dst + c0 + h, v, 0);
+            planes32(yp + c0 + h, ldm * ldr, v);
         }
         return true;
     }
 };
 
-// Backward solve, update: S_j -= Y_i L_ij for all j < i (NN form, L_ij[t][c]).
+// Backward solve, update: S_j -= sum_{i in [i0, i0 + nsrc)} Y_i L_ij for the
+// target tiles j in [j0, j0 + nj), all below i0 (NN form, L_ij[t][c]), one
+// k-segment per source column.
+template <int N>
 struct OpBUpd {
     static constexpr bool kBMN = true;
+    static constexpr int kN = N;
     float* R32;
     int64_t ldr;
-    int b, i, Q, nmb;
-    int a_ps, b_ps;
+    int b, i0, nsrc, j0, nj, Qn, nmb;
     __device__ bool skip_all() const { return false; }
-    __device__ int units() const { return i * Q * nmb; }
+    __device__ int units() const { return nj * Qn * nmb; }
     __device__ bool active(int) const { return true; }
-    __device__ int nseg(int) const { return 1; }
-    __device__ Seg seg(int u, int) const
+    __device__ int nseg(int) const { return nsrc; }
+    __device__ void decode(int u, int64_t& j, int& cn, int& mb) const
     {
-        const int nx = i * Q, x = u % nx, mb = u / nx;
-        const int64_t j = x / Q;
-        const int cb = x % Q;
-        return Seg{mb * 128, 0, (int)(tri_index(i, j) * 3 * b), cb * 128, 0, b};
+        const int nx = nj * Qn, x = u % nx;
+        mb = u / nx;
+        j = j0 + x / Qn;
+        cn = x % Qn;
+    }
+    __device__ Seg seg(int u, int q) const
+    {
+        int64_t j;
+        int cn, mb;
+        decode(u, j, cn, mb);
+        const int64_t i = i0 + q;
+        return Seg{mb * 128, (int)(i * b), (int)(tri_index(i, j) * 3 * b), cn * N, 0, b};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
-        const int nx = i * Q, x = u % nx, mb = u / nx;
-        const int64_t j = x / Q;
-        const int cb = x % Q;
-        float* dst = R32 + ((int64_t)mb * 128 + row) * ldr + j * b + cb * 128 + c0;
-        Row64 cur;
-        row_load(cur, dst);
-        if (!wait()) return false;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float v[32];
-            tc::tmem_ld32(t + c0 + 32 * h, v);
-            row_axpy(dst, cur, v, h, -1.f);
-        }
-        return true;
+        int64_t j;
+        int cn, mb;
+        decode(u, j, cn, mb);
+        float* dst = R32 + ((int64_t)mb * 128 + row) * ldr + j * b + cn * N;
+        return epi_rows(dst, t, c0, N / 2, -1.f, false, N, wait);
     }
 };
 
@@ -715,19 +745,37 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn_tg()
     return fn;
 }
 
-// Row-major BF16 matrix (rows x cols, row stride cols) as TMA boxes: K-major
-// operands as {32 k, 128 rows} with 64-byte swizzle (mn = false), an MN-major
-// B as {64 n, 32 k rows} with 128-byte swizzle (mn = true).
-bool map_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols, bool mn = false)
+// Three-plane BF16 operand (plane p of row r at row r + p * plane_rows of a
+// rows x cols row-major array) as one TMA box per stage.  K-major (mn =
+// false): dims {cols, rows - 2 plane_rows, 3}, box {32 k, box_rows, 3
+// planes}, 64-byte swizzle.  MN-major B (mn = true, rows are k, n
+// contiguous): dims {64 n, rows - 2 plane_rows, cols / 64, 3}, box {64 n,
+// 32 k, box_rows / 64 column groups, 3 planes}, 128-byte swizzle, which lands
+// as [plane][group][k][n].  The row extent stops two planes short of the
+// array's end, so the plane offset of any in-range coordinate stays inside
+// the allocation.
+bool map_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols, int64_t plane_rows, int box_rows,
+               bool mn = false)
 {
     auto enc = encode_fn_tg();
-    if (!enc || ((uintptr_t)p & 15) || (cols * 2) % 16 || rows >= (1ll << 31)) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {mn ? 64u : (cuuint32_t)TG_KS, mn ? (cuuint32_t)TG_KS : 128u}, es[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(p), dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, mn ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const int64_t ext = rows - 2 * plane_rows;
+    if (!enc || ((uintptr_t)p & 15) || (cols * 2) % 16 || ext <= 0 || rows >= (1ll << 31) || (mn && cols % 64))
+        return false;
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (!mn) {
+        cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)ext, 3};
+        cuuint64_t strides[2] = {(cuuint64_t)cols * 2, (cuuint64_t)(plane_rows * cols * 2)};
+        cuuint32_t box[3] = {(cuuint32_t)TG_KS, (cuuint32_t)box_rows, 3u};
+        return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(p), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    cuuint64_t dims[4] = {64, (cuuint64_t)ext, (cuuint64_t)(cols / 64), 3};
+    cuuint64_t strides[3] = {(cuuint64_t)cols * 2, 128, (cuuint64_t)(plane_rows * cols * 2)};
+    cuuint32_t box[4] = {64u, (cuuint32_t)TG_KS, (cuuint32_t)(box_rows / 64), 3u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(p), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int g_num_sms = 0;
@@ -739,7 +787,7 @@ bool launch(gp_t h, int phase, const CUtensorMap& mA, const CUtensorMap& mB, con
     int dev = 0;
     cudaGetDevice(&dev);
     if (done_dev != dev) {
-        cudaFuncSetAttribute(k_tgemm<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, TG_SMEM);
+        cudaFuncSetAttribute(k_tgemm<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgCfg<Op::kN>::SMEM);
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         done_dev = dev;
     }
@@ -747,108 +795,148 @@ bool launch(gp_t h, int phase, const CUtensorMap& mA, const CUtensorMap& mB, con
     int* err = tc_error_dev();
     if (!err) return false;
     const int grid = units < g_num_sms ? units : g_num_sms;
-    GPK_LAUNCH(h, phase, k_tgemm<Op>, (unsigned)grid, TG_THREADS, TG_SMEM, mA, mB, op, err);
+    GPK_LAUNCH(h, phase, k_tgemm<Op>, (unsigned)grid, TG_THREADS, TgCfg<Op::kN>::SMEM, mA, mB, op, err);
     h->tc_pending = true;
     return true;
 }
 
-}  // namespace
+// Column units of the tile edge b: 256 wide where b allows it.
+bool wide(gp_t h) { return h->b % 256 == 0; }
 
-bool tg_panel(gp_t h, int64_t k)
+int64_t lp_rows(gp_t h) { return 3 * h->T * (h->T + 1) / 2 * h->b; }
+
+template <int N>
+bool panel_n(gp_t h, int64_t k)
 {
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
+    const int b = (int)h->b, T = (int)h->T;
     CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->PA, 3 * (int64_t)(T > 1 ? T - 1 : 1) * b, b) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b))
+    if (!map_tiles(&mA, h->PA, 3 * (int64_t)(T > 1 ? T - 1 : 1) * b, b, b, 128) ||
+        !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N))
         return false;
     const int tt = T - (int)k - 1;
-    OpPanel op{h->A32, h->LP, b, (int)k, tt, Q, b, b, (const unsigned long long*)h->info};
-    return launch(h, GP_PH_TRSM, mA, mB, op, tt * Q * Q);
+    OpPanel<N> op{h->A32, h->LP, b, (int)k, tt, b / 128, b / N, (const unsigned long long*)h->info};
+    return launch(h, GP_PH_TRSM, mA, mB, op, tt * (b / 128) * (b / N));
 }
 
-bool tg_update(gp_t h, int64_t k)
+template <int N>
+bool update_n(gp_t h, int64_t k)
 {
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
-    CUtensorMap mA;
-    if (!map_tiles(&mA, h->LP, 3 * (int64_t)T * (T + 1) / 2 * b, b)) return false;
+    const int b = (int)h->b, T = (int)h->T;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->LP, lp_rows(h), b, b, 128) || !map_tiles(&mB, h->LP, lp_rows(h), b, b, N)) return false;
     const int tt = T - (int)k - 1;
-    OpUpdate op{h->A32, b, (int)k, tt, Q, b, b, (const unsigned long long*)h->info};
-    return launch(h, GP_PH_UPDATE, mA, mA, op, tt * (tt + 1) / 2 * Q * Q);
+    OpUpdate<N> op{h->A32, b, (int)k, tt, b / 128, b / N, (const unsigned long long*)h->info};
+    return launch(h, GP_PH_UPDATE, mA, mB, op, tt * (tt + 1) / 2 * (b / 128) * (b / N));
 }
+
+template <int N>
+bool diag_w_n(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j)
+{
+    const int b = (int)h->b, T = (int)h->T;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->RP, 3 * ldm, b, ldm, 128) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N))
+        return false;
+    OpDiagW<N> op{h->WP, R, vpart, h->Np, ldm, b, (int)j, b / N, (int)(ldm / 128)};
+    return launch(h, phase, mA, mB, op, (b / N) * (int)(ldm / 128));
+}
+
+template <int N>
+bool upd_w_n(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni)
+{
+    const int b = (int)h->b;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np, ldm, 128) || !map_tiles(&mB, h->LP, lp_rows(h), b, b, N))
+        return false;
+    OpUpdW<N> op{R, h->Np, b, j0, nsrc, i0, ni, b / N, (int)(ldm / 128)};
+    return launch(h, phase, mA, mB, op, ni * (b / N) * (int)(ldm / 128));
+}
+
+template <int N>
+bool trtri_fin_n(gp_t h, int64_t t)
+{
+    const int b = (int)h->b, T = (int)h->T;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->PA, 3 * (int64_t)(T > 1 ? T - 1 : 1) * b, b, b, 128) ||
+        !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N))
+        return false;
+    OpTrtriFin<N> op{h->ZP, b, (int)t, b / 128, b / N};
+    return launch(h, GP_PH_TRTRI, mA, mB, op, (int)t * (b / 128) * (b / N));
+}
+
+template <int N>
+bool trtri_acc_n(gp_t h, int64_t t)
+{
+    const int b = (int)h->b, T = (int)h->T;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->ZP, lp_rows(h), b, b, 128) || !map_tiles(&mB, h->LP, lp_rows(h), b, b, N)) return false;
+    OpTrtriAcc<N> op{h->U32, b, (int)t, T, b / 128, b / N};
+    return launch(h, GP_PH_TRTRI, mA, mB, op, (T - (int)t - 1) * ((int)t + 1) * (b / 128) * (b / N));
+}
+
+template <int N>
+bool lauum_n(gp_t h)
+{
+    const int b = (int)h->b, T = (int)h->T;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->ZP, lp_rows(h), b, b, 128) || !map_tiles(&mB, h->ZP, lp_rows(h), b, b, N)) return false;
+    OpLauum<N> op{h->Kinv32, b, T, b / 128, b / N};
+    return launch(h, GP_PH_LAUUM, mA, mB, op, T * (T + 1) / 2 * (b / 128) * (b / N));
+}
+
+template <int N>
+bool bdiag_n(gp_t h, int64_t ldm, int64_t i)
+{
+    const int b = (int)h->b, T = (int)h->T;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->RP, 3 * ldm, b, ldm, 128) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N, true))
+        return false;
+    OpBDiag<N> op{h->R32, h->WP, h->Np, ldm, b, (int)i, b / N, (int)(ldm / 128)};
+    return launch(h, GP_PH_BSOLVE, mA, mB, op, (b / N) * (int)(ldm / 128));
+}
+
+template <int N>
+bool bupd_n(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj)
+{
+    const int b = (int)h->b;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np, ldm, 128) || !map_tiles(&mB, h->LP, lp_rows(h), b, b, N, true))
+        return false;
+    OpBUpd<N> op{h->R32, h->Np, b, i0, nsrc, j0, nj, b / N, (int)(ldm / 128)};
+    return launch(h, GP_PH_BSOLVE, mA, mB, op, nj * (b / N) * (int)(ldm / 128));
+}
+
+}  // namespace
+
+bool tg_panel(gp_t h, int64_t k) { return wide(h) ? panel_n<256>(h, k) : panel_n<128>(h, k); }
+bool tg_update(gp_t h, int64_t k) { return wide(h) ? update_n<256>(h, k) : update_n<128>(h, k); }
 
 bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j)
 {
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
-    CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->RP, 3 * ldm, b) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b)) return false;
-    OpDiagW op{h->WP, R, vpart, h->Np, ldm, b, (int)j, Q, (int)(ldm / 128), (int)ldm, b};
-    return launch(h, phase, mA, mB, op, Q * (int)(ldm / 128));
+    return wide(h) ? diag_w_n<256>(h, phase, R, ldm, vpart, j) : diag_w_n<128>(h, phase, R, ldm, vpart, j);
 }
 
-bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int64_t j)
+bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni)
 {
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
-    CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np) || !map_tiles(&mB, h->LP, 3 * (int64_t)T * (T + 1) / 2 * b, b))
-        return false;
-    OpUpdW op{R, h->Np, b, (int)j, T, Q, (int)(ldm / 128), (int)ldm, b};
-    return launch(h, phase, mA, mB, op, (T - (int)j - 1) * Q * (int)(ldm / 128));
+    return wide(h) ? upd_w_n<256>(h, phase, R, ldm, j0, nsrc, i0, ni)
+                   : upd_w_n<128>(h, phase, R, ldm, j0, nsrc, i0, ni);
 }
 
 bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov)
 {
     CUtensorMap mA;
-    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np)) return false;
+    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np, ldm, 128)) return false;
     const int nb = (int)((m + 127) / 128);
-    OpSyrkCov op{cov, m, (int)h->Np, nb, (int)ldm, (int)ldm};
+    OpSyrkCov op{cov, m, (int)h->Np, nb};
     return launch(h, GP_PH_COV, mA, mA, op, nb * (nb + 1) / 2);
 }
 
-bool tg_trtri_fin(gp_t h, int64_t t)
+bool tg_trtri_fin(gp_t h, int64_t t) { return wide(h) ? trtri_fin_n<256>(h, t) : trtri_fin_n<128>(h, t); }
+bool tg_trtri_acc(gp_t h, int64_t t) { return wide(h) ? trtri_acc_n<256>(h, t) : trtri_acc_n<128>(h, t); }
+bool tg_lauum(gp_t h) { return wide(h) ? lauum_n<256>(h) : lauum_n<128>(h); }
+bool tg_bdiag(gp_t h, int64_t ldm, int64_t i) { return wide(h) ? bdiag_n<256>(h, ldm, i) : bdiag_n<128>(h, ldm, i); }
+bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj)
 {
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
-    CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->PA, 3 * (int64_t)(T > 1 ? T - 1 : 1) * b, b) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b))
-        return false;
-    OpTrtriFin op{h->ZP, b, (int)t, Q, b, b};
-    return launch(h, GP_PH_TRTRI, mA, mB, op, (int)t * Q * Q);
-}
-
-bool tg_trtri_acc(gp_t h, int64_t t)
-{
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
-    CUtensorMap mA, mB;
-    const int64_t rows = 3 * (int64_t)T * (T + 1) / 2 * b;
-    if (!map_tiles(&mA, h->ZP, rows, b) || !map_tiles(&mB, h->LP, rows, b)) return false;
-    OpTrtriAcc op{h->U32, b, (int)t, T, Q, b, b};
-    return launch(h, GP_PH_TRTRI, mA, mB, op, (T - (int)t - 1) * ((int)t + 1) * Q * Q);
-}
-
-bool tg_lauum(gp_t h)
-{
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
-    CUtensorMap mA;
-    if (!map_tiles(&mA, h->ZP, 3 * (int64_t)T * (T + 1) / 2 * b, b)) return false;
-    OpLauum op{h->Kinv32, b, T, Q, b, b};
-    return launch(h, GP_PH_LAUUM, mA, mA, op, T * (T + 1) / 2 * Q * Q);
-}
-
-bool tg_bdiag(gp_t h, int64_t ldm, int64_t i)
-{
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
-    CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->RP, 3 * ldm, b) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, true)) return false;
-    OpBDiag op{h->R32, h->YP, h->Np, ldm, b, (int)i, Q, (int)(ldm / 128), (int)ldm, b};
-    return launch(h, GP_PH_BSOLVE, mA, mB, op, Q * (int)(ldm / 128));
-}
-
-bool tg_bupd(gp_t h, int64_t ldm, int64_t i)
-{
-    const int b = (int)h->b, T = (int)h->T, Q = b / 128;
-    CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->YP, 3 * ldm, b) || !map_tiles(&mB, h->LP, 3 * (int64_t)T * (T + 1) / 2 * b, b, true))
-        return false;
-    OpBUpd op{h->R32, h->Np, b, (int)i, Q, (int)(ldm / 128), (int)ldm, b};
-    return launch(h, GP_PH_BSOLVE, mA, mB, op, (int)i * Q * (int)(ldm / 128));
+    return wide(h) ? bupd_n<256>(h, ldm, i0, nsrc, j0, nj) : bupd_n<128>(h, ldm, i0, nsrc, j0, nj);
 }
 
 }  // namespace gpk

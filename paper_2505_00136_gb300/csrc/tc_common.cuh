@@ -94,6 +94,25 @@ __device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap
         ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "l"(policy) : "memory");
 }
 
+// 3-D and 4-D tiled loads with an L2 cache policy (coordinates innermost first).
+__device__ __forceinline__ void tma_load_3d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                                 uint32_t mbar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;\n"
+        ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "r"(z), "l"(policy) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                                 uint32_t mbar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2], %7;\n"
+        ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "r"(z), "r"(w), "l"(policy) : "memory");
+}
+
 // As tma_load_2d, the box written to the same shared-memory offset in every
 // CTA of the cluster named in mask, each of whose mbarrier at offset mbar
 // receives the completed bytes.

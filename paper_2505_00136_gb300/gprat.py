@@ -30,7 +30,7 @@ GP_MLP_NPARAM = 83203
 GP_MLP_MODEL_FLOATS = GP_MLP_NPARAM + 128
 GP_LEARNED_INIT_SCRATCH = 72
 PHASES = ["assemble", "potrf", "trsm", "update", "solve", "cross", "vsolve", "reduce", "cov",
-          "trtri", "lauum", "adjoint", "adam", "refine", "bsolve", "ozaki", "rsolve", "other"]
+          "trtri", "lauum", "adjoint", "adam", "refine", "bsolve", "ozaki", "rsolve", "slices", "other"]
 
 
 class gp_hyper(ctypes.Structure):
