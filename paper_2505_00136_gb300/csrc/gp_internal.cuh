@@ -176,7 +176,7 @@ cudaError_t tc_error_fetch(gp_t h, int* out);                   // read and clea
 int* tc_error_dev();                                            // device address of that word
 // kernels_tgemm.cu: split-BF16 block products on tcgen05 (false: tensor map not encodable)
 bool tg_panel(gp_t h, int64_t k);
-bool tg_update(gp_t h, int64_t k);
+bool tg_update(gp_t h, int k0, int nsrc, int j0, int w);   // A_ij -= sum_k L_ik L_jk^T on a column band
 bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j);
 bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni);   // R_i -= sum W_j L_ij^T
 bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov);

@@ -743,22 +743,38 @@ static void ensure_attrs_mixed()
     done_dev = dev;
 }
 
+// The factorisation and the multi-RHS sweeps update their trailing FP32
+// matrix once per block of SWEEP_BLOCK tile columns (one k-segment per
+// column), so it is read and written T / SWEEP_BLOCK times, not T.
+constexpr int SWEEP_BLOCK = 4;
+
+// Right-looking, in super-panels of SWEEP_BLOCK tile columns: each column k
+// of a super-panel is factored (diagonal tile, panel) and applied only to the
+// super-panel's later columns; then one update with a k-segment per column
+// applies the whole super-panel to the trailing triangle.
 bool factor_mixed(gp_t h)
 {
     ensure_attrs_mixed();
-    const int64_t T = h->T, b = h->b, bb = b * b;
-    for (int64_t k = 0; k < T; ++k) {
-        GPK_LAUNCH(h, GP_PH_POTRF, k_potrf32, 1, NTH, POTRF32_SMEM, h->A32 + tri_index(k, k) * bb,
-                   h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b, k * b, h->logdet_part + k, h->info);
-        if (k + 1 < T) {
-            const unsigned tt = (unsigned)(T - k - 1);
-            GPK_LAUNCH(h, GP_PH_TRSM, k_split_panel, dim3((unsigned)grid_for(bb) / 4 + 1, tt), NTH, 0,
-                       (const float*)h->A32, h->PA, b, k);
-            if (!tg_panel(h, k) || !tg_update(h, k)) return false;
+    const int T = (int)h->T;
+    const int64_t b = h->b, bb = b * b;
+    for (int K0 = 0; K0 < T; K0 += SWEEP_BLOCK) {
+        const int e = K0 + SWEEP_BLOCK < T ? K0 + SWEEP_BLOCK : T;
+        for (int k = K0; k < e; ++k) {
+            GPK_LAUNCH(h, GP_PH_POTRF, k_potrf32, 1, NTH, POTRF32_SMEM, h->A32 + tri_index(k, k) * bb,
+                       h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b, (int64_t)k * b, h->logdet_part + k, h->info);
+            if (k + 1 < T) {
+                const unsigned tt = (unsigned)(T - k - 1);
+                GPK_LAUNCH(h, GP_PH_TRSM, k_split_panel, dim3((unsigned)grid_for(bb) / 4 + 1, tt), NTH, 0,
+                           (const float*)h->A32, h->PA, b, (int64_t)k);
+                if (!tg_panel(h, k)) return false;
+                if (k + 1 < e && !tg_update(h, k, 1, k + 1, e - k - 1)) return false;
+            }
         }
+        if (e < T && !tg_update(h, K0, e - K0, e, T - e)) return false;
     }
     return true;
 }
+
 
 // out32 = L~^{-1} in32 (lower) or L~^{-T} in32 (upper), FP32 throughout.
 static void solve32(gp_t h, const float* in32, float* out32, bool upper)
@@ -829,10 +845,6 @@ void nlml_mixed(gp_t h)
 
 // Forward multi-RHS solve W = R L~^{-T} in place over R (ldm x Np, FP32): W
 // planes into WP, FP32 W over R, FP64 row sums of W^2 into vpart.
-// Multi-RHS sweeps update the trailing right-hand side once per block of
-// SWEEP_BLOCK tile columns (each block step one k-segment per column), so the
-// FP32 right-hand side is read and written T / SWEEP_BLOCK times, not T.
-constexpr int SWEEP_BLOCK = 4;
 
 static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase)
 {

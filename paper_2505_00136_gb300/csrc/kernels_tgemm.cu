@@ -352,23 +352,34 @@ struct OpPanel {
     }
 };
 
-// Trailing update: A_ij -= L_ik L_jk^T for k < j <= i; in diagonal tiles only
+// Trailing update: A_ij -= sum_{k in [k0, k0 + nsrc)} L_ik L_jk^T over the
+// target tiles of a band of w columns j in [j0, j0 + w) and all rows i in
+// [j, T) (one k-segment per source column).  w = T - j0 is the whole
+// trailing triangle.  Units: the rows j0 .. j0+w-2 hold 1 .. w-1 tiles of the
+// band (the triangle part, row j0 + r holding r + 1), every later row w tiles.  In diagonal tiles only
 // the column blocks up to the row's own diagonal 128-block are written.
 template <int N>
 struct OpUpdate {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
     float* A32;
-    int b, k, tt, Q, Qn;
+    int b, k0, nsrc, j0, w, T, Q, Qn;
     const unsigned long long* info;
     __device__ bool skip_all() const { return failed(info); }
-    __device__ int units() const { return tt * (tt + 1) / 2 * Q * Qn; }
+    __device__ int units() const { return (w * (w - 1) / 2 + w * (T - j0 - w + 1)) * Q * Qn; }
     __device__ void decode(int u, int64_t& i, int64_t& j, int& rb, int& cn) const
     {
-        int64_t ii, jj;
-        tri_decode(u / (Q * Qn), ii, jj);
-        i = k + 1 + ii;
-        j = k + 1 + jj;
+        const int64_t p = u / (Q * Qn), tp = (int64_t)w * (w - 1) / 2;
+        if (p < tp) {
+            int64_t r, c;
+            tri_decode(p, r, c);
+            i = j0 + r;
+            j = j0 + c;
+        } else {
+            const int64_t v = p - tp;
+            i = j0 + w - 1 + v / w;
+            j = j0 + v % w;
+        }
         rb = (u % (Q * Qn)) / Qn;
         cn = u % Qn;
     }
@@ -379,12 +390,13 @@ struct OpUpdate {
         decode(u, i, j, rb, cn);
         return !(i == j && cn * N > rb * 128);
     }
-    __device__ int nseg(int) const { return 1; }
-    __device__ Seg seg(int u, int) const
+    __device__ int nseg(int) const { return nsrc; }
+    __device__ Seg seg(int u, int q) const
     {
         int64_t i, j;
         int rb, cn;
         decode(u, i, j, rb, cn);
+        const int64_t k = k0 + q;
         return Seg{(int)(tri_index(i, k) * 3 * b) + rb * 128, 0, (int)(tri_index(j, k) * 3 * b) + cn * N, 0, 0, b};
     }
     template <class W>
@@ -819,14 +831,13 @@ bool panel_n(gp_t h, int64_t k)
 }
 
 template <int N>
-bool update_n(gp_t h, int64_t k)
+bool update_n(gp_t h, int k0, int nsrc, int j0, int w)
 {
     const int b = (int)h->b, T = (int)h->T;
     CUtensorMap mA, mB;
     if (!map_tiles(&mA, h->LP, lp_rows(h), b, b, 128) || !map_tiles(&mB, h->LP, lp_rows(h), b, b, N)) return false;
-    const int tt = T - (int)k - 1;
-    OpUpdate<N> op{h->A32, b, (int)k, tt, b / 128, b / N, (const unsigned long long*)h->info};
-    return launch(h, GP_PH_UPDATE, mA, mB, op, tt * (tt + 1) / 2 * (b / 128) * (b / N));
+    OpUpdate<N> op{h->A32, b, k0, nsrc, j0, w, T, b / 128, b / N, (const unsigned long long*)h->info};
+    return launch(h, GP_PH_UPDATE, mA, mB, op, (w * (w - 1) / 2 + w * (T - j0 - w + 1)) * (b / 128) * (b / N));
 }
 
 template <int N>
@@ -908,7 +919,10 @@ bool bupd_n(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj)
 }  // namespace
 
 bool tg_panel(gp_t h, int64_t k) { return wide(h) ? panel_n<256>(h, k) : panel_n<128>(h, k); }
-bool tg_update(gp_t h, int64_t k) { return wide(h) ? update_n<256>(h, k) : update_n<128>(h, k); }
+bool tg_update(gp_t h, int k0, int nsrc, int j0, int w)
+{
+    return wide(h) ? update_n<256>(h, k0, nsrc, j0, w) : update_n<128>(h, k0, nsrc, j0, w);
+}
 
 bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j)
 {
