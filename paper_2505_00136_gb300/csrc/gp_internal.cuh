@@ -181,7 +181,7 @@ bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t 
 bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni);   // R_i -= sum W_j L_ij^T
 bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov);
 bool tg_trtri_fin(gp_t h, int64_t t);
-bool tg_trtri_acc(gp_t h, int64_t t);
+bool tg_trtri_acc(gp_t h, int t0, int t1, int i0, int ni, int nj);   // U_ij (+)= sum_t Z_tj L_it^T
 bool tg_lauum(gp_t h);
 bool tg_bdiag(gp_t h, int64_t ldm, int64_t i);                  // Y_i = S_i Linv_ii (NN form)
 bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj);   // S_j -= sum Y_i L_ij (NN form)

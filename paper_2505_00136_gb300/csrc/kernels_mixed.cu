@@ -923,13 +923,21 @@ bool inverse_mixed(gp_t h)
     const int64_t T = h->T, b = h->b, bb = b * b;
     GPK_LAUNCH(h, GP_PH_TRTRI, k_zdiag, dim3((unsigned)grid_for(bb) / 4 + 1, (unsigned)T), NTH, 0,
                (const float*)h->Linv32, h->ZP, b);
-    for (int64_t t = 0; t < T; ++t) {
-        if (t > 0) {
-            GPK_LAUNCH(h, GP_PH_TRTRI, k_split_row, dim3((unsigned)grid_for(bb) / 4 + 1, (unsigned)t), NTH, 0,
-                       (const float*)h->U32, h->PA, b, t);
-            if (!tg_trtri_fin(h, t)) return false;
+    // blocks of SWEEP_BLOCK steps t: each step's accumulation reaches only the
+    // block's rows; one multi-segment accumulation then applies the block to
+    // every later row, so U32 is read and written once per block
+    const int TT = (int)T;
+    for (int T0 = 0; T0 < TT; T0 += SWEEP_BLOCK) {
+        const int e = T0 + SWEEP_BLOCK < TT ? T0 + SWEEP_BLOCK : TT;
+        for (int t = T0; t < e; ++t) {
+            if (t > 0) {
+                GPK_LAUNCH(h, GP_PH_TRTRI, k_split_row, dim3((unsigned)grid_for(bb) / 4 + 1, (unsigned)t), NTH, 0,
+                           (const float*)h->U32, h->PA, b, (int64_t)t);
+                if (!tg_trtri_fin(h, t)) return false;
+            }
+            if (t + 1 < e && !tg_trtri_acc(h, t, t + 1, t + 1, e - t - 1, t + 1)) return false;
         }
-        if (t + 1 < T && !tg_trtri_acc(h, t)) return false;
+        if (e < TT && !tg_trtri_acc(h, T0, e, e, TT - e, e)) return false;
     }
     return tg_lauum(h);
 }

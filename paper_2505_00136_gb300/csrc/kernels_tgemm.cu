@@ -573,30 +573,40 @@ struct OpTrtriFin {
     }
 };
 
-// Inverse, accumulation step: U_ij (+)= Z_tj L_it^T for i > t >= j; t == j overwrites.
+// Inverse, accumulation: U_ij (+)= sum_{t in [max(t0, j), t1)} Z_tj L_it^T for
+// the target tiles i in [i0, i0 + ni) (all >= t1), j in [0, nj), one
+// k-segment per t.  A tile's first contribution (t == j, inside the range
+// exactly when j >= t0) overwrites, later ones add.
 template <int N>
 struct OpTrtriAcc {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
     float* U32;
-    int b, t, T, Q, Qn;
+    int b, t0, t1, i0, ni, nj, Q, Qn;
     __device__ bool skip_all() const { return false; }
-    __device__ int units() const { return (T - t - 1) * (t + 1) * Q * Qn; }
+    __device__ int units() const { return ni * nj * Q * Qn; }
     __device__ bool active(int) const { return true; }
-    __device__ int nseg(int) const { return 1; }
     __device__ void decode(int u, int64_t& i, int64_t& j, int& rb, int& cn) const
     {
         const int x = u / (Q * Qn);
-        i = t + 1 + x / (t + 1);
-        j = x % (t + 1);
+        i = i0 + x / nj;
+        j = x % nj;
         rb = (u % (Q * Qn)) / Qn;
         cn = u % Qn;
     }
-    __device__ Seg seg(int u, int) const
+    __device__ int nseg(int u) const
     {
         int64_t i, j;
         int rb, cn;
         decode(u, i, j, rb, cn);
+        return t1 - (int)(j > t0 ? j : t0);
+    }
+    __device__ Seg seg(int u, int q) const
+    {
+        int64_t i, j;
+        int rb, cn;
+        decode(u, i, j, rb, cn);
+        const int64_t t = (j > t0 ? j : t0) + q;
         return Seg{(int)(tri_index(t, j) * 3 * b) + rb * 128, 0, (int)(tri_index(i, t) * 3 * b) + cn * N, 0, 0, b};
     }
     template <class W>
@@ -606,7 +616,7 @@ struct OpTrtriAcc {
         int rb, cn;
         decode(u, i, j, rb, cn);
         float* dst = U32 + tri_index(i, j) * (int64_t)b * b + (int64_t)(rb * 128 + row) * b + cn * N;
-        return epi_rows(dst, tm, c0, N / 2, 1.f, t == j, N, wait);
+        return epi_rows(dst, tm, c0, N / 2, 1.f, j >= t0, N, wait);
     }
 };
 
@@ -875,13 +885,13 @@ bool trtri_fin_n(gp_t h, int64_t t)
 }
 
 template <int N>
-bool trtri_acc_n(gp_t h, int64_t t)
+bool trtri_acc_n(gp_t h, int t0, int t1, int i0, int ni, int nj)
 {
-    const int b = (int)h->b, T = (int)h->T;
+    const int b = (int)h->b;
     CUtensorMap mA, mB;
     if (!map_tiles(&mA, h->ZP, lp_rows(h), b, b, 128) || !map_tiles(&mB, h->LP, lp_rows(h), b, b, N)) return false;
-    OpTrtriAcc<N> op{h->U32, b, (int)t, T, b / 128, b / N};
-    return launch(h, GP_PH_TRTRI, mA, mB, op, (T - (int)t - 1) * ((int)t + 1) * (b / 128) * (b / N));
+    OpTrtriAcc<N> op{h->U32, b, t0, t1, i0, ni, nj, b / 128, b / N};
+    return launch(h, GP_PH_TRTRI, mA, mB, op, ni * nj * (b / 128) * (b / N));
 }
 
 template <int N>
@@ -945,7 +955,10 @@ bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov)
 }
 
 bool tg_trtri_fin(gp_t h, int64_t t) { return wide(h) ? trtri_fin_n<256>(h, t) : trtri_fin_n<128>(h, t); }
-bool tg_trtri_acc(gp_t h, int64_t t) { return wide(h) ? trtri_acc_n<256>(h, t) : trtri_acc_n<128>(h, t); }
+bool tg_trtri_acc(gp_t h, int t0, int t1, int i0, int ni, int nj)
+{
+    return wide(h) ? trtri_acc_n<256>(h, t0, t1, i0, ni, nj) : trtri_acc_n<128>(h, t0, t1, i0, ni, nj);
+}
 bool tg_lauum(gp_t h) { return wide(h) ? lauum_n<256>(h) : lauum_n<128>(h); }
 bool tg_bdiag(gp_t h, int64_t ldm, int64_t i) { return wide(h) ? bdiag_n<256>(h, ldm, i) : bdiag_n<128>(h, ldm, i); }
 bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj)
