@@ -2,8 +2,8 @@
 
 Workload (default): N = 32768 training and M = 8192 test points of the seeded
 mass-spring-damper generator, 8 lagged-input regressors, (l, nu, sigma^2) =
-(1, 1, 0.1); mixed precision (256 x 256 tiles of 128) by default, with one
-FP64 run (128 x 128 tiles of 256) on the same inputs for the speed-up and the
+(1, 1, 0.1); mixed precision (128 x 128 tiles of 256) by default, with one
+FP64 run (same tiles) on the same inputs for the speed-up and the
 per-output relative errors; --precision fp64 benchmarks the FP64 path.
 Inputs are resident in HBM before the timed region; the factor alone (4.3 GB
 of tiles) is far larger than L2.
@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--m", type=int, default=8192)
     ap.add_argument("--d", type=int, default=8)
-    ap.add_argument("--tiles", type=int, default=None, help="tiles per dimension (default 128 fp64, 256 mixed)")
+    ap.add_argument("--tiles", type=int, default=None, help="tiles per dimension (default 128: tiles of 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=4096)
@@ -64,7 +64,7 @@ def parse():
                     help="skip the learned-initialiser measurement (small corpus, untimed for value)")
     args = ap.parse_args()
     if args.tiles is None:
-        args.tiles = 256 if args.precision == "mixed" else 128
+        args.tiles = 128
     return args
 
 
