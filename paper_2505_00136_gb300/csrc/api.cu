@@ -563,7 +563,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(dev_alloc(h, &h->PA, 3 * (h->T > 1 ? h->T - 1 : 1) * bb));
         TRY(dev_alloc(h, &h->r32, h->Np));
         TRY(dev_alloc(h, &h->t32, h->Np));
-        TRY(dev_alloc(h, &h->w32, h->Np));
+        TRY(dev_alloc(h, &h->w32, h->Np * (h->b >= 64 ? h->b / 64 : 1)));   // partial sums of the solves
         TRY(dev_alloc(h, &h->solve_flags, 2));
         TRY(cuda_status(h, cudaMemset(h->solve_flags, 0, 2 * sizeof(int))));
         TRY(dev_alloc(h, &h->res, h->Np));

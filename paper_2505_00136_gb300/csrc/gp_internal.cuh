@@ -77,7 +77,7 @@ struct gp_handle {
     float* Linv32;            // T tiles: inverses of the diagonal factor tiles
     __nv_bfloat16* LinvP;     // T tiles x 3 planes of Linv32
     __nv_bfloat16* PA;        // (T-1) tiles x 3 planes: panel operand scratch
-    float *r32, *t32, *w32;   // Np FP32 vectors of the refinement solves
+    float *r32, *t32, *w32;   // FP32 vectors of the refinement solves (w32: b / 64 copies of Np)
     double* res;              // Np FP64 residual
     double* norms;            // 2 FP64 norms
     float* R32;               // m_cap x Np: K_{Z*,Z}, overwritten by the W solve

@@ -17,6 +17,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <utility>
+
 #include "split_bf16.cuh"
 #include "gp_internal.cuh"
 #include "se_common.cuh"
@@ -37,13 +39,31 @@ struct SView {
 constexpr int SG_KC = 32;                     // k per shared-memory chunk
 constexpr int SG_FLOATS = 2 * SG_KC * 65;     // A and B chunks, k-major, padded
 
-__device__ __forceinline__ void sg_stage(const SView& v, int64_t k0, int64_t ke, float* dst)
+constexpr int SG_PER = 64 * SG_KC / NTH;   // elements of one chunk per thread
+
+__device__ __forceinline__ void sg_index(const SView& v, int e, int& r, int& kk)
 {
-    for (int e = threadIdx.x; e < 64 * SG_KC; e += NTH) {
+    if (v.sk == 1) { r = e / SG_KC; kk = e % SG_KC; }
+    else           { kk = e / 64;   r = e % 64; }
+}
+
+__device__ __forceinline__ void sg_load(const SView& v, int64_t k0, int64_t ke, float (&t)[SG_PER])
+{
+#pragma unroll
+    for (int i = 0; i < SG_PER; ++i) {
         int r, kk;
-        if (v.sk == 1) { r = e / SG_KC; kk = e % SG_KC; }
-        else           { kk = e / 64;   r = e % 64; }
-        dst[kk * 65 + r] = (k0 + kk < ke) ? __ldcg(v.p + (int64_t)r * v.sr + (k0 + kk) * v.sk) : 0.f;
+        sg_index(v, threadIdx.x + i * NTH, r, kk);
+        t[i] = (k0 + kk < ke) ? __ldcg(v.p + (int64_t)r * v.sr + (k0 + kk) * v.sk) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void sg_store(const SView& v, const float (&t)[SG_PER], float* dst)
+{
+#pragma unroll
+    for (int i = 0; i < SG_PER; ++i) {
+        int r, kk;
+        sg_index(v, threadIdx.x + i * NTH, r, kk);
+        dst[kk * 65 + r] = t[i];
     }
 }
 
@@ -52,11 +72,21 @@ __device__ void sgemm64(float (&acc)[4][4], const SView& A, const SView& B, int6
     float* As = sm;
     float* Bs = sm + SG_KC * 65;
     const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+    float ta[SG_PER], tb[SG_PER];   // the next chunk's loads, in flight during this chunk's products
+    __syncthreads();                // the operands may be the block's own writes just before the call
+    if (kb < ke) {
+        sg_load(A, kb, ke, ta);
+        sg_load(B, kb, ke, tb);
+    }
     for (int64_t k0 = kb; k0 < ke; k0 += SG_KC) {
         __syncthreads();
-        sg_stage(A, k0, ke, As);
-        sg_stage(B, k0, ke, Bs);
+        sg_store(A, ta, As);
+        sg_store(B, tb, Bs);
         __syncthreads();
+        if (k0 + SG_KC < ke) {
+            sg_load(A, k0 + SG_KC, ke, ta);
+            sg_load(B, k0 + SG_KC, ke, tb);
+        }
 #pragma unroll 8
         for (int kk = 0; kk < SG_KC; ++kk) {
             float a[4], bv[4];
@@ -92,6 +122,48 @@ __device__ __forceinline__ void sacc_zero(float (&acc)[4][4])
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
 }
 
+// Step j of the register-resident 64 x 64 factor (one warp, lane l holds
+// row l in ra and row l + 32 in rb): pivot, scale column j, rank-1 update of
+// the later columns.  bad = first non-positive pivot.
+template <int J>
+__device__ __forceinline__ void chol64_step(float (&ra)[32], float (&rb)[64], int l, int& bad)
+{
+    const float d = __shfl_sync(0xffffffffu, J < 32 ? ra[J & 31] : rb[J], J & 31);
+    if (!(d > 0.f) && bad < 0) bad = J;
+    const float dj = sqrtf(d), dinv = 1.f / dj;
+    if (J < 32) ra[J & 31] = (l == J) ? dj : ra[J & 31] * dinv;
+    rb[J] = (l + 32 == J) ? dj : rb[J] * dinv;
+#pragma unroll
+    for (int c = J + 1; c < 64; ++c) {
+        const float lc = __shfl_sync(0xffffffffu, c < 32 ? ra[J & 31] : rb[J], c & 31);
+        if (c < 32) ra[c & 31] = fmaf(-ra[J & 31], lc, ra[c & 31]);
+        rb[c] = fmaf(-rb[J], lc, rb[c]);
+    }
+}
+
+template <int... J>
+__device__ __forceinline__ void chol64_steps(float (&ra)[32], float (&rb)[64], int l, int& bad,
+                                             std::integer_sequence<int, J...>)
+{
+    (chol64_step<J>(ra, rb, l, bad), ...);
+}
+
+// Row r of the forward substitution L x = e_c (L in S, row stride 65).
+template <int R>
+__device__ __forceinline__ void trinv64_row(const float* S, int c, float (&x)[64])
+{
+    float s4[4] = {(R == c) ? 1.f : 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < R; ++t) s4[t & 3] = fmaf(-S[R * 65 + t], x[t], s4[t & 3]);
+    x[R] = ((s4[0] + s4[1]) + (s4[2] + s4[3])) / S[R * 65 + R];
+}
+
+template <int... R>
+__device__ __forceinline__ void trinv64_rows(const float* S, int c, float (&x)[64], std::integer_sequence<int, R...>)
+{
+    (trinv64_row<R>(S, c, x), ...);
+}
+
 constexpr int POTRF32_SMEM = (2 * 64 * 65 + SG_FLOATS) * 4;
 
 // Cholesky factor and inverse of one b x b diagonal tile in FP32 (one CTA):
@@ -109,7 +181,6 @@ __global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat
     float* Iv = S + 64 * 65;
     float* gsm = Iv + 64 * 65;
     __shared__ double logacc;
-    __shared__ float rcp;
     __shared__ int fail;
     if (failed(info)) return;
     const int tid = threadIdx.x;
@@ -128,54 +199,63 @@ __global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat
             });
         }
         __syncthreads();
-        for (int e = tid; e < 64 * 64; e += NTH) {
-            const int r = e >> 6, c = e & 63;
-            S[r * 65 + c] = (c <= r) ? __ldcg(App + (int64_t)r * b + c) : 0.f;
-            Iv[r * 65 + c] = 0.f;
+        {   // the 64-block's lower triangle into S, all loads in flight first
+            float t[64 * 64 / NTH];
+#pragma unroll
+            for (int i = 0; i < 64 * 64 / NTH; ++i) {
+                const int e = tid + i * NTH, r = e >> 6, c = e & 63;
+                t[i] = (c <= r) ? __ldcg(App + (int64_t)r * b + c) : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 64 * 64 / NTH; ++i) {
+                const int e = tid + i * NTH;
+                S[(e >> 6) * 65 + (e & 63)] = t[i];
+            }
         }
         __syncthreads();
-        for (int j = 0; j < 64; ++j) {
-            if (tid == 0) {
-                const float piv = S[j * 65 + j];
-                if (piv > 0.f) {
-                    const float sq = sqrtf(piv);
-                    S[j * 65 + j] = sq;
-                    rcp = 1.f / sq;
-                } else {
+        // Unblocked right-looking factor of the 64-block in the registers of
+        // warp 0: lane l holds row l (columns 0..31) and row l + 32; the
+        // multipliers L(c, j) of column j are broadcast by shuffles.  Entries
+        // above the diagonal are scratch and written back as zero.
+        if (tid < 32) {
+            const int l = tid;
+            float ra[32], rb[64];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) ra[c] = S[l * 65 + c];
+#pragma unroll
+            for (int c = 0; c < 64; ++c) rb[c] = S[(l + 32) * 65 + c];
+            int bad = -1;
+            chol64_steps(ra, rb, l, bad, std::make_integer_sequence<int, 64>{});
+            if (bad >= 0) {   // the same pivot on every lane
+                if (l == 0) {
                     fail = 1;
-                    atomicMin(info, (unsigned long long)(row0 + p * 64 + j));
+                    atomicMin(info, (unsigned long long)(row0 + p * 64 + bad));
                 }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) S[l * 65 + c] = (c <= l) ? ra[c] : 0.f;
+#pragma unroll
+                for (int c = 0; c < 64; ++c) S[(l + 32) * 65 + c] = (c <= l + 32) ? rb[c] : 0.f;
             }
-            __syncthreads();
-            if (fail) return;
-            const float dinv = rcp;
-            for (int r = j + 1 + tid; r < 64; r += NTH) S[r * 65 + j] *= dinv;
-            __syncthreads();
-            const int ty = tid >> 4, tx = tid & 15;
-            for (int r = j + 1 + ty; r < 64; r += 16) {
-                const float lr = S[r * 65 + j];
-                for (int c = j + 1 + tx; c <= r; c += 16) S[r * 65 + c] -= lr * S[c * 65 + j];
-            }
-            __syncthreads();
         }
+        __syncthreads();
+        if (fail) return;
         if (tid < 32) {
             double lg = log((double)S[tid * 65 + tid]) + log((double)S[(tid + 32) * 65 + tid + 32]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
             if (tid == 0) logacc += lg;
         }
-        {   // inverse of the 64-block factor, row by row, 4 threads per column
-            const int c = tid >> 2, q = tid & 3;
-            for (int r = 0; r < 64; ++r) {
-                float sum = 0.f;
-                if (c < r)
-                    for (int t = c + q; t < r; t += 4) sum = fmaf(S[r * 65 + t], Iv[t * 65 + c], sum);
-                sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-                sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-                if (q == 0 && c <= r) Iv[r * 65 + c] = ((r == c) ? 1.f : -sum) / S[r * 65 + r];
-                __syncthreads();
-            }
+        // Inverse of the 64-block factor: thread c solves L x = e_c by forward
+        // substitution in registers (x(r) = 0 for r < c falls out exactly).
+        if (tid < 64) {
+            const int c = tid;
+            float x[64];
+            trinv64_rows(S, c, x, std::make_integer_sequence<int, 64>{});
+#pragma unroll
+            for (int r = 0; r < 64; ++r) Iv[r * 65 + c] = x[r];
         }
+        __syncthreads();
         float* Xpp = X + (int64_t)p * 64 * b + p * 64;
         for (int e = tid; e < 64 * 64; e += NTH) {
             const int r = e >> 6, c = e & 63;
@@ -202,13 +282,14 @@ __global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat
         }
     }
     __syncthreads();
-    for (int64_t e = tid; e < b * b; e += NTH) {
-        const int64_t r = e / b, c = e % b;
-        if (c > r) {
-            A[e] = 0.f;
-            X[e] = 0.f;
-        }
-    }
+    // strictly upper 64-blocks of L and X are zero (the diagonal blocks were written whole)
+    for (int q = 0; q < P; ++q)
+        for (int pc = q + 1; pc < P; ++pc)
+            for (int e = tid; e < 64 * 64; e += NTH) {
+                const int64_t o = (int64_t)(q * 64 + (e >> 6)) * b + pc * 64 + (e & 63);
+                A[o] = 0.f;
+                X[o] = 0.f;
+            }
     for (int r = 1; r < P; ++r) {
         for (int q = 0; q < r; ++q) {
             float* Xrq = X + (int64_t)r * 64 * b + q * 64;
@@ -223,13 +304,32 @@ __global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat
         }
     }
     __syncthreads();
-    const int64_t bb = b * b;
-    for (int64_t e = tid; e < bb; e += NTH) {
-        __nv_bfloat16 hi, mid, lo;
-        split3(__ldcg(X + e), hi, mid, lo);
-        XP[e] = hi;
-        XP[bb + e] = mid;
-        XP[2 * bb + e] = lo;
+    const int64_t bb = b * b, q4 = bb / 4;
+    for (int64_t e0 = tid; e0 < q4; e0 += 4 * NTH) {   // planes of X, four float4 loads in flight
+        float4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t e = e0 + i * NTH;
+            v[i] = e < q4 ? __ldcg(reinterpret_cast<const float4*>(X) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t e = e0 + i * NTH;
+            if (e >= q4) continue;
+            const float f[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+            __nv_bfloat16 h[3][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) split3(f[u], h[0][u], h[1][u], h[2][u]);
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl) {
+                __nv_bfloat162 lo2 = __halves2bfloat162(h[pl][0], h[pl][1]);
+                __nv_bfloat162 hi2 = __halves2bfloat162(h[pl][2], h[pl][3]);
+                uint2 w;
+                w.x = *reinterpret_cast<unsigned*>(&lo2);
+                w.y = *reinterpret_cast<unsigned*>(&hi2);
+                reinterpret_cast<uint2*>(XP + pl * bb)[e] = w;
+            }
+        }
     }
     if (tid == 0) *logdet_slot = logacc;
 }
@@ -254,14 +354,21 @@ __global__ void k_split_panel(const float* A32, __nv_bfloat16* PA, int64_t b, in
 // One cooperative launch per solve, every CTA on every step: out = L~^{-1} in
 // (upper = 0) or out = L~^{-T} in (upper = 1), FP32 throughout.  Lower, for
 // t = 0 .. T-1: (A) out_t = Linv_tt (in_t - s_t), the rows of the b x b
-// product spread over all warps; (B) s_i += L_it out_t for every i > t, each
-// of the (T-t-1) b rows owned by one warp (deterministic).  Upper, for
-// t = T-1 .. 0: (A) out_t = Linv_tt^T (in_t - s_t) by four-column groups;
-// (B) s_j += L_tj^T out_t for every j < t, four-column groups over warps.
-// s (Np floats) holds the partial sums; in_t - s_t is formed inside (A).
+// product spread over all warps; (B) s_i += L_it out_t for every i > t.
+// Upper, for t = T-1 .. 0: (A) out_t = Linv_tt^T (in_t - s_t) by four-column
+// groups; (B) s_j += L_tj^T out_t for every j < t.  Phase (B) runs over
+// chunks of SV_CH rows of a tile, one chunk per CTA at a time, eight rows per
+// warp with all of a warp's loads in flight before any product.  Lower: each
+// row's dot product belongs to one warp, s has one copy.  Upper: a chunk's
+// column sums are reduced over its warps in shared memory and added to the
+// chunk's own copy of s (b / SV_CH copies, summed in phase (A)), so every
+// element has one writer per step and the result is deterministic.
 // Phases are separated by a grid barrier (arrival counter and generation
 // word, bounded wait); a timeout sets *err and the kernel leaves, the caller
 // reports it.
+constexpr int SV_CH = 64;     // rows per chunk of a tile in phase (B)
+constexpr int SV_SEG = 256;   // columns per pass: lanes hold 4 lane + 128 u, u = 0, 1
+
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err,
                                              int* okb)
 {
@@ -314,16 +421,28 @@ __device__ __forceinline__ float warp_row_dot(const float* row, const float* x, 
     return sum;
 }
 
-// Four columns c4 .. c4+3 of M^T (x - z) (M b x b row-major, z may be null)
-// over one warp: lanes take rows lane, lane + 32, ...
-__device__ __forceinline__ float4 warp_col4_dot(const float* M, const float* x, const float* z, int64_t b, int64_t c4,
-                                                int lane)
+__device__ __forceinline__ float4 ld4_or0(const float* base, int64_t c, int64_t b, bool stream)
+{
+    if (c >= b) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return stream ? __ldcs((const float4*)(base + c)) : __ldcg((const float4*)(base + c));
+}
+
+__device__ __forceinline__ float dot4(const float4& a, const float4& x)
+{
+    return fmaf(a.x, x.x, fmaf(a.y, x.y, fmaf(a.z, x.z, a.w * x.w)));
+}
+
+// Four columns c4 .. c4+3 of M^T w, w_r = x_r - sum_{k < np} z[k * zs + r]
+// (M b x b row-major) over one warp: lanes take rows lane, lane + 32, ...
+__device__ __forceinline__ float4 warp_col4_dot(const float* M, const float* x, const float* z, int64_t zs, int np,
+                                                int64_t b, int64_t c4, int lane)
 {
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
     for (int64_t r = lane; r < b; r += 32) {
         const float4 v = __ldcs((const float4*)(M + r * b + c4));
-        const float xr = __ldcg(x + r) - (z ? __ldcg(z + r) : 0.f);
+        float xr = __ldcg(x + r);
+        for (int k = 0; k < np; ++k) xr -= __ldcg(z + k * zs + r);
         s.x = fmaf(v.x, xr, s.x);
         s.y = fmaf(v.y, xr, s.y);
         s.z = fmaf(v.z, xr, s.z);
@@ -339,17 +458,87 @@ __device__ __forceinline__ float4 warp_col4_dot(const float* M, const float* x, 
     return s;
 }
 
+// Phase (B), lower: s_i(r0 + k) += L_it(r0 + k, :) . x for the warp's rows k < 8.
+__device__ __forceinline__ void chunk_rows_dot(const float* Lb, const float* x, float* s, int64_t b, int lane)
+{
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    for (int64_t seg = 0; seg < b; seg += SV_SEG) {
+        float4 xv[2], v[8][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) xv[u] = ld4_or0(x, seg + 4 * lane + 128 * u, b, false);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) v[k][u] = ld4_or0(Lb + k * b, seg + 4 * lane + 128 * u, b, true);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += dot4(v[k][0], xv[0]) + dot4(v[k][1], xv[1]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (lane == k) s[k] = __ldcg(s + k) + acc[k];
+}
+
+// Phase (B), upper: s(c) += sum over the chunk's SV_CH rows r of L(r, c) x(r),
+// Lc = the chunk's first row; red = 8 x SV_SEG floats of shared memory.
+__device__ __forceinline__ void chunk_cols_dot(const float* Lc, const float* x, float* s, int64_t b, float* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float* Lb = Lc + (int64_t)warp * 8 * b;
+    float xr[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xr[k] = __ldcg(x + warp * 8 + k);
+    for (int64_t seg = 0; seg < b; seg += SV_SEG) {
+        float4 v[8][2];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) v[k][u] = ld4_or0(Lb + k * b, seg + 4 * lane + 128 * u, b, true);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                a.x = fmaf(v[k][u].x, xr[k], a.x);
+                a.y = fmaf(v[k][u].y, xr[k], a.y);
+                a.z = fmaf(v[k][u].z, xr[k], a.z);
+                a.w = fmaf(v[k][u].w, xr[k], a.w);
+            }
+            *(float4*)(red + warp * SV_SEG + 4 * lane + 128 * u) = a;
+        }
+        __syncthreads();
+        const int64_t c = seg + threadIdx.x;
+        if (threadIdx.x < SV_SEG && c < b) {
+            float sum = 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) sum += red[w * SV_SEG + threadIdx.x];
+            s[c] = __ldcg(s + c) + sum;
+        }
+        __syncthreads();
+    }
+}
+
+// s = sbuf: Np floats (lower) or (b / SV_CH) copies of Np floats (upper).
 __global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* Linv, int64_t b, int64_t T,
                                                   const float* in, float* out, float* sbuf, int upper, unsigned* bar,
                                                   int* err)
 {
+    static_assert(NTH == 256 && NTH / 32 * 8 == SV_CH && NTH >= SV_SEG, "chunk of 8 warps x 8 rows");
     __shared__ int okb;
+    __shared__ __align__(16) float red[8 * SV_SEG];
     if (threadIdx.x == 0) okb = 1;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nw = (int64_t)gridDim.x * (NTH / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (NTH / 32) + (threadIdx.x >> 5);
-    const int64_t Np = T * b;
-    for (int64_t e = (int64_t)blockIdx.x * NTH + threadIdx.x; e < Np; e += (int64_t)gridDim.x * NTH) sbuf[e] = 0.f;
+    const int64_t gw = (int64_t)blockIdx.x * (NTH / 32) + warp;
+    const int64_t Np = T * b, cpt = b / SV_CH;
+    const int np = upper ? (int)cpt : 1;
+    for (int64_t e = (int64_t)blockIdx.x * NTH + threadIdx.x; e < np * Np; e += (int64_t)gridDim.x * NTH)
+        sbuf[e] = 0.f;
     if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
     for (int64_t q = 0; q < T; ++q) {
         const int64_t t = upper ? T - 1 - q : q;
@@ -362,34 +551,25 @@ __global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* 
             }
         } else {
             for (int64_t c4 = 4 * gw; c4 < b; c4 += 4 * nw) {
-                const float4 v = warp_col4_dot(X, in + t * b, sbuf + t * b, b, c4, lane);
+                const float4 v = warp_col4_dot(X, in + t * b, sbuf + t * b, Np, np, b, c4, lane);
                 if (lane == 0) *(float4*)(out + t * b + c4) = v;
             }
         }
         if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
-        // (B) partial sums of the blocks still to solve
+        // (B) partial sums of the blocks still to solve, chunk by chunk
         const float* xt = out + t * b;
         if (!upper) {
-            const int64_t rows = (T - t - 1) * b;
-            for (int64_t R = gw; R < rows; R += nw) {
-                const int64_t i = t + 1 + R / b, r = R % b;
-                const float v = warp_row_dot(Lt + tri_index(i, t) * b * b + r * b, xt, nullptr, b, lane);
-                if (lane == 0) sbuf[i * b + r] += v;
+            const int64_t nch = (T - t - 1) * cpt;
+            for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+                const int64_t i = t + 1 + ch / cpt, r0 = (ch % cpt) * SV_CH + warp * 8;
+                chunk_rows_dot(Lt + tri_index(i, t) * b * b + r0 * b, xt, sbuf + i * b + r0, b, lane);
             }
         } else {
-            const int64_t quads = t * (b / 4);
-            for (int64_t Q = gw; Q < quads; Q += nw) {
-                const int64_t j = Q / (b / 4), c4 = 4 * (Q % (b / 4));
-                const float4 v = warp_col4_dot(Lt + tri_index(t, j) * b * b, xt, nullptr, b, c4, lane);
-                if (lane == 0) {
-                    float4* p = (float4*)(sbuf + j * b + c4);
-                    float4 o = __ldcg(p);
-                    o.x += v.x;
-                    o.y += v.y;
-                    o.z += v.z;
-                    o.w += v.w;
-                    *p = o;
-                }
+            const int64_t nch = t * cpt;
+            for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+                const int64_t j = ch / cpt, kc = ch % cpt;
+                chunk_cols_dot(Lt + tri_index(t, j) * b * b + kc * SV_CH * b, xt + kc * SV_CH,
+                               sbuf + kc * Np + j * b, b, red);
             }
         }
         if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
