@@ -728,6 +728,101 @@ __global__ __launch_bounds__(NT) void k_adjoint(const KT* Kinv, const double* al
     }
 }
 
+// Mixed path: the same partial sums with K_f,ij read from the FP64 K of the
+// factorisation (same hyperparameters; K_f = K - sigma^2 on the diagonal)
+// instead of regenerated with an FP64 exponential, and r2_ij and the sums of
+// one thread's 16 elements in FP32: the FP32 inverse in W bounds the accuracy
+// of this path.  Coordinates are taken relative to the block's first row (in
+// FP64) before rounding to FP32, so differences of nearby points keep their
+// digits.
+__global__ __launch_bounds__(NT) void k_adjoint_k(const float* Kinv, const double* K64, const double* alpha,
+                                                  const double* X, int64_t n, int64_t d, int64_t b,
+                                                  const GpHyperDev* hyp, double* gpart)
+{
+    __shared__ float sp[64 * 17], sq[64 * 17];
+    __shared__ float sa[2][64];
+    __shared__ double red[3][NT];
+    const int P = (int)(b / TB);
+    int64_t i, j;
+    tri_decode(blockIdx.x, i, j);
+    const int rb = blockIdx.y / P, cb = blockIdx.y % P;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const bool live = !(i == j && cb > rb);
+    const int64_t r0 = i * b + (int64_t)rb * TB, c0 = j * b + (int64_t)cb * TB;
+    float r2[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) r2[a][c] = 0.f;
+    if (live) {
+        if (tid < 128) {
+            const int q = tid & 63;
+            const int64_t g = (tid < 64 ? r0 : c0) + q;
+            sa[tid >> 6][q] = g < n ? (float)alpha[g] : 0.f;
+        }
+        for (int64_t d0 = 0; d0 < d; d0 += 16) {
+            __syncthreads();
+            for (int idx = tid; idx < 1024; idx += NT) {
+                const int r = idx >> 4, k = idx & 15;
+                const int64_t gp = r0 + r, gq = c0 + r;
+                const bool kin = d0 + k < d;
+                const double ref = (kin && r0 < n) ? X[r0 * d + d0 + k] : 0.0;
+                sp[r * 17 + k] = (gp < n && kin) ? (float)(X[gp * d + d0 + k] - ref) : 0.f;
+                sq[r * 17 + k] = (gq < n && kin) ? (float)(X[gq * d + d0 + k] - ref) : 0.f;
+            }
+            __syncthreads();
+            const int kmax = (int)((d - d0) < 16 ? (d - d0) : 16);
+            for (int k = 0; k < kmax; ++k) {
+                float pa[4], qc[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) pa[a] = sp[(ty + 16 * a) * 17 + k];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) qc[c] = sq[(tx + 16 * c) * 17 + k];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float t = pa[a] - qc[c];
+                        r2[a][c] = fmaf(t, t, r2[a][c]);
+                    }
+            }
+        }
+    }
+    float s_l = 0.f, s_nu = 0.f, s_s2 = 0.f;
+    if (live) {
+        const double s2 = hyp->s2;
+        const int64_t off = tri_index(i, j) * b * b + (int64_t)rb * TB * b + cb * TB;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int rr = ty + 16 * a, cc = tx + 16 * c;
+                const int64_t gi = r0 + rr, gj = c0 + cc;
+                if (gi >= n || gj >= n || gj > gi) continue;
+                const int64_t e = off + (int64_t)rr * b + cc;
+                const float w = __ldcs(Kinv + e) - sa[0][rr] * sa[1][cc];
+                const float kf = (float)(gi == gj ? __ldcs(K64 + e) - s2 : __ldcs(K64 + e));
+                const float wt = (gi == gj) ? 1.f : 2.f;
+                s_l = fmaf(wt * w * kf, r2[a][c], s_l);
+                s_nu = fmaf(wt * w, kf, s_nu);
+                if (gi == gj) s_s2 += w;
+            }
+    }
+    red[0][tid] = s_l;
+    red[1][tid] = s_nu;
+    red[2][tid] = s_s2;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (tid < o)
+            for (int p = 0; p < 3; ++p) red[p][tid] += red[p][tid + o];
+        __syncthreads();
+    }
+    if (tid < 3) {
+        const int64_t blk = (int64_t)blockIdx.x * gridDim.y + blockIdx.y;
+        gpart[blk * 3 + tid] = red[tid][0];
+    }
+}
+
 // grad = 1/2 (sum_l / l^2, sum_nu, sigma^2 sum_s2), deterministic single-CTA reduction.
 __global__ void k_grad_finish(const double* gpart, int64_t nblk, const GpHyperDev* hyp, double* scal)
 {
@@ -981,7 +1076,7 @@ void adjoint_grad(gp_t h)
     const int P = (int)(h->b / TB);
     dim3 grid((unsigned)(T * (T + 1) / 2), (unsigned)(P * P));
     if (h->opt.prec == GP_MIXED)
-        GPK_LAUNCH(h, GP_PH_ADJOINT, k_adjoint<float>, grid, NT, 0, (const float*)h->Kinv32,
+        GPK_LAUNCH(h, GP_PH_ADJOINT, k_adjoint_k, grid, NT, 0, (const float*)h->Kinv32, (const double*)h->L,
                    (const double*)h->alpha, (const double*)h->X, h->n, h->d, h->b, (const GpHyperDev*)h->hyp,
                    h->gpart);
     else
