@@ -801,20 +801,60 @@ __device__ __forceinline__ double pow2_ceil(double x)   // smallest power of two
     return (f == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
 }
 
-// Balanced base-2^OZ_B digits of a in [-1, 1]: q = rint(a 2^(OZ_B OZ_S))
-// (exact in a 64-bit integer), d_s = q rounded to a multiple of
+// Binary exponent of a power of two (a normal double).
+__device__ __forceinline__ int pow2_exp(double p) { return (int)((__double_as_longlong(p) >> 52) & 0x7ff) - 1023; }
+
+// rint(mant 2^(e2 + sc)) with the sign neg, in integer arithmetic: round half
+// to even, as rint in the default rounding mode; exact whenever the result is
+// below 2^62.  No FP64 instruction is involved.
+__device__ __forceinline__ long long rint_scaled_bits(unsigned long long mant, int e2, bool neg, int sc)
+{
+    const int s = -(e2 + sc);   // right shift of the significand
+    unsigned long long q;
+    if (mant == 0 || s >= 64) {
+        q = 0;
+    } else if (s <= 0) {
+        q = mant << (-s);
+    } else {
+        q = mant >> s;
+        const unsigned long long rem = mant & ((1ull << s) - 1), half = 1ull << (s - 1);
+        q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+    }
+    return neg ? -(long long)q : (long long)q;
+}
+
+// rint(v 2^sc) from the IEEE-754 fields of v (v = mant 2^e2, subnormals included).
+__device__ __forceinline__ long long rint_scaled(double v, int sc)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((u >> 52) & 0x7ff);
+    unsigned long long m = u & 0xfffffffffffffull;
+    if (ex) m |= 1ull << 52;
+    return rint_scaled_bits(m, (ex ? ex : 1) - 1075, (u >> 63) != 0, sc);
+}
+
+__device__ __forceinline__ long long rint_scaled(float v, int sc)
+{
+    const unsigned u = __float_as_uint(v);
+    const int ex = (int)((u >> 23) & 0xff);
+    unsigned long long m = u & 0x7fffffu;
+    if (ex) m |= 1ull << 23;
+    return rint_scaled_bits(m, (ex ? ex : 1) - 150, (u >> 31) != 0, sc);
+}
+
+// Balanced base-2^OZ_B digits of a in [-1, 1] given q = rint(a 2^(OZ_B OZ_S))
+// (exact in a 64-bit integer): d_s = q rounded to a multiple of
 // 2^(OZ_B (OZ_S - s)) and removed from q, most significant first, so that
 // a ~ sum_s d_s 2^{-OZ_B s} with |d_1| <= 2^OZ_B, |d_s| <= 2^(OZ_B - 1) for
 // s > 1, the error at most 2^{-OZ_B OZ_S - 1}.
-__device__ __forceinline__ void oz_digits(double a, __nv_bfloat16 (&d)[OZ_S])
+__device__ __forceinline__ void oz_digits(long long q, __nv_bfloat16 (&d)[OZ_S])
 {
-    long long q = llrint(ldexp(a, OZ_B * OZ_S));
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
         const int sh = OZ_B * (OZ_S - 1 - s);
         const long long dg = sh > 0 ? ((q + (1ll << (sh - 1))) >> sh) : q;
         q -= dg * (1ll << sh);
-        d[s] = __float2bfloat16_rn((float)dg);
+        d[s] = __int2bfloat16_rn((int)dg);
     }
 }
 
@@ -835,10 +875,10 @@ __global__ void k_yslices(const float* Y, int64_t Np, __nv_bfloat16* YS, int64_t
     }
     const double m = red[0] > 0.f ? pow2_ceil((double)red[0]) : 1.0;
     if (threadIdx.x == 0) mu[row] = m;
-    const double inv = 1.0 / m;
+    const int sc = OZ_B * OZ_S - pow2_exp(m);   // y / m 2^(OZ_B OZ_S) = y 2^sc
     for (int64_t c = threadIdx.x; c < Np; c += NTH) {
         __nv_bfloat16 d[OZ_S];
-        oz_digits((double)y[c] * inv, d);
+        oz_digits(rint_scaled(y[c], sc), d);
 #pragma unroll
         for (int s = 0; s < OZ_S; ++s) YS[s * ps + row * Np + c] = d[s];
     }
@@ -855,7 +895,7 @@ __global__ void k_kslices(const double* K64, int64_t b, int64_t Np, const GpHype
     __shared__ double tile[64][65];
     const double kappa = pow2_ceil(fmax(hyp->nu + hyp->s2, 1.0));
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *kappa_out = kappa;
-    const double inv = 1.0 / kappa;
+    const int sc = OZ_B * OZ_S - pow2_exp(kappa);   // v / kappa 2^(OZ_B OZ_S) = v 2^sc
     const int64_t R0 = (int64_t)blockIdx.y * 64, C0 = (int64_t)blockIdx.x * 64;
     const int64_t LR = R0 >= C0 ? R0 : C0, LC = R0 >= C0 ? C0 : R0;   // lower block
     const double* src = K64 + tri_index(LR / b, LC / b) * b * b + (LR % b) * b + (LC % b);
@@ -872,7 +912,7 @@ __global__ void k_kslices(const double* K64, int64_t b, int64_t Np, const GpHype
         else if (R0 < C0) v = tile[c][r];
         else v = (c <= r) ? tile[r][c] : tile[c][r];
         __nv_bfloat16 d[OZ_S];
-        oz_digits(v * inv, d);
+        oz_digits(rint_scaled(v, sc), d);
         const int64_t o = (R0 + r) * Np + C0 + c;
 #pragma unroll
         for (int s = 0; s < OZ_S; ++s) KS[s * ps + o] = d[s];
