@@ -30,14 +30,16 @@ constexpr int NTH = 256;
 // ---------------------------------------------------------------- FP32 diagonal-tile factor
 // 64 x 64 FP32 block product for the diagonal tile: acc(r, c) += sum over k in
 // [kb, ke) of A(r, k) B(c, k), element (row, k) of a view at p[row*sr + k*sk].
-// 256 threads as 16 x 16, thread (tr, tc) owns rows tr + 16 i, columns tc + 16 j.
+// 256 threads as 16 x 16, thread (tr, tc) owns rows 4 tr + i, columns 4 tc + j,
+// so one k step reads its operands with two 16-byte shared-memory loads.
 struct SView {
     const float* p;
     int64_t sr, sk;
 };
 
 constexpr int SG_KC = 32;                     // k per shared-memory chunk
-constexpr int SG_FLOATS = 2 * SG_KC * 65;     // A and B chunks, k-major, padded
+constexpr int SG_LD = 68;                     // padded row of a k-major chunk (16-byte aligned)
+constexpr int SG_FLOATS = 2 * SG_KC * SG_LD;  // A and B chunks, k-major, padded
 
 constexpr int SG_PER = 64 * SG_KC / NTH;   // elements of one chunk per thread
 
@@ -63,14 +65,14 @@ __device__ __forceinline__ void sg_store(const SView& v, const float (&t)[SG_PER
     for (int i = 0; i < SG_PER; ++i) {
         int r, kk;
         sg_index(v, threadIdx.x + i * NTH, r, kk);
-        dst[kk * 65 + r] = t[i];
+        dst[kk * SG_LD + r] = t[i];
     }
 }
 
 __device__ void sgemm64(float (&acc)[4][4], const SView& A, const SView& B, int64_t kb, int64_t ke, float* sm)
 {
     float* As = sm;
-    float* Bs = sm + SG_KC * 65;
+    float* Bs = sm + SG_KC * SG_LD;
     const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
     float ta[SG_PER], tb[SG_PER];   // the next chunk's loads, in flight during this chunk's products
     __syncthreads();                // the operands may be the block's own writes just before the call
@@ -89,12 +91,9 @@ __device__ void sgemm64(float (&acc)[4][4], const SView& A, const SView& B, int6
         }
 #pragma unroll 8
         for (int kk = 0; kk < SG_KC; ++kk) {
-            float a[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                a[i] = As[kk * 65 + tr + 16 * i];
-                bv[i] = Bs[kk * 65 + tc + 16 * i];
-            }
+            const float4 a4 = *reinterpret_cast<const float4*>(As + kk * SG_LD + 4 * tr);
+            const float4 b4 = *reinterpret_cast<const float4*>(Bs + kk * SG_LD + 4 * tc);
+            const float a[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -104,14 +103,23 @@ __device__ void sgemm64(float (&acc)[4][4], const SView& A, const SView& B, int6
     __syncthreads();
 }
 
+// f(row, first column, the thread's four consecutive results of that row)
 template <class F>
-__device__ __forceinline__ void sacc_for_each(const float (&acc)[4][4], F&& f)
+__device__ __forceinline__ void sacc_rows(const float (&acc)[4][4], F&& f)
 {
     const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) f(tr + 16 * i, tc + 16 * j, acc[i][j]);
+    for (int i = 0; i < 4; ++i) f(4 * tr + i, 4 * tc, make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
+}
+
+__device__ __forceinline__ void sub4_cg(float* q, const float4& v)   // *q -= v, q 16-byte aligned
+{
+    float4 o = __ldcg(reinterpret_cast<const float4*>(q));
+    o.x -= v.x;
+    o.y -= v.y;
+    o.z -= v.z;
+    o.w -= v.w;
+    *reinterpret_cast<float4*>(q) = o;
 }
 
 __device__ __forceinline__ void sacc_zero(float (&acc)[4][4])
@@ -176,7 +184,7 @@ constexpr int POTRF32_SMEM = (2 * 64 * 65 + SG_FLOATS) * 4;
 __global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat16* XP, int64_t b, int64_t row0,
                                                  double* logdet_slot, unsigned long long* info)
 {
-    extern __shared__ float fsm[];
+    extern __shared__ __align__(16) float fsm[];
     float* S = fsm;
     float* Iv = S + 64 * 65;
     float* gsm = Iv + 64 * 65;
@@ -193,10 +201,7 @@ __global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat
             sacc_zero(acc);
             const SView va{A + (int64_t)p * 64 * b, b, 1};
             sgemm64(acc, va, va, 0, (int64_t)p * 64, gsm);
-            sacc_for_each(acc, [&](int r, int c, float v) {
-                float* q = App + (int64_t)r * b + c;
-                *q = __ldcg(q) - v;
-            });
+            sacc_rows(acc, [&](int r, int c, const float4& v) { sub4_cg(App + (int64_t)r * b + c, v); });
         }
         __syncthreads();
         {   // the 64-block's lower triangle into S, all loads in flight first
@@ -270,15 +275,14 @@ __global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat
                 sacc_zero(acc);
                 sgemm64(acc, SView{A + (int64_t)r * 64 * b, b, 1}, SView{A + (int64_t)p * 64 * b, b, 1}, 0,
                         (int64_t)p * 64, gsm);
-                sacc_for_each(acc, [&](int rr, int c, float v) {
-                    float* q = Arp + (int64_t)rr * b + c;
-                    *q = __ldcg(q) - v;
-                });
+                sacc_rows(acc, [&](int rr, int c, const float4& v) { sub4_cg(Arp + (int64_t)rr * b + c, v); });
             }
             float acc[4][4];
             sacc_zero(acc);
             sgemm64(acc, SView{Arp, b, 1}, SView{Xpp, b, 1}, 0, 64, gsm);
-            sacc_for_each(acc, [&](int rr, int c, float v) { Arp[(int64_t)rr * b + c] = v; });
+            sacc_rows(acc, [&](int rr, int c, const float4& v) {
+                *reinterpret_cast<float4*>(Arp + (int64_t)rr * b + c) = v;
+            });
         }
     }
     __syncthreads();
@@ -297,23 +301,27 @@ __global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat
             sacc_zero(acc);
             sgemm64(acc, SView{A + (int64_t)r * 64 * b, b, 1}, SView{X + q * 64, 1, b}, (int64_t)q * 64,
                     (int64_t)r * 64, gsm);
-            sacc_for_each(acc, [&](int rr, int c, float v) { Xrq[(int64_t)rr * b + c] = v; });
+            sacc_rows(acc, [&](int rr, int c, const float4& v) {
+                *reinterpret_cast<float4*>(Xrq + (int64_t)rr * b + c) = v;
+            });
             sacc_zero(acc);
             sgemm64(acc, SView{X + (int64_t)r * 64 * b + r * 64, b, 1}, SView{Xrq, 1, b}, 0, 64, gsm);
-            sacc_for_each(acc, [&](int rr, int c, float v) { Xrq[(int64_t)rr * b + c] = -v; });
+            sacc_rows(acc, [&](int rr, int c, const float4& v) {
+                *reinterpret_cast<float4*>(Xrq + (int64_t)rr * b + c) = make_float4(-v.x, -v.y, -v.z, -v.w);
+            });
         }
     }
     __syncthreads();
     const int64_t bb = b * b, q4 = bb / 4;
-    for (int64_t e0 = tid; e0 < q4; e0 += 4 * NTH) {   // planes of X, four float4 loads in flight
-        float4 v[4];
+    for (int64_t e0 = tid; e0 < q4; e0 += 8 * NTH) {   // planes of X, eight float4 loads in flight
+        float4 v[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 8; ++i) {
             const int64_t e = e0 + i * NTH;
             v[i] = e < q4 ? __ldcg(reinterpret_cast<const float4*>(X) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 8; ++i) {
             const int64_t e = e0 + i * NTH;
             if (e >= q4) continue;
             const float f[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
