@@ -67,7 +67,8 @@ typedef struct {
 
 typedef struct {
     int n_tiles;            /* tiles per dimension T (paper: 1, 4, 16); tile size is
-                               ceil(n / T) rounded up to a multiple of 64 */
+                               ceil(n / T) rounded up to a multiple of 64 (128 for
+                               GP_MIXED); 0 chooses T = gp_auto_tiles(n) */
     gp_precision prec;      /* GP_FP64 or GP_MIXED */
     int noisy_test_var;     /* 1: add sigma^2 to predictive (co)variances */
     double refine_tol;      /* GP_MIXED: stop refinement at ||r|| / ||y|| < tol */
@@ -86,9 +87,19 @@ typedef struct {
  * scheduler, variance correction on, DAG wait bound 10000 ms. */
 void gp_default_options(gp_options* opt);
 
+/* Automatic tile count (the tile-size selection the paper leaves to future
+ * work, Section 6): T = ceil(n / 256), i.e. tiles of 256.  Measured on GB300
+ * for both precisions at n = 8192, 16384 and 32768 against tiles of 128, 512
+ * and 1024: larger tiles lengthen the single-SM diagonal factor on the
+ * critical path of the tile DAG (Fig. 1), smaller ones give narrower tensor
+ * units and more launches.  Returns 0 for n < 1.  Pure host function: no
+ * device work, callable without a GPU. */
+int64_t gp_auto_tiles(int64_t n);
+
 /* Creates a GP over n training points X (n x d) with targets y (n).  Copies
  * X and y to the device.  Fails with GP_ERR_ARG on NULL pointers, n < 1,
- * d < 1 or d > 1024, n_tiles < 1, non-positive l or nu or negative sigma^2. */
+ * d < 1 or d > 1024, n_tiles < 0, non-positive l or nu or negative sigma^2.
+ * n_tiles = 0 takes gp_auto_tiles(n). */
 gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d,
                     const gp_hyper* hyper, const gp_options* opt, gp_t* out);
 

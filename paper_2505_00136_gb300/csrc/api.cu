@@ -1,6 +1,7 @@
 // C ABI entry points (include/gprat_gb.h): handle lifecycle, argument
 // validation, host/device pointer detection and stream-ordered orchestration
 // of the kernels.  No call throws; every failure becomes a gp_status.
+#include <limits.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -446,6 +447,12 @@ int64_t gp_launch_count(gp_t h) { return h ? h->launches : -1; }
 
 extern "C" {
 
+int64_t gp_auto_tiles(int64_t n)
+{
+    constexpr int64_t kTile = 256;   // fastest tile edge measured on GB300, both precisions
+    return n < 1 ? 0 : (n + kTile - 1) / kTile;
+}
+
 void gp_default_options(gp_options* opt)
 {
     if (!opt) return;
@@ -507,12 +514,17 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     gp_options opt;
     if (opt_in) opt = *opt_in;
     else gp_default_options(&opt);
-    if (!X || !y || n < 1 || d < 1 || d > 1024 || !hyper_ok(hyper) || opt.n_tiles < 1 ||
+    if (!X || !y || n < 1 || d < 1 || d > 1024 || !hyper_ok(hyper) || opt.n_tiles < 0 ||
         (opt.prec != GP_FP64 && opt.prec != GP_MIXED) ||
         (opt.scheduler != GP_SCHED_STREAM && opt.scheduler != GP_SCHED_PERSISTENT) ||
         (opt.scheduler == GP_SCHED_PERSISTENT && opt.prec != GP_FP64) || opt.dag_timeout_ms < 0)
         return GP_ERR_ARG;
     if (opt.dag_timeout_ms == 0) opt.dag_timeout_ms = 10000;
+    if (opt.n_tiles == 0) {
+        const int64_t t = gp_auto_tiles(n);
+        if (t > INT_MAX) return GP_ERR_ARG;
+        opt.n_tiles = (int)t;
+    }
     gp_t h = new (std::nothrow) gp_handle();
     if (!h) return GP_ERR_OOM;
     memset((void*)h, 0, sizeof(*h));

@@ -85,6 +85,7 @@ _SIGS = {
     "gp_profile": (ctypes.c_int, [_H, ctypes.c_int]),
     "gp_profile_read": (ctypes.c_int, [_H, _vp, _vp, ctypes.c_int]),
     "gp_launch_count": (_i64, [_H]),
+    "gp_auto_tiles": (_i64, [_i64]),
     "gp_predict_mean_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, ctypes.c_double,
                                                ctypes.c_double, _vp, _vp]),
     "gp_summary": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
@@ -139,6 +140,12 @@ def _check(status, h=None, where=""):
     if status != GP_OK:
         info = _lib.gp_last_error_info(h) if h else -1
         raise GPError(status, info, where)
+
+
+def auto_tiles(n: int) -> int:
+    """Tiles per dimension chosen for n training points (``gp_auto_tiles``);
+    ``GP(..., n_tiles=0)`` uses it."""
+    return int(_lib.gp_auto_tiles(int(n)))
 
 
 def default_options() -> gp_options:

@@ -70,7 +70,20 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
         assert st == g.GP_ERR_ARG
     bad = g.gp_hyper(-1.0, 1.0, 0.1, (ctypes.c_int * 3)(1, 1, 1))
     assert g.gp_create(px, py, 4, 2, ctypes.byref(bad), ctypes.byref(opt), ctypes.byref(h)) == g.GP_ERR_ARG
-    opt.n_tiles = 0
+    opt.n_tiles = -1                        # 0 selects gp_auto_tiles; negative is invalid
     assert g.gp_create(px, py, 4, 2, ctypes.byref(hp), ctypes.byref(opt), ctypes.byref(h)) == g.GP_ERR_ARG
     assert g.gp_factor(None) == g.GP_ERR_ARG
     assert g.gp_status_str(g.GP_ERR_NOT_PD) == b"matrix not positive definite"
+
+
+def test_auto_tiles_gives_tiles_of_256(lib):
+    """Automatic tile count: T = ceil(n / 256), the tile edge measured fastest
+    on GB300 for both precisions (host logic only)."""
+    from paper_2505_00136_gb300 import gprat as g
+    for n, t in [(0, 0), (-5, 0), (1, 1), (256, 1), (257, 2), (1024, 4), (8192, 32), (32768, 128),
+                 (65536, 256), (100000, 391)]:
+        assert g.auto_tiles(n) == t, (n, g.auto_tiles(n))
+    for n in range(1, 3000, 37):
+        t = g.auto_tiles(n)
+        b = -(-n // t)                      # tile edge gp_create derives before rounding up
+        assert b <= 256 and (t == 1 or -(-n // (t - 1)) > 256)

@@ -70,6 +70,17 @@ def test_many_regressors_degenerate_unit_lengthscale(g, orc):
     check_predict(g, orc, X, y, Xs, (1.0, 1.0, 0.1), n_tiles=2, cov=False)
 
 
+def test_automatic_tile_count(g, orc):
+    """n_tiles = 0 takes gp_auto_tiles(n): 1000 points -> 4 tiles of 256 (ragged
+    last tile), same results as the oracle."""
+    X, y, Xs, _ = dg.msd_dataset(1000, 96, 8, seed=1005)
+    assert g.auto_tiles(1000) == 4
+    with g.GP(X, y, (1.0, 1.0, 0.1), n_tiles=0) as gp:
+        info = gp.info()
+        assert info["n_tiles"] == 4 and info["tile"] == 256
+    check_predict(g, orc, X, y, Xs, (1.0, 1.0, 0.1), n_tiles=0, cov=False)
+
+
 def test_tile_count_invariance_and_factor(g, orc):
     X, y, Xs, _ = dg.msd_dataset(1024, 128, 8, seed=1001)
     hyp = (1.0, 1.0, 0.1)
