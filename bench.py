@@ -26,6 +26,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -145,7 +146,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: GPRAT_CLOCKS_DIR if set, else the system temporary directory
+        cdir = os.environ.get("GPRAT_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(cdir, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
