@@ -202,6 +202,24 @@ def update_flops(T, b):
     return tot
 
 
+def replica_seed(rank):
+    """Every rank of a multi-GPU launch solves its own problem (replicas, no
+    data-path exchange): seed 1002 + rank."""
+    return 1002 + rank
+
+
+def max_over_ranks(values, device):
+    """Element-wise maximum over the ranks of the initialised process group
+    (the slowest replica sets the job's time); the values themselves when
+    there is no group or it has one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -222,7 +240,7 @@ def run_ours(args):
     from paper_2505_00136_gb300 import datagen as dg
     from paper_2505_00136_gb300 import gprat
 
-    seed = 1002 + rank
+    seed = replica_seed(rank)
     Xh, yh, Xsh, _ = dg.msd_dataset(args.n, args.m, args.d, seed)
     X = torch.from_numpy(Xh).to(dev)
     y = torch.from_numpy(yh).to(dev)
@@ -269,10 +287,7 @@ def run_ours(args):
                       + ph["rsolve"])
     grad_ms = factor_ms + ph["trtri"] + ph["lauum"] + ph["adjoint"] + ph["adam"]
     ms_per_step = total_ms / K
-    vals = torch.tensor([predict_var_ms, grad_ms, ms_per_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    predict_var_ms, grad_ms, ms_per_step = (float(v) for v in vals.cpu())
+    predict_var_ms, grad_ms, ms_per_step = max_over_ranks([predict_var_ms, grad_ms, ms_per_step], dev)
 
     # roofline of the dominant kernel (largest share of the step in the ncu launch list)
     upd_launch_ms = prof["update"][0] / max(prof["update"][1], 1)
