@@ -1,19 +1,25 @@
 // Mixed-precision hot path (GP_MIXED): FP32-accurate split-BF16 tile products
 // on the BF16 tensor pipe, FP64 where accuracy is decided.
 //
-//  - K is assembled once in FP64 (kept for residuals) and in FP32 (working copy).
-//  - Tiled right-looking Cholesky (Fig. 1) on the FP32 copy: each diagonal tile
-//    is factored and inverted in FP32 by one CTA (k_potrf32), the panel TRSM
-//    (L_ik = A_ik Linv_kk^T) and the trailing SYRK/GEMM run as bf16x6 products
-//    with FP32 accumulation on the tensor cores.  Every finished off-diagonal
+//  - K is assembled once in FP64 (kept for residuals, the exact product and
+//    the gradient) and in FP32 (working copy).
+//  - Tiled right-looking Cholesky (Fig. 1) on the FP32 copy, in super-panels
+//    of SWEEP_BLOCK tile columns: each diagonal tile is factored and inverted
+//    in FP32 by one CTA (k_potrf32), the panel TRSM (L_ik = A_ik Linv_kk^T)
+//    and the trailing SYRK/GEMM run as bf16x6 products with FP32 accumulation
+//    on the tensor cores (kernels_tgemm.cu).  Every finished off-diagonal
 //    tile of L is also kept as three BF16 planes, the operand format of later
 //    products.
 //  - log|K| = 2 sum log L_jj, the logarithms taken and summed in FP64.
 //  - alpha = K^{-1} y by iterative refinement: FP32 triangular solves with the
-//    mixed factor, residual y - K alpha in FP64 against the FP64 K.
+//    mixed factor (one cooperative launch per solve, k_solve32p), residual
+//    y - K alpha in FP64 against the FP64 K (k_sym_resid).
 //  - Prediction: the mean is K_{Z*,Z} alpha in FP64 (fused into the cross-
-//    covariance assembly); the variance uses W = K_{Z*,Z} L^{-T} from bf16x6
-//    products, var = k** - rowsum(W^2).
+//    covariance assembly).  Variances: W = K_{Z*,Z} L^{-T} from bf16x6
+//    products gives x0 = L^{-T} W^T; with r0 = k* - K x0 from the exact digit
+//    product (kernels_tc.cu) the quadratic form is k*^T x0 + x0^T r0 +
+//    ||L^{-1} r0||^2, FP64-accurate up to a third-order term; without the
+//    correction var = k** - rowsum(W^2).
 #include <cuda_bf16.h>
 #include <math.h>
 
