@@ -3,22 +3,23 @@
 Workload (default): N = 32768 training and M = 8192 test points of the seeded
 mass-spring-damper generator, 8 lagged-input regressors, (l, nu, sigma^2) =
 (1, 1, 0.1); mixed precision (128 x 128 tiles of 256) by default, with one
-FP64 run (same tiles) on the same inputs for the speed-up and the
-per-output relative errors; --precision fp64 benchmarks the FP64 path.
-Inputs are resident in HBM before the timed region; the factor alone (4.3 GB
-of tiles) is far larger than L2.
+FP64 run (same tiles) on the same inputs for the speed-ups and the
+per-output relative errors, and the same workload with 128 regressors;
+--precision fp64 benchmarks the FP64 path.  Inputs are resident in HBM
+before the timed region; the factor alone (4.3 GB of tiles) is far larger
+than L2.
 
-One step = one pass of the whole hot path:
-  set_hyper(theta0) ; gp_predict(Xs -> mean, var, full cov)      (assembly, Cholesky,
-                                                                  solves, cross-covariance,
-                                                                  multi-RHS solve, mean,
-                                                                  variance, covariance)
-                    ; gp_optimize(1 step, reusing the factor)    (NLML, K^{-1}, adjoint
-                                                                  gradient, Adam)
-Headline value: predict+variance ms (the predict call minus its covariance
-phase), plus NLML+grad steps/s, both from per-launch CUDA events of the timed
-steps.  --impl reference times the plain FP64 CPU oracle on a bounded sample of
-the same workload and scales it by the algorithmic flop count.
+One step = one pass of the whole hot path, three calls on the handle:
+  set_hyper(theta0) ; gp_predict(Xs -> mean, var)   predict+variance (assembly, Cholesky,
+                                                    alpha, cross-covariance, multi-RHS solve,
+                                                    mean, variance and its correction)
+  gp_predict(Xs -> full covariance)                 on the same factor
+  set_hyper(theta0) ; gp_optimize(1 step)           NLML+grad (assembly, Cholesky, alpha,
+                                                    NLML, K^{-1}, adjoint gradient, Adam)
+Headline value: predict+variance ms, plus NLML+grad steps/s, each the mean
+over the timed steps of one CUDA-event interval around its call sequence.
+--impl reference times the plain FP64 CPU oracle on a bounded sample of the
+same workload and scales each phase by its own operation count.
 """
 from __future__ import annotations
 
@@ -36,9 +37,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "predict+variance ms & NLML+grad steps/s @n=32768; mixed vs FP64 at 1e-8 rel"
-# DRAM bytes (read + write) of one k_ozaki_tc launch at N = 32768, M = 8192, from the
-# ncu capture of that launch (None until a capture of the current kernel exists).
-OZAKI_TRAFFIC_PER_LAUNCH = 201.14e9 + 1.20e9
+# Exact digit-pair products of k_ozaki_tc: x~0 in 2 digits, K in 6, pairs (s, u) with s + u <= 7.
+OZAKI_PAIRS = 11
+# DRAM bytes (read + write) of one k_ozaki_tc launch at N = 32768, M = 8192, from an
+# ncu capture of the current kernel (None until one exists).
+OZAKI_TRAFFIC_PER_LAUNCH = None
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL_BF16_TFLOPS = 2250.0      # dense, per GPU
 NOMINAL_FP64_TFLOPS = 1.25
@@ -61,6 +64,7 @@ def parse():
     ap.add_argument("--cpu-sample-m", type=int, default=128)
     ap.add_argument("--no-compare", action="store_true", help="mixed: skip the FP64 comparison run")
     ap.add_argument("--fp64-tiles", type=int, default=128)
+    ap.add_argument("--no-d128", action="store_true", help="mixed: skip the 128-regressor line")
     ap.add_argument("--no-learned-init", action="store_true",
                     help="skip the learned-initialiser measurement (small corpus, untimed for value)")
     args = ap.parse_args()
@@ -85,13 +89,22 @@ def peaks():
         return None
 
 
+_FP64_PEAK = None
+
+
 def fp64_peak():
-    """FP64 tensor peak: measured bf16 burst x nominal FP64/BF16 ratio (or the fallback)."""
-    pk = peaks()
-    if pk and "bf16_tflops" in pk:
-        return pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS, \
-            "of measured (bf16 burst x nominal fp64/bf16)"
-    return 1900.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS, "of fallback (1.9 PF bf16 x nominal fp64/bf16)"
+    """FP64 tensor peak: mma.sync.m8n8k4.f64 throughput measured on this GPU in this
+    run (gp_measure_fp64_peaks), else the fallback (nominal FP64/BF16 ratio x 1.9 PF)."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        try:
+            from paper_2505_00136_gb300 import gprat
+            dmma, _ = gprat.measure_fp64_peaks()
+            _FP64_PEAK = (dmma, "of measured (mma.sync f64 throughput loop, this run)")
+        except Exception:   # no device: fallback figure
+            _FP64_PEAK = (1900.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS,
+                          "of fallback (1.9 PF bf16 x nominal fp64/bf16)")
+    return _FP64_PEAK
 
 
 # ---------------------------------------------------------------- CPU oracle baseline
@@ -220,6 +233,53 @@ def max_over_ranks(values, device):
     return [float(v) for v in t.cpu()]
 
 
+def profiled_step(gprat, gp, Xs):
+    """timed_step's three calls with per-launch events: phase ms and launch
+    counts of each call (predict+variance, full covariance, NLML+grad)."""
+    gp.profile(True)
+    gp.profile_read()
+    gp.set_hyper(HYP0)
+    gp.predict(Xs, mean=True, var=True)
+    p_pv = gp.profile_read()
+    gp.predict(Xs, mean=False, var=False, cov=True)
+    p_cv = gp.profile_read()
+    gp.set_hyper(HYP0)
+    st = gprat._lib.gp_optimize(gp.h, 1, 0.1, None)
+    if st != gprat.GP_OK:
+        raise gprat.GPError(st, -1, "gp_optimize")
+    p_ng = gp.profile_read()
+    gp.profile(False)
+    return p_pv, p_cv, p_ng
+
+
+def timed_step(gprat, gp, Xs, stream, torch):
+    """One pass of the whole hot path, with CUDA events on the handle's stream
+    around its two timed calls:
+      predict+variance: set_hyper(theta0) ; gp_predict(Xs -> mean, var)
+        (assembly, Cholesky, alpha, cross-covariance, multi-RHS solve, mean,
+        variance; on the mixed path also the variance correction);
+      full covariance: gp_predict(Xs -> cov) on the same factor;
+      NLML+grad step: set_hyper(theta0) ; gp_optimize(1 step)
+        (assembly, Cholesky, alpha, NLML, K^{-1}, adjoint gradient, Adam).
+    Returns the three intervals in ms."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    gp.set_hyper(HYP0)
+    ev[0].record(stream)
+    gp.predict(Xs, mean=True, var=True)
+    ev[1].record(stream)
+    ev[2].record(stream)
+    gp.predict(Xs, mean=False, var=False, cov=True)
+    ev[3].record(stream)
+    gp.set_hyper(HYP0)
+    ev[4].record(stream)
+    st = gprat._lib.gp_optimize(gp.h, 1, 0.1, None)
+    ev[5].record(stream)
+    if st != gprat.GP_OK:
+        raise gprat.GPError(st, -1, "gp_optimize")
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3]), ev[4].elapsed_time(ev[5])
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -250,101 +310,71 @@ def run_ours(args):
     info = gp.info()
     T, b = info["n_tiles"], info["tile"]
 
-    def step():
-        gp.set_hyper(HYP0)
-        gp.predict(Xs, mean=True, var=True, cov=True)
-        gp.optimize(1, lr=0.1)
-
     for _ in range(args.warmup):
-        step()
+        timed_step(gprat, gp, Xs, stream, torch)
     torch.cuda.synchronize(dev)
-    gp.profile(True)
-    gp.profile_read()
     l0 = gp.launch_count()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    pv, cv, ng = [], [], []
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            step()
+            a, c, g = timed_step(gprat, gp, Xs, stream, torch)
+            pv.append(a)
+            cv.append(c)
+            ng.append(g)
         e1.record(stream)
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     total_ms = e0.elapsed_time(e1)
     launches = gp.launch_count() - l0
-    prof = gp.profile_read()
-    gp.profile(False)
     K = args.steps
-    ph = {k: v[0] / K for k, v in prof.items()}
-    factor_ms = ph["assemble"] + ph["potrf"] + ph["trsm"] + ph["update"] + ph["solve"] + ph["refine"]
-    # predict+variance = factor + cross-covariance + multi-RHS solve (+ the variance correction's
-    # backward solve, exact product and second forward solve on the mixed path)
-    predict_var_ms = (factor_ms + ph["cross"] + ph["vsolve"] + ph["bsolve"] + ph["slices"] + ph["ozaki"]
-                      + ph["rsolve"])
-    grad_ms = factor_ms + ph["trtri"] + ph["lauum"] + ph["adjoint"] + ph["adam"]
+    predict_var_ms, cov_ms, grad_ms = float(np.mean(pv)), float(np.mean(cv)), float(np.mean(ng))
     ms_per_step = total_ms / K
-    predict_var_ms, grad_ms, ms_per_step = max_over_ranks([predict_var_ms, grad_ms, ms_per_step], dev)
+    predict_var_ms, cov_ms, grad_ms, ms_per_step = max_over_ranks([predict_var_ms, cov_ms, grad_ms, ms_per_step],
+                                                                  dev)
 
-    # roofline of the dominant kernel (largest share of the step in the ncu launch list)
-    upd_launch_ms = prof["update"][0] / max(prof["update"][1], 1)
-    upd_flops_per_launch = update_flops(T, b) / max(T - 1, 1)
-    if args.precision == "mixed":
-        pk = peaks() or {}
-        # kernels timed inside a seconds-long step: the sustained BF16 figure
-        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
-        peak_note = ("of measured bf16 sustained" if "bf16_tflops_sustained" in pk else
-                     "of measured bf16 burst" if "bf16_tflops" in pk else "of fallback bf16")
-        # k_ozaki_tc: 21 digit pairs (7-bit digits, 6 slices, s + u <= 7), each a BF16 product
-        # Y_s K_u of M x N x N (K x0 for every test point) with exact FP32 chunk sums
-        oz_pairs = 21
-        oz_flops = 2.0 * oz_pairs * args.m * args.n * args.n
-        oz_ms = prof["ozaki"][0] / max(prof["ozaki"][1], 1)
-        oz_achieved = oz_flops / (oz_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": "k_ozaki_tc (exact digit-pair product K x0, BF16 tcgen05, 2x2 clusters)",
-                "achieved": oz_achieved, "peak": peak, "unit": "TFLOP/s", "frac": oz_achieved / peak,
-                "peak_note": peak_note, "traffic": OZAKI_TRAFFIC_PER_LAUNCH,
-                "algorithmic_flops_per_launch": oz_flops, "avg_launch_ms": oz_ms,
-                "launches": prof["ozaki"][1] // K}
-        tensor_flops = 6.0 * upd_flops_per_launch      # six BF16 plane products per FP32-accurate product
-        upd = tensor_flops / (upd_launch_ms * 1e-3) / 1e12
-        roof["second"] = {"kernel": "k_tgemm<OpUpdate> (trailing SYRK/GEMM, split-BF16 x6, tcgen05)",
-                          "achieved": upd, "peak": peak, "unit": "TFLOP/s", "frac": upd / peak,
-                          "tensor_flops_per_launch": tensor_flops,
-                          "algorithmic_flops_per_launch": upd_flops_per_launch,
-                          "fp32_equivalent_tflops": upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12,
-                          "avg_launch_ms": upd_launch_ms, "launches": prof["update"][1] // K}
-    else:
-        peak, peak_note = fp64_peak()
-        achieved = upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": "k_update (trailing SYRK/GEMM, mma.sync f64)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_note": peak_note, "traffic": None,
-                "algorithmic_flops_per_launch": upd_flops_per_launch,
-                "avg_launch_ms": upd_launch_ms, "launches": prof["update"][1] // K}
-    peak64, _ = fp64_peak()
-    chol_flops = args.n ** 3 / 3.0
-    chol_ms = ph["potrf"] + ph["trsm"] + ph["update"]
+    # one more step with per-launch events (outside the timed region) for the phase
+    # breakdown and the dominant kernel's launch time
+    p_pv, p_cv, p_ng = profiled_step(gprat, gp, Xs)
+    roof = roofline(args, p_pv, T, b)
+    chol_ms = p_pv["potrf"][0] + p_pv["trsm"][0] + p_pv["update"][0]
+
+    def phases(p):
+        return {k: round(v[0], 3) for k, v in p.items() if v[1]}
 
     line = {"metric": METRIC, "value": predict_var_ms, "unit": "ms", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "mixed",
             "data": "synthetic mass-spring-damper (seeded), inputs resident in HBM",
             "config": workload_config(args),
-            "nlml_grad_steps_per_s": 1e3 / grad_ms, "nlml_grad_ms": grad_ms,
-            "cholesky_tflops": chol_flops / (chol_ms * 1e-3) / 1e12,
-            "cholesky_frac_of_fp64_peak": chol_flops / (chol_ms * 1e-3) / 1e12 / peak64,
-            "phases_ms": {k: round(v, 3) for k, v in ph.items()},
+            "nlml_grad_steps_per_s": 1e3 / grad_ms, "nlml_grad_ms": grad_ms, "full_cov_ms": cov_ms,
+            "timing": "predict+variance and NLML+grad are each one timed call sequence (CUDA events on the "
+                      "handle's stream around set_hyper+gp_predict and set_hyper+gp_optimize(1)); "
+                      "phases_ms comes from one extra profiled step",
+            "phases_ms": {"predict_var": phases(p_pv), "full_cov": phases(p_cv), "nlml_grad": phases(p_ng)},
             "roofline": roof, "gpu_launches": launches, "clocks": clk.summary()}
-
-    if args.precision == "mixed":
+    if args.precision == "fp64":
+        peak64 = fp64_peak()
+        line["cholesky_tflops_fp64"] = (args.n ** 3 / 3.0) / (chol_ms * 1e-3) / 1e12
+        line["cholesky_frac_of_fp64_peak"] = line["cholesky_tflops_fp64"] / peak64[0]
+        line["fp64_peak_note"] = peak64[1]
+    else:
         line["refine_iters"] = gp.info()["refine_iters"]
         line["refine_residual"] = gp.info()["refine_residual"]
+        line["accuracy_note"] = ("mixed path: alpha, mean and variances FP64-level (refinement, exact "
+                                 "variance correction); NLML, gradient and full covariance FP32-factor level "
+                                 "(see mixed_vs_fp64.rel_err); the NLML+grad figure at FP64 accuracy is "
+                                 "mixed_vs_fp64.fp64_nlml_grad_ms")
     if args.precision == "mixed" and not args.no_compare:
-        line["mixed_vs_fp64"] = compare_fp64(args, gprat, torch, dev, gp, X, y, Xs, predict_var_ms)
+        line["mixed_vs_fp64"] = compare_fp64(args, gprat, torch, dev, gp, X, y, Xs, predict_var_ms, grad_ms)
+    if args.precision == "mixed" and not args.no_d128:
+        line["d128"] = d128_block(args, gprat, torch, dev, dg)
     if rank == 0 and world == 1 and not args.no_e2e:
         line["e2e"] = e2e(args, gprat, torch, dev, Xh, yh, Xsh)
     if rank == 0 and world == 1 and not args.no_learned_init:
@@ -358,31 +388,137 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def compare_fp64(args, gprat, torch, dev, gp_mixed, X, y, Xs, mixed_ms):
-    """The FP64 path on the same inputs (one warm run, after one untimed run):
-    its predict+variance time and the mixed path's relative errors against it."""
+def roofline(args, prof, T, b):
+    """Roofline of the dominant kernel from one profiled step (per-launch CUDA
+    events on the launching stream)."""
+    upd_launch_ms = prof["update"][0] / max(prof["update"][1], 1)
+    upd_flops_per_launch = update_flops(T, b) / max(T - 1, 1)
+    if args.precision == "mixed":
+        pk = peaks() or {}
+        # kernels timed inside a seconds-long step: the sustained BF16 figure
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
+        peak_note = ("of measured bf16 sustained" if "bf16_tflops_sustained" in pk else
+                     "of measured bf16 burst" if "bf16_tflops" in pk else "of fallback bf16")
+        # k_ozaki_tc computes C = K x~0 for every test point (2 M N^2 flops of the method's own
+        # work) as OZAKI_PAIRS exact BF16 digit-pair products, each 2 M N^2 tensor flops
+        method_flops = 2.0 * args.m * args.n * args.n
+        tensor_flops = OZAKI_PAIRS * method_flops
+        oz_ms = prof["ozaki"][0] / max(prof["ozaki"][1], 1)
+        achieved = method_flops / (oz_ms * 1e-3) / 1e12
+        tensor_achieved = tensor_flops / (oz_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k_ozaki_tc (K x~0 for the exact variance correction, "
+                                             f"{OZAKI_PAIRS} BF16 digit-pair products on tcgen05)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_note": peak_note, "traffic": OZAKI_TRAFFIC_PER_LAUNCH,
+                "algorithmic_flops_per_launch": method_flops,
+                "work_note": "achieved/frac count the method's own work, 2 M N^2 (K x~0); the emulation "
+                             f"executes {OZAKI_PAIRS}x that on the BF16 tensor pipe (tensor_op_frac)",
+                "tensor_flops_per_launch": tensor_flops, "tensor_achieved": tensor_achieved,
+                "tensor_op_frac": tensor_achieved / peak,
+                "avg_launch_ms": oz_ms, "launches": prof["ozaki"][1]}
+        tensor_upd = 6.0 * upd_flops_per_launch      # six BF16 plane products per FP32-accurate product
+        roof["second"] = {"kernel": "k_tgemm<OpUpdate> (trailing SYRK/GEMM, split-BF16 x6, tcgen05)",
+                          "achieved": upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12, "peak": peak,
+                          "unit": "TFLOP/s",
+                          "frac": upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12 / peak,
+                          "tensor_op_frac": tensor_upd / (upd_launch_ms * 1e-3) / 1e12 / peak,
+                          "algorithmic_flops_per_launch": upd_flops_per_launch,
+                          "avg_launch_ms": upd_launch_ms, "launches": prof["update"][1]}
+        return roof
+    peak, peak_note = fp64_peak()
+    achieved = upd_flops_per_launch / (upd_launch_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "k_update (trailing SYRK/GEMM, mma.sync f64)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_note": peak_note, "traffic": None,
+            "algorithmic_flops_per_launch": upd_flops_per_launch,
+            "avg_launch_ms": upd_launch_ms, "launches": prof["update"][1]}
+
+
+def compare_fp64(args, gprat, torch, dev, gp_mixed, X, y, Xs, mixed_ms, mixed_grad_ms):
+    """The FP64 path on the same inputs: its predict+variance and NLML+grad step
+    times (each one timed call sequence, as the mixed path's) and the mixed
+    path's relative errors against it, output by output."""
     def rel(a, b):
         return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
 
+    def worst(a, b, floor):
+        return float(torch.max(torch.abs(a - b) / torch.clamp(torch.abs(b), min=floor)))
+
     gp_mixed.set_hyper(HYP0)
     mu_m, va_m, _ = gp_mixed.predict(Xs, mean=True, var=True)
-    f_m = gp_mixed.nlml()
+    f_m, g_m = gp_mixed.nlml_grad()
     stream = torch.cuda.current_stream(dev)
     with gprat.GP(X, y, HYP0, n_tiles=args.fp64_tiles) as g64:
-        g64.predict(Xs, mean=True, var=True)
+        pv, _, ng = timed_step_no_cov(gprat, g64, Xs, stream, torch)
         g64.set_hyper(HYP0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
         mu_d, va_d, _ = g64.predict(Xs, mean=True, var=True)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        f_d = g64.nlml()
-    fp64_ms = e0.elapsed_time(e1)
-    return {"fp64_predict_var_ms": fp64_ms, "speedup": fp64_ms / mixed_ms,
-            "rel_err": {"mean": rel(mu_m, mu_d), "var": rel(va_m, va_d), "nlml": abs(f_m - f_d) / abs(f_d)},
-            "note": "norm-wise relative error of the mixed outputs against the FP64 GPU path, same inputs"}
+        f_d, g_d = g64.nlml_grad()
+    return {"fp64_predict_var_ms": pv, "fp64_nlml_grad_ms": ng, "fp64_nlml_grad_steps_per_s": 1e3 / ng,
+            "speedup_predict_var": pv / mixed_ms, "speedup_nlml_grad": ng / mixed_grad_ms,
+            "rel_err": {"mean": rel(mu_m, mu_d), "var": rel(va_m, va_d),
+                        "mean_worst": worst(mu_m, mu_d, 1e-3 * float(torch.abs(mu_d).max())),
+                        "var_worst": worst(va_m, va_d, 1e-12),
+                        "nlml": abs(f_m - f_d) / abs(f_d),
+                        "grad": float(np.linalg.norm(g_m - g_d) / np.linalg.norm(g_d)),
+                        "grad_worst": float(np.max(np.abs(g_m - g_d) / np.abs(g_d)))},
+            "note": "relative errors of the mixed outputs against the FP64 GPU path on the same inputs "
+                    "(norm-wise, and worst element); the FP64 times are one cold call each"}
+
+
+def timed_step_no_cov(gprat, gp, Xs, stream, torch):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    gp.set_hyper(HYP0)
+    ev[0].record(stream)
+    gp.predict(Xs, mean=True, var=True)
+    ev[1].record(stream)
+    gp.set_hyper(HYP0)
+    ev[2].record(stream)
+    st = gprat._lib.gp_optimize(gp.h, 1, 0.1, None)
+    ev[3].record(stream)
+    if st != gprat.GP_OK:
+        raise gprat.GPError(st, -1, "gp_optimize")
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]), None, ev[2].elapsed_time(ev[3])
+
+
+def d128_block(args, gprat, torch, dev, dg):
+    """The same workload with 128 lagged-input regressors (l = sqrt(128), the
+    non-degenerate length scale at that width): mixed predict+variance and
+    NLML+grad, 2 warm-up and 3 timed steps."""
+    d = 128
+    Xh, yh, Xsh, _ = dg.msd_dataset(args.n, args.m, d, 1002)
+    X = torch.from_numpy(Xh).to(dev)
+    y = torch.from_numpy(yh).to(dev)
+    Xs = torch.from_numpy(Xsh).to(dev)
+    hyp = (d ** 0.5, 1.0, 0.1)
+    stream = torch.cuda.current_stream(dev)
+    with gprat.GP(X, y, hyp, n_tiles=args.tiles, precision=args.precision) as gp:
+        pv, ng = [], []
+        for i in range(5):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            gp.set_hyper(hyp)
+            ev[0].record(stream)
+            gp.predict(Xs, mean=True, var=True)
+            ev[1].record(stream)
+            gp.set_hyper(hyp)
+            ev[2].record(stream)
+            st = gprat._lib.gp_optimize(gp.h, 1, 0.1, None)
+            ev[3].record(stream)
+            if st != gprat.GP_OK:
+                raise gprat.GPError(st, -1, "gp_optimize")
+            torch.cuda.synchronize()
+            if i >= 2:
+                pv.append(ev[0].elapsed_time(ev[1]))
+                ng.append(ev[2].elapsed_time(ev[3]))
+        gp.profile(True)
+        gp.profile_read()
+        gp.set_hyper(hyp)
+        gp.predict(Xs, mean=True, var=True)
+        prof = gp.profile_read()
+        gp.profile(False)
+    return {"regressors": d, "lengthscale": hyp[0], "predict_var_ms": float(np.mean(pv)),
+            "nlml_grad_ms": float(np.mean(ng)), "nlml_grad_steps_per_s": 1e3 / float(np.mean(ng)),
+            "predict_phases_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
 
 
 def learned_init_block(args, gprat, torch, dev, X, y):

@@ -179,9 +179,9 @@ typedef enum {
     GP_PH_ADAM,
     GP_PH_REFINE,       /* mixed path: FP64 residuals and corrections of alpha */
     GP_PH_BSOLVE,       /* mixed variance correction: x0^T = W L~^{-1} (backward multi-RHS solve) */
-    GP_PH_OZAKI,        /* mixed variance correction: the exact digit-pair product K x0 */
+    GP_PH_OZAKI,        /* mixed variance correction: the exact digit-pair product K x~0 */
     GP_PH_RSOLVE,       /* mixed variance correction: L~^{-1} r0 (forward multi-RHS solve) */
-    GP_PH_SLICES,       /* mixed variance correction: digit slices of x0 and K */
+    GP_PH_SLICES,       /* mixed variance correction: x0 rounded to x~0, digit slices of x~0 and K */
     GP_PH_OTHER,
     GP_NPHASE
 } gp_phase;
@@ -264,7 +264,8 @@ gp_status gp_info(gp_t h, gp_info_t* out);
  *   row-major float64; lengthscale l and vertical nu as in Eq. 2; cuda_stream
  *   as in gp_options (NULL: legacy default stream).  Stream-ordered, no sync.
  * Limits: 1 <= m <= GP_NOALLOC_MAX_TEST, 1 <= d <= 1024; larger or invalid
- * arguments, or host pointers, return GP_ERR_ARG before any work.
+ * arguments, host pointers (pinned ones included) and device memory of a GPU
+ * other than the current one return GP_ERR_ARG before any work.
  * Scratch: a fixed GP_NOALLOC_CHUNKS x GP_NOALLOC_MAX_TEST array of doubles
  * (16 MiB) in the library's device data, held by every GPU that loads the
  * library until the process exits and shared by all calls on that GPU.  The
@@ -277,6 +278,14 @@ gp_status gp_info(gp_t h, gp_info_t* out);
 gp_status gp_predict_mean_noalloc(const double* X, const double* alpha, int64_t n, int64_t d,
                                   const double* Xs, int64_t m, double lengthscale, double vertical,
                                   double* mean, void* cuda_stream);
+
+/* Measurement aid (no counterpart in the paper): the FP64 arithmetic peaks of
+ * the current GPU in TFLOP/s, from register-only throughput loops of
+ * mma.sync.m8n8k4.f64 (the FP64 tensor path the FP64 tile products use) and
+ * of DFMA, timed with CUDA events on cuda_stream (the third of three
+ * repetitions).  They are the denominators of the FP64 path's roofline
+ * fractions.  Allocates and frees two small device buffers; synchronises. */
+gp_status gp_measure_fp64_peaks(double* dmma_tflops, double* dfma_tflops, void* cuda_stream);
 
 int64_t gp_last_error_info(gp_t h);
 const char* gp_status_str(gp_status s);

@@ -126,7 +126,7 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     dev_free(h, &h->outv, old);
     dev_free(h, &h->R64, old * h->Np);
     dev_free(h, &h->Rr32, old * h->Np);
-    dev_free(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * old * h->Np);
+    dev_free(h, &h->YS, (int64_t)gpk::GP_OZ_YSLICES * old * h->Np);
     dev_free(h, &h->mu, old);
     dev_free(h, &h->qpart, 2 * old * (h->Np / 64));
     dev_free(h, &h->vpart2, old * (h->Np / 64));
@@ -137,7 +137,7 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     if (h->opt.var_correction) {
         if ((s = dev_alloc(h, &h->R64, ldm * h->Np)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->Rr32, ldm * h->Np)) != GP_OK) return s;
-        if ((s = dev_alloc(h, &h->YS, (int64_t)gpk::GP_OZ_SLICES * ldm * h->Np)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->YS, (int64_t)gpk::GP_OZ_YSLICES * ldm * h->Np)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->mu, ldm)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->qpart, 2 * ldm * (h->Np / 64))) != GP_OK) return s;   // one slot per 64 columns
         if ((s = dev_alloc(h, &h->vpart2, ldm * (h->Np / 64))) != GP_OK) return s;   // one slot per 64 columns
@@ -533,12 +533,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     cudaGetDevice(&h->device);
     h->n = n;
     h->d = d;
-    h->oz_lmax = 7;
     h->dag_stall = -1;
-    if (const char* e = getenv("GPRAT_OZAKI_LMAX")) {   // accuracy/speed study knob: 5, 6 or 7
-        int v = atoi(e);
-        if (v >= 4 && v <= 2 * gpk::GP_OZ_SLICES) h->oz_lmax = v;
-    }
     int64_t per = (n + opt.n_tiles - 1) / opt.n_tiles;
     h->b = round_up(per, opt.prec == GP_MIXED ? 2 * TB : TB);
     h->T = (n + h->b - 1) / h->b;

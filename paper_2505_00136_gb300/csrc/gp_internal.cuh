@@ -87,14 +87,13 @@ struct gp_handle {
     // variance correction (GP_MIXED)
     double* R64;              // m_cap x Np: FP64 K_{Z*,Z}
     float* Rr32;              // m_cap x Np: r0 = K_{Z*,Z} - x0^T K
-    __nv_bfloat16* YS;        // digit slices of x0^T, OZ_S x m_cap x Np
+    __nv_bfloat16* YS;        // digit slices of x~0^T, GP_OZ_YSLICES x m_cap x Np
     __nv_bfloat16* KS;        // digit slices of K, OZ_S x Np x Np (allocated on first use)
     double* mu;               // m_cap row scales of x0^T
     double* kappa;            // scale of K
     double* qpart;            // 2 x (Np/64) x m_cap partial sums (one per 64 columns)
     double* vpart2;           // (Np/64) x m_cap partial sums of ||L~^{-1} r0||^2
     bool ks_valid;            // KS matches the current K
-    int oz_lmax;              // digit pairs (s, u) with s + u <= oz_lmax enter the exact product
     bool tc_pending;          // a tensor-core kernel ran since its timeout word was last read
     int* solve_flags;         // grid barrier of the persistent FP32 solve: arrival count, generation
     __nv_bfloat16* ZP;        // T(T+1)/2 tiles x 3 planes of (L^{-1})^T tiles (gradient)
@@ -185,8 +184,10 @@ bool tg_trtri_acc(gp_t h, int t0, int t1, int i0, int ni, int nj);   // U_ij (+)
 bool tg_lauum(gp_t h);
 bool tg_bdiag(gp_t h, int64_t ldm, int64_t i);                  // Y_i = S_i Linv_ii (NN form)
 bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj);   // S_j -= sum Y_i L_ij (NN form)
-constexpr int GP_OZ_SLICES = 6;                                // digit slices per operand (kernels_mixed.cu)
+constexpr int GP_OZ_SLICES = 6;                                // digit slices of K (kernels_mixed.cu)
+constexpr int GP_OZ_YSLICES = 2;                               // digit slices of x~0: x0 rounded to 14 bits per row
 constexpr int GP_OZ_BITS = 7;                                   // bits per signed digit: |d| <= 2^7, exact in BF16
+constexpr int GP_OZ_LMAX = 7;                                   // digit pairs (s, u) with s + u <= 7 enter K x~0
 }  // namespace gpk
 
 #define GP_CUDA_OK(call)                                                   \

@@ -16,10 +16,10 @@
 //    y - K alpha in FP64 against the FP64 K (k_sym_resid).
 //  - Prediction: the mean is K_{Z*,Z} alpha in FP64 (fused into the cross-
 //    covariance assembly).  Variances: W = K_{Z*,Z} L^{-T} from bf16x6
-//    products gives x0 = L^{-T} W^T; with r0 = k* - K x0 from the exact digit
-//    product (kernels_tc.cu) the quadratic form is k*^T x0 + x0^T r0 +
-//    ||L^{-1} r0||^2, FP64-accurate up to a third-order term; without the
-//    correction var = k** - rowsum(W^2).
+//    products gives x0 = L^{-T} W^T, rounded to x~0 (14 bits per test point);
+//    with r0 = k* - K x~0 from the exact digit product (kernels_tc.cu) the
+//    quadratic form is k*^T x~0 + x~0^T r0 + ||L^{-1} r0||^2, FP64-accurate up
+//    to a third-order term; without the correction var = k** - rowsum(W^2).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -793,19 +793,19 @@ __global__ void k_split_row(const float* U32, __nv_bfloat16* PA, int64_t b, int6
 }
 
 // ---------------------------------------------------------------- variance correction
-// With x0 = (L~ L~^T)^{-1} k* from the mixed factor and r0 = k* - K x0,
-//   k*^T K^{-1} k* = k*^T x0 + x0^T r0 + r0^T K^{-1} r0,
-// and the last term is taken with the mixed factor, ||L~^{-1} r0||^2 (its
-// error is third order in the factor's error).  Only K x0 must be accurate to
-// FP64 level; it is formed from exactly-accumulated BF16 digit slices (Ozaki
-// et al. 2012): each row of Y = x0^T and all of K are scaled by a power of two
-// and split into 7-bit signed integer digits (|d| <= 128, exact in BF16),
-// every digit product is exact (|d e| <= 2^14), sums of at most 1024 of them
-// are exact in FP32 (<= 2^24), and the partial sums are carried in
+// With any x0 and r0 = k* - K x0,
+//   k*^T K^{-1} k* = k*^T x0 + x0^T r0 + r0^T K^{-1} r0
+// holds exactly.  x0 is the mixed-factor solution (L~ L~^T)^{-1} k* rounded to
+// 14 bits per test point (x~0, k_yslices), and the last term is taken with the
+// mixed factor, ||L~^{-1} r0||^2 (its error is third order).  Only K x~0 must
+// be accurate to FP64 level; it is formed from exactly-accumulated BF16 digit
+// slices (Ozaki et al. 2012): each row of x~0^T and all of K are scaled by a
+// power of two and split into 7-bit signed integer digits (|d| <= 128, exact
+// in BF16), every digit product is exact (|d e| <= 2^14), sums of at most 1024
+// of them are exact in FP32 (<= 2^24), and the partial sums are carried in
 // double-FP32.
 
-
-constexpr int OZ_S = GP_OZ_SLICES;   // digit slices per operand
+constexpr int OZ_S = GP_OZ_SLICES;   // digit slices of K
 constexpr int OZ_B = GP_OZ_BITS;     // bits per digit
 
 __device__ __forceinline__ double pow2_ceil(double x)   // smallest power of two >= x (x > 0)
@@ -856,29 +856,39 @@ __device__ __forceinline__ long long rint_scaled(float v, int sc)
     return rint_scaled_bits(m, (ex ? ex : 1) - 150, (u >> 31) != 0, sc);
 }
 
-// Balanced base-2^OZ_B digits of a in [-1, 1] given q = rint(a 2^(OZ_B OZ_S))
+// Balanced base-2^OZ_B digits of a in [-1, 1] given q = rint(a 2^(OZ_B S))
 // (exact in a 64-bit integer): d_s = q rounded to a multiple of
-// 2^(OZ_B (OZ_S - s)) and removed from q, most significant first, so that
+// 2^(OZ_B (S - s)) and removed from q, most significant first, so that
 // a ~ sum_s d_s 2^{-OZ_B s} with |d_1| <= 2^OZ_B, |d_s| <= 2^(OZ_B - 1) for
-// s > 1, the error at most 2^{-OZ_B OZ_S - 1}.
-__device__ __forceinline__ void oz_digits(long long q, __nv_bfloat16 (&d)[OZ_S])
+// s > 1, the error at most 2^{-OZ_B S - 1}; the digits of q itself are exact.
+template <int S>
+__device__ __forceinline__ void oz_digits(long long q, __nv_bfloat16 (&d)[S])
 {
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-        const int sh = OZ_B * (OZ_S - 1 - s);
+    for (int s = 0; s < S; ++s) {
+        const int sh = OZ_B * (S - 1 - s);
         const long long dg = sh > 0 ? ((q + (1ll << (sh - 1))) >> sh) : q;
         q -= dg * (1ll << sh);
         d[s] = __int2bfloat16_rn((int)dg);
     }
 }
 
-// Digits of each row of Y (R32, ldm x Np): mu[row] = power of two >= max |Y|,
-// YS[s][row][col] = s-th digit of Y / mu.  One CTA per row.
-__global__ void k_yslices(const float* Y, int64_t Np, __nv_bfloat16* YS, int64_t ps, double* mu)
+constexpr int OZ_YS = GP_OZ_YSLICES;   // digit slices of x~0
+
+// Rounds each row of Y (R32, ldm x Np) to OZ_YS digits and splits it:
+// mu[row] = power of two >= max |Y|, q = rint(Y 2^(OZ_B OZ_YS) / mu)
+// (|q| <= 2^(OZ_B OZ_YS)), YS[s][row][col] = s-th digit of q, and Y is
+// overwritten by x~0 = q mu 2^{-OZ_B OZ_YS}, exact in FP32.  The variance
+// correction then uses this x~0 in every term, which makes it exact for x~0
+// whatever the rounding (the identity behind it holds for any x0); only
+// r0 = k* - K x~0 grows, to about 2^{-14} of k*, and its quadratic term
+// stays far below the FP64 target.  A row whose rounded values would fall
+// below the FP32 grid (max |Y| < 2^-135) is taken as zero.  One CTA per row.
+__global__ void k_yslices(float* Y, int64_t Np, __nv_bfloat16* YS, int64_t ps, double* mu)
 {
     __shared__ float red[NTH];
     const int64_t row = blockIdx.x;
-    const float* y = Y + row * Np;
+    float* y = Y + row * Np;
     float mx = 0.f;
     for (int64_t c = threadIdx.x; c < Np; c += NTH) mx = fmaxf(mx, fabsf(y[c]));
     red[threadIdx.x] = mx;
@@ -889,12 +899,16 @@ __global__ void k_yslices(const float* Y, int64_t Np, __nv_bfloat16* YS, int64_t
     }
     const double m = red[0] > 0.f ? pow2_ceil((double)red[0]) : 1.0;
     if (threadIdx.x == 0) mu[row] = m;
-    const int sc = OZ_B * OZ_S - pow2_exp(m);   // y / m 2^(OZ_B OZ_S) = y 2^sc
+    const int ex = pow2_exp(m);
+    const int sc = OZ_B * OZ_YS - ex;   // y / m 2^(OZ_B OZ_YS) = y 2^sc
+    const bool tiny = ex - OZ_B * OZ_YS < -149;
     for (int64_t c = threadIdx.x; c < Np; c += NTH) {
-        __nv_bfloat16 d[OZ_S];
-        oz_digits(rint_scaled(y[c], sc), d);
+        const long long q = tiny ? 0ll : rint_scaled(y[c], sc);
+        __nv_bfloat16 d[OZ_YS];
+        oz_digits<OZ_YS>(q, d);
 #pragma unroll
-        for (int s = 0; s < OZ_S; ++s) YS[s * ps + row * Np + c] = d[s];
+        for (int s = 0; s < OZ_YS; ++s) YS[s * ps + row * Np + c] = d[s];
+        y[c] = ldexpf((float)q, -sc);
     }
 }
 
@@ -926,7 +940,7 @@ __global__ void k_kslices(const double* K64, int64_t b, int64_t Np, const GpHype
         else if (R0 < C0) v = tile[c][r];
         else v = (c <= r) ? tile[r][c] : tile[c][r];
         __nv_bfloat16 d[OZ_S];
-        oz_digits(rint_scaled(v, sc), d);
+        oz_digits<OZ_S>(rint_scaled(v, sc), d);
         const int64_t o = (R0 + r) * Np + C0 + c;
 #pragma unroll
         for (int s = 0; s < OZ_S; ++s) KS[s * ps + o] = d[s];
@@ -1130,7 +1144,7 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
         }
         if (lo > 0 && !tg_bupd(h, ldm, lo, I - lo + 1, 0, lo)) return false;
     }
-    GPK_LAUNCH(h, GP_PH_SLICES, k_yslices, (unsigned)ldm, NTH, 0, (const float*)h->R32, Np, h->YS, ldm * Np, h->mu);
+    GPK_LAUNCH(h, GP_PH_SLICES, k_yslices, (unsigned)ldm, NTH, 0, h->R32, Np, h->YS, ldm * Np, h->mu);
     if (!h->ks_valid) {
         GPK_LAUNCH(h, GP_PH_SLICES, k_kslices, dim3((unsigned)(Np / 64), (unsigned)(Np / 64)), NTH, 0, (const double*)h->L, b, Np,
                    (const GpHyperDev*)h->hyp, h->KS, Np * Np, h->kappa);

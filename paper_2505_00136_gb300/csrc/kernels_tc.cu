@@ -1,34 +1,34 @@
 // tcgen05 kernels of the mixed-precision path (5th-generation tensor cores,
 // accumulators in tensor memory, operands staged by TMA).
 //
-// k_ozaki_tc: C = Y K for the third-order variance correction, Y (test rows x
-// Np) and K (Np x Np, symmetric) each given as BF16 slices of signed
-// GP_OZ_BITS-bit digits (|d| <= 2^GP_OZ_BITS), C = sum over kept digit pairs
-// (s, u) of 2^{-GP_OZ_BITS (s+u)} Y_s K_u.  Each pair's product is summed
-// exactly in FP32 over chunks of 2^(24 - 2 GP_OZ_BITS) k (1024 for 7-bit
-// digits: a product is at most 2^(2 GP_OZ_BITS), so a chunk sum stays within
-// 2^24), and each chunk sum is added into a double-FP32
-// (hi + lo) running sum, which carries about 48 bits.  The fused epilogue
-// forms r0 = Kc - C and the partial row sums of Kc Y and Y r0 (the terms
-// k*^T x0 and x0^T r0 of the corrected variance).
+// k_ozaki_tc: C = Y K for the third-order variance correction.  Y (test rows
+// x Np) holds x~0^T, the mixed-factor solution rounded, row by row, to
+// GP_OZ_YSLICES signed GP_OZ_BITS-bit digits (k_yslices writes that rounded
+// value back, so the correction uses the same x~0 everywhere and is exact
+// for it); K (Np x Np, symmetric) is split into GP_OZ_SLICES digits.  Both are
+// given as BF16 slices of integer digits (|d| <= 2^GP_OZ_BITS, exact in
+// BF16), C = sum over digit pairs (s, u) with s + u <= GP_OZ_LMAX of
+// 2^{-GP_OZ_BITS (s+u)} Y_s K_u.  Pairs of equal level l = s + u share one
+// FP32 accumulator: at most two pairs per level, each product at most
+// 2^(2 GP_OZ_BITS), so an exact chunk of OZT_CHUNK k (2 x 512 x 2^14 = 2^24)
+// stays exact in FP32, and each chunk sum is added into a double-FP32
+// (hi + lo) running sum, about 48 bits, held in registers.  The fused
+// epilogue forms r0 = Kc - C and the partial row sums of Kc x~0 and x~0 r0
+// (the terms k*^T x~0 and x~0^T r0 of the corrected variance).
 //
-// Clusters of 2 x 2 CTAs (two row blocks x two column blocks): the two CTAs
-// of a row block share its Y tile and the two of a column block its K tile,
-// so each CTA loads half of each (64 rows) and multicasts it to the CTA that
-// shares it, halving the operand traffic from L2.  A stage of a CTA's ring is
-// written by three CTAs (itself, its Y partner, its K partner) and released
-// to all three by a multicast MMA commit; before leaving, a CTA waits for its
-// partners' last releases and the cluster synchronises, so no cross-CTA
-// arrival or copy can land in a CTA that has exited.
+// Operand reuse without any cross-CTA traffic: the six levels 2..7 run in
+// three groups of two levels; a 32-k stage of a group holds the two Y slices
+// and the two or three K slices its pairs need (five 8 KB slots), and all of
+// the group's three or four pair products are issued from that one stage, so
+// a 128 x 128 x 16 product needs about 5 KB of operands from L2 instead of 8.
 //
-// Roles (320 threads, one CTA per SM): warp 0 issues TMA loads into a
-// 3-stage ring of 128-k stages {Y tile, K tile} (64 KB per stage, eight
-// MMAs per stage and one release commit); warp 1 owns the 512
-// TMEM columns and issues the MMAs; warps 2-9 (two per TMEM lane quarter,
-// one output row and 64 columns per thread) flush chunk sums and run the
-// epilogue.  TMEM columns: two 128-column accumulators used alternately per
-// chunk (the MMAs of chunk c+1 run while chunk c is flushed), hi at 256, lo
-// at 384.
+// Roles (320 threads, one CTA per 128 x 128 output tile): warp 0 issues TMA
+// loads into a 5-stage ring; warp 1 owns the 512 TMEM columns (two pairs of
+// 128-column level accumulators, used alternately by successive group
+// chunks) and issues the MMAs; warps 2-9 (two per TMEM lane quarter, one
+// output row and 64 columns per thread) flush each group chunk's two level
+// sums into their registers' running sums while the next chunk's MMAs run,
+// then run the epilogue.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -44,28 +44,29 @@ __device__ int g_tc_error;
 
 namespace {
 
-constexpr int OZT_STAGES = 3;
-constexpr int OZT_KS = 128;                                      // k per stage
-constexpr int OZT_KCH = (1 << (24 - 2 * GP_OZ_BITS)) / OZT_KS;   // stages per exact chunk
+static_assert(GP_OZ_YSLICES == 2 && GP_OZ_SLICES == 6 && GP_OZ_LMAX == 7 && GP_OZ_BITS == 7,
+              "the level groups below are laid out for 2 x 6 slices of 7-bit digits and levels 2..7");
+
+constexpr int OZT_STAGES = 5;
+constexpr int OZT_KS = 32;                                 // k per stage
+constexpr int OZT_SLOT = 128 * OZT_KS * 2;                 // one 128 x 32 BF16 tile, 64-byte swizzle
+constexpr int OZT_STAGE_BYTES = 5 * OZT_SLOT;              // Y_1, Y_2 and up to three K slices
+constexpr int OZT_CHUNK = 512;                             // k per exact chunk
+constexpr int OZT_STAGES_PER_CHUNK = OZT_CHUNK / OZT_KS;
+constexpr int OZT_GROUPS = 3;                              // levels (2, 3), (4, 5), (6, 7)
 constexpr int OZT_THREADS = 320;
 constexpr int OZT_EPI_WARPS = 8;
-constexpr int OZT_STAGE_BYTES = 4 * tc::TILE_BYTES;            // Y (two 64-k tiles), K (two 64-k tiles)
 constexpr int OZT_BAR_OFF = OZT_STAGES * OZT_STAGE_BYTES;
 constexpr int OZT_SMEM = 1024 + OZT_BAR_OFF + 256;
+constexpr int OZT_RASTER = 16;                             // row blocks that share a K column block in flight
 constexpr uint32_t OZT_IDESC = tc::idesc_bf16(128, 128);
+static_assert((2 * OZT_CHUNK) << (2 * GP_OZ_BITS) <= (1 << 24), "a level's chunk sum must stay exact in FP32");
+static_assert(OZT_SMEM <= 227 * 1024, "shared memory");
 
-// p-th kept digit pair (s, u), 1-based, s-major, s + u <= lmax, s, u <= GP_OZ_SLICES.
-__device__ __forceinline__ void oz_pair_tc(int p, int lmax, int& s, int& u)
-{
-    s = 1;
-    while (true) {
-        const int cnt = max(0, min(GP_OZ_SLICES, lmax - s));
-        if (p < cnt) break;
-        p -= cnt;
-        ++s;
-    }
-    u = p + 1;
-}
+// Lowest K slice (1-based) and number of K slices of group g (levels 2g + 2, 2g + 3):
+// group 0 pairs (1,1) | (1,2) (2,1); group 1 (1,3) (2,2) | (1,4) (2,3); group 2 (1,5) (2,4) | (1,6) (2,5).
+__host__ __device__ constexpr int grp_u0(int g) { return g == 0 ? 1 : 2 * g; }
+__host__ __device__ constexpr int grp_nk(int g) { return g == 0 ? 2 : 3; }
 
 __device__ __forceinline__ bool drain_wait(uint32_t mbar, uint32_t parity)
 {
@@ -75,15 +76,32 @@ __device__ __forceinline__ bool drain_wait(uint32_t mbar, uint32_t parity)
     return true;
 }
 
+__device__ __forceinline__ void mma_first(uint32_t d, uint64_t da, uint64_t db, bool& first)
+{
+    if (first) tc::mma_bf16(d, da, db, OZT_IDESC, 0u);
+    else tc::mma_bf16_acc(d, da, db, OZT_IDESC);
+    first = false;
+}
+
+// TwoSum (Knuth): hi + lo += x with the rounding error of hi + x kept in lo.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bv = s - hi;
+    const float er = (hi - (s - bv)) + (x - bv);
+    hi = s;
+    lo += er;
+}
+
 __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
     const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapK, int64_t ldm, int64_t Np,
     const double* mu, const double* kappa_p, const double* R64, const float* Y, float* Rr32, double* qpart,
-    int64_t m, int64_t n_valid, int lmax, int* err)
+    int64_t m, int64_t n_valid, int* err)
 {
     extern __shared__ unsigned char dyn[];
     unsigned char* base = dyn + ((1024 - (tc::su32(dyn) & 1023)) & 1023);
     const uint32_t sbase = tc::su32(base);
-    const uint32_t bar = sbase + OZT_BAR_OFF;   // full[6], empty[6], accf[2], acce[2], drain
+    const uint32_t bar = sbase + OZT_BAR_OFF;   // full[S], empty[S], accf[2], acce[2], drain
     auto full = [&](int s) { return bar + 8 * s; };
     auto empty = [&](int s) { return bar + 8 * (OZT_STAGES + s); };
     auto accf = [&](int a) { return bar + 8 * (2 * OZT_STAGES + a); };
@@ -93,27 +111,19 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
     volatile int* abort = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // cluster rank = 2 cm + cn: row block pair member cm, column block pair member cn
-    const uint32_t rank = tc::cluster_rank();
-    const int cm = (int)(rank >> 1), cn = (int)(rank & 1);
-    const uint16_t mask_y = (uint16_t)(3u << (2 * cm)), mask_k = (uint16_t)((1u << cn) | (1u << (cn + 2)));
-    const uint16_t mask_rel = (uint16_t)((1u << rank) | (1u << (rank ^ 1)) | (1u << (rank ^ 2)));
-    // grouped raster over 2 x 2 block clusters: 4 cluster rows share each cluster column in flight
+    // grouped raster: OZT_RASTER consecutive CTAs take consecutive row blocks of one column block,
+    // so the CTAs in flight share each K column block and each Y row block through L2
     const int64_t nbn = Np / 128, nbm = ldm / 128;
-    const int64_t nbn2 = (nbn + 1) / 2, nbm2 = (nbm + 1) / 2;
-    const int64_t g = blockIdx.x >> 2, G = 4;
-    const int64_t grp = g / (G * nbn2), first = grp * G;
-    const int64_t gsz = (nbm2 - first) < G ? (nbm2 - first) : G;
-    const int64_t mc = first + (g % (G * nbn2)) % gsz, nc = (g % (G * nbn2)) / gsz;
-    // odd block counts: the missing block of a pair repeats the last one and stores nothing
-    const bool valid = 2 * mc + cm < nbm && 2 * nc + cn < nbn;
-    const int64_t mb = min(2 * mc + cm, nbm - 1), nb = min(2 * nc + cn, nbn - 1);
-    const int64_t m0 = mb * 128, n0 = nb * 128;
+    const int64_t t = blockIdx.x;
+    const int64_t first_rb = (t / (OZT_RASTER * nbn)) * OZT_RASTER;
+    const int64_t gsz = (nbm - first_rb) < OZT_RASTER ? (nbm - first_rb) : OZT_RASTER;
+    const int64_t r_in = t % (OZT_RASTER * nbn);
+    const int64_t m0 = (first_rb + r_in % gsz) * 128, n0 = (r_in / gsz) * 128;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OZT_STAGES; ++s) {
             tc::mbar_init(full(s), 1);
-            tc::mbar_init(empty(s), 3);
+            tc::mbar_init(empty(s), 1);
         }
         tc::mbar_init(accf(0), 1);
         tc::mbar_init(accf(1), 1);
@@ -125,86 +135,85 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
     }
     if (warp == 1) tc::tmem_alloc(tc::su32(tmem_slot), 512);
     tc::fence_before();
-    tc::cluster_sync();   // every barrier of the cluster initialised before any copy or commit
+    __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    int np = 0;
-    for (int s = 1; s <= GP_OZ_SLICES; ++s) np += max(0, min(GP_OZ_SLICES, lmax - s));
     const int kst = (int)(Np / OZT_KS);
-    const int nkc = (kst + OZT_KCH - 1) / OZT_KCH;   // exact chunks along k; all pairs of a chunk run together
+    const int nwin = (kst + OZT_STAGES_PER_CHUNK - 1) / OZT_STAGES_PER_CHUNK;   // exact chunks along k
 
     if (warp == 0) {
         if (lane == 0) {
             int gs = 0;
             bool ok = true;
             const uint64_t pol = tc::policy_evict_last();
-            for (int kc = 0; kc < nkc && ok; ++kc)
-            for (int p = 0; p < np && ok; ++p) {
-                int s, u;
-                oz_pair_tc(p, lmax, s, u);
-                const int ya = (int)((s - 1) * ldm + m0), kb = (int)((u - 1) * Np + n0);
-                for (int k = kc * OZT_KCH; k < min(kst, (kc + 1) * OZT_KCH); ++k, ++gs) {
-                    const int st = gs % OZT_STAGES, use = gs / OZT_STAGES;
-                    if (use > 0 && !tc::mbar_wait(empty(st), (uint32_t)((use - 1) & 1), abort, err)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t dst = sbase + st * OZT_STAGE_BYTES;
-                    tc::mbar_expect_tx(full(st), OZT_STAGE_BYTES);   // eight 8 KB halves from three CTAs
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int kx = k * OZT_KS + 64 * j;
-                        tc::tma_load_2d_mc_hint(dst + j * tc::TILE_BYTES + cn * (tc::TILE_BYTES / 2), &mapY, kx,
-                                                ya + 64 * cn, full(st), mask_y, pol);
-                        tc::tma_load_2d_mc_hint(dst + (2 + j) * tc::TILE_BYTES + cm * (tc::TILE_BYTES / 2), &mapK, kx,
-                                                kb + 64 * cm, full(st), mask_k, pol);
+            for (int w = 0; w < nwin && ok; ++w) {
+                const int k_lo = w * OZT_STAGES_PER_CHUNK;
+                const int k_hi = min(kst, k_lo + OZT_STAGES_PER_CHUNK);
+                for (int g = 0; g < OZT_GROUPS && ok; ++g) {
+                    const int u0 = grp_u0(g), nk = grp_nk(g);
+                    for (int k = k_lo; k < k_hi; ++k, ++gs) {
+                        const int st = gs % OZT_STAGES, use = gs / OZT_STAGES;
+                        if (use > 0 && !tc::mbar_wait(empty(st), (uint32_t)((use - 1) & 1), abort, err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t dst = sbase + st * OZT_STAGE_BYTES;
+                        const int kx = k * OZT_KS;
+                        tc::mbar_expect_tx(full(st), (uint32_t)((2 + nk) * OZT_SLOT));
+                        tc::tma_load_2d_hint(dst, &mapY, kx, (int)m0, full(st), pol);
+                        tc::tma_load_2d_hint(dst + OZT_SLOT, &mapY, kx, (int)(ldm + m0), full(st), pol);
+                        for (int j = 0; j < nk; ++j)
+                            tc::tma_load_2d_hint(dst + (2 + j) * OZT_SLOT, &mapK, kx,
+                                                 (int)((u0 - 1 + j) * Np + n0), full(st), pol);
                     }
                 }
             }
-            if (!ok) {   // let the copies in flight land before the CTA exits
+            if (!ok)   // let the copies in flight land before the CTA exits
                 for (int q = gs - 1; q >= 0 && q >= gs - OZT_STAGES; --q)
                     drain_wait(full(q % OZT_STAGES), (uint32_t)((q / OZT_STAGES) & 1));
-            }
-            // the partners' releases of each stage's last use have landed here
-            for (int q = gs - 1; q >= 0 && q >= gs - OZT_STAGES; --q)
-                drain_wait(empty(q % OZT_STAGES), (uint32_t)((q / OZT_STAGES) & 1));
         }
     } else if (warp == 1) {
         if (lane == 0) {
             int gs = 0, c = 0;
             bool ok = true;
-            for (int kc = 0; kc < nkc && ok; ++kc) {
-                for (int p = 0; p < np && ok; ++p, ++c) {
-                    const int k0 = kc * OZT_KCH;
+            constexpr uint64_t slot16 = (uint64_t)(OZT_SLOT >> 4);
+            for (int w = 0; w < nwin && ok; ++w) {
+                const int k_lo = w * OZT_STAGES_PER_CHUNK;
+                const int k_hi = min(kst, k_lo + OZT_STAGES_PER_CHUNK);
+                for (int g = 0; g < OZT_GROUPS && ok; ++g, ++c) {
                     const int a = c & 1;
                     if (c >= 2 && !tc::mbar_wait(acce(a), (uint32_t)(((c >> 1) - 1) & 1), abort, err)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after();
-                    const uint32_t d = tmem + (uint32_t)(a * 128);
-                    const int k1 = min(kst, k0 + OZT_KCH);
-                    for (int k = k0; k < k1; ++k, ++gs) {
+                    const uint32_t d0 = tmem + (uint32_t)(a * 256), d1 = d0 + 128;
+                    bool f0 = true, f1 = true;
+                    for (int k = k_lo; k < k_hi; ++k, ++gs) {
                         const int st = gs % OZT_STAGES;
                         if (!tc::mbar_wait(full(st), (uint32_t)((gs / OZT_STAGES) & 1), abort, err)) {
                             ok = false;
                             break;
                         }
                         tc::fence_after();
-                        // descriptors of the stage's first Y and K tiles; a 16-k step adds 32 bytes (2 in the
-                        // address field) inside a 64-k tile, the second 64-k tile starts TILE_BYTES on
-                        const uint64_t da = tc::desc_sw128(sbase + st * OZT_STAGE_BYTES);
-                        const uint64_t db = da + (uint64_t)((2 * tc::TILE_BYTES) >> 4);
-                        constexpr uint64_t tstep = (uint64_t)(tc::TILE_BYTES >> 4);
-                        if (k == k0) tc::mma_bf16(d, da, db, OZT_IDESC, 0u);
-                        else tc::mma_bf16_acc(d, da, db, OZT_IDESC);
+                        const uint64_t y1 = tc::desc_sw64(sbase + st * OZT_STAGE_BYTES);
+                        const uint64_t y2 = y1 + slot16, k0 = y1 + 2 * slot16, k1 = k0 + slot16, k2 = k1 + slot16;
 #pragma unroll
-                        for (int kk = 1; kk < 8; ++kk) {
-                            const uint64_t off = (uint64_t)((kk >> 2) * tstep + 2 * (kk & 3));
-                            tc::mma_bf16_acc(d, da + off, db + off, OZT_IDESC);
+                        for (int kk = 0; kk < OZT_KS / 16; ++kk) {
+                            const uint64_t o = (uint64_t)(2 * kk);   // a 16-k step is 32 bytes
+                            if (g == 0) {   // level 2: (1,1); level 3: (1,2), (2,1)
+                                mma_first(d0, y1 + o, k0 + o, f0);
+                                mma_first(d1, y1 + o, k1 + o, f1);
+                                tc::mma_bf16_acc(d1, y2 + o, k0 + o, OZT_IDESC);
+                            } else {        // level 2g+2: (1, u0+1), (2, u0); level 2g+3: (1, u0+2), (2, u0+1)
+                                mma_first(d0, y1 + o, k1 + o, f0);
+                                tc::mma_bf16_acc(d0, y2 + o, k0 + o, OZT_IDESC);
+                                mma_first(d1, y1 + o, k2 + o, f1);
+                                tc::mma_bf16_acc(d1, y2 + o, k1 + o, OZT_IDESC);
+                            }
                         }
-                        tc::mma_commit_mc(empty(st), mask_rel);
+                        tc::mma_commit(empty(st));
                     }
                     if (ok) tc::mma_commit(accf(a));
                 }
@@ -216,95 +225,111 @@ __global__ __launch_bounds__(OZT_THREADS, 1) void k_ozaki_tc(
         }
     } else {
         const int wq = warp & 3, row = wq * 32 + lane, c0 = ((warp - 2) >> 2) * 64;
-        const uint32_t lrow = (uint32_t)(wq * 32) << 16;
-        const uint32_t t_hi = tmem + lrow + 256, t_lo = tmem + lrow + 384;
+        const uint32_t tl = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0;
+        float hi[64], lo[64];
+#pragma unroll
+        for (int q = 0; q < 64; ++q) hi[q] = lo[q] = 0.f;
         bool ok = true;
         int c = 0;
-        for (int kc = 0; kc < nkc && ok; ++kc) {
-            for (int p = 0; p < np; ++p, ++c) {
-                int s, u;
-                oz_pair_tc(p, lmax, s, u);
-                const float scale = ldexpf(1.f, -GP_OZ_BITS * (s + u));
+        for (int w = 0; w < nwin && ok; ++w) {
+            for (int g = 0; g < OZT_GROUPS; ++g, ++c) {
                 const int a = c & 1;
                 ok = __all_sync(0xffffffffu, tc::mbar_wait(accf(a), (uint32_t)((c >> 1) & 1), abort, err));
                 if (!ok) break;
                 tc::fence_after();
-                const uint32_t t_acc = tmem + lrow + (uint32_t)(a * 128);
-#pragma unroll 1
-                for (int col = c0; col < c0 + 64; col += 16) {
-                    float v[16], hi[16], lo[16];
-                    tc::tmem_ld16(t_acc + col, v);
-                    if (c == 0) {
+                // 2^{-7 l} for the group's levels l = 2g + 2 and 2g + 3 (normal FP32 powers of two)
+                const float sc0 = __int_as_float((127 - GP_OZ_BITS * (2 * g + 2)) << 23);
+                const float sc1 = __int_as_float((127 - GP_OZ_BITS * (2 * g + 3)) << 23);
+                const uint32_t ta = tl + (uint32_t)(a * 256);
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            hi[q] = v[q] * scale;
-                            lo[q] = 0.f;
-                        }
-                    } else {
-                        tc::tmem_ld16(t_hi + col, hi);
-                        tc::tmem_ld16(t_lo + col, lo);
+                for (int q8 = 0; q8 < 8; ++q8) {
+                    float v0[8], v1[8];
+                    tc::tmem_ld8x2(ta + 8 * q8, ta + 128 + 8 * q8, v0, v1);
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) {   // TwoSum of an exact term into hi + lo
-                            const float x = v[q] * scale;
-                            const float sm = hi[q] + x;
-                            const float bv = sm - hi[q];
-                            const float er = (hi[q] - (sm - bv)) + (x - bv);
-                            hi[q] = sm;
-                            lo[q] += er;
-                        }
+                    for (int e = 0; e < 8; ++e) {   // chunk sums are exact; the scaling by 2^-7l too
+                        two_sum_acc(hi[8 * q8 + e], lo[8 * q8 + e], v0[e] * sc0);
+                        two_sum_acc(hi[8 * q8 + e], lo[8 * q8 + e], v1[e] * sc1);
                     }
-                    tc::tmem_st16(t_hi + col, hi);
-                    tc::tmem_st16(t_lo + col, lo);
                 }
-                tc::tmem_st_wait();
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(acce(a));
             }
         }
+        // The running sums go back to tensor memory (every MMA has completed: the last
+        // chunk's commit covers all earlier ones), so the epilogue below can walk the
+        // columns in a rolled loop instead of holding 128 sums in registers.
+        if (ok) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float h16[16], l16[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    h16[e] = hi[16 * q + e];
+                    l16[e] = lo[16 * q + e];
+                }
+                tc::tmem_st16(tl + 16 * q, h16);
+                tc::tmem_st16(tl + 256 + 16 * q, l16);
+            }
+            tc::tmem_st_wait();
+        }
         // fused epilogue, one output row and 64 columns per thread
         const int64_t gm = m0 + row;
-        const bool live = ok && valid && gm < m;
+        const bool live = ok && gm < m;
         const double sc = live ? mu[gm] * (*kappa_p) : 0.0;
         double s1 = 0.0, s2 = 0.0;
-        const double* r64 = R64 + gm * Np + n0;
-        const float* yrow = Y + gm * Np + n0;
-        float* rr = Rr32 + gm * Np + n0;
+        const double* r64 = R64 + gm * Np + n0 + c0;
+        const float* yrow = Y + gm * Np + n0 + c0;
+        float* rr = Rr32 + gm * Np + n0 + c0;
 #pragma unroll 1
-        for (int col = c0; col < c0 + 64; col += 16) {
-            float hi[16], lo[16];
-            if (ok) {
-                tc::tmem_ld16(t_hi + col, hi);
-                tc::tmem_ld16(t_lo + col, lo);
-            }
-            if (!valid) continue;
+        for (int q = 0; q < 4; ++q) {
+            float h[16], l[16];
+            if (ok) tc::tmem_ld16x2(tl + 16 * q, tl + 256 + 16 * q, h, l);
+            double kc[16];
+            float x[16];
+            if (live) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int64_t gn = n0 + col + q;
-                float outv = 0.f;
-                if (!ok) {
-                    outv = __int_as_float(0x7fc00000);
-                } else if (live && gn < n_valid) {
-                    const double Cv = ((double)hi[q] + (double)lo[q]) * sc;
-                    const double kc = r64[col + q], x = (double)yrow[col + q];
-                    const double r = kc - Cv;
-                    outv = (float)r;
-                    s1 = fma(kc, x, s1);
-                    s2 = fma(x, r, s2);
+                for (int e = 0; e < 8; ++e) {
+                    const double2 v = __ldcs((const double2*)(r64 + 16 * q) + e);
+                    kc[2 * e] = v.x;
+                    kc[2 * e + 1] = v.y;
                 }
-                rr[col + q] = outv;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float4 v = __ldcs((const float4*)(yrow + 16 * q) + e);
+                    x[4 * e] = v.x;
+                    x[4 * e + 1] = v.y;
+                    x[4 * e + 2] = v.z;
+                    x[4 * e + 3] = v.w;
+                }
             }
+            float outv[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int64_t gn = n0 + c0 + 16 * q + e;
+                outv[e] = 0.f;
+                if (!ok) {
+                    outv[e] = __int_as_float(0x7fc00000);
+                } else if (live && gn < n_valid) {
+                    const double Cv = ((double)h[e] + (double)l[e]) * sc;
+                    const double r = kc[e] - Cv;
+                    outv[e] = (float)r;
+                    s1 = fma(kc[e], (double)x[e], s1);
+                    s2 = fma((double)x[e], r, s2);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                __stcs((float4*)(rr + 16 * q) + e,
+                       make_float4(outv[4 * e], outv[4 * e + 1], outv[4 * e + 2], outv[4 * e + 3]));
         }
         if (!ok) s1 = s2 = __longlong_as_double(0x7ff8000000000000ll);
-        if (valid) {
-            const int64_t nslot = Np / 64, slot = (n0 + c0) / 64;
-            qpart[slot * ldm + gm] = s1;
-            qpart[(nslot + slot) * ldm + gm] = s2;
-        }
+        const int64_t nslot = Np / 64, slot = (n0 + c0) / 64;
+        qpart[slot * ldm + gm] = s1;
+        qpart[(nslot + slot) * ldm + gm] = s2;
     }
     tc::fence_before();
     __syncthreads();
-    tc::cluster_sync();   // no partner still sends copies or releases into this CTA
     if (warp == 1) {
         __syncwarp();
         tc::fence_after();
@@ -328,17 +353,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// Row-major BF16 matrix (rows x cols, row stride cols) as 64 x 64 boxes
-// (half operand tiles), 128-byte swizzle.
-bool map_bf16_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols)
+// Row-major BF16 matrix (rows x cols, row stride cols) as 32-column x
+// 128-row boxes (one 8 KB operand tile), 64-byte swizzle.
+bool map_bf16_tiles32(CUtensorMap* map, const void* p, int64_t rows, int64_t cols)
 {
     auto enc = encode_fn();
-    if (!enc || ((uintptr_t)p & 15) || (cols * 2) % 16 || rows >= (1ll << 31)) return false;
+    if (!enc || ((uintptr_t)p & 15) || (cols * 2) % 16 || rows >= (1ll << 31) || cols >= (1ll << 31)) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {64, 64}, es[2] = {1, 1};
+    cuuint32_t box[2] = {(cuuint32_t)OZT_KS, 128}, es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(p), dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -361,31 +386,18 @@ bool ozaki_tc(gp_t h, int64_t m, int64_t ldm)
         done_dev = dev;
     }
     const int64_t Np = h->Np;
+    if (Np % 128 || ldm % 128) return false;
     CUtensorMap mY, mK;
-    if (!map_bf16_tiles(&mY, h->YS, GP_OZ_SLICES * ldm, Np) || !map_bf16_tiles(&mK, h->KS, GP_OZ_SLICES * Np, Np))
+    if (!map_bf16_tiles32(&mY, h->YS, GP_OZ_YSLICES * ldm, Np) || !map_bf16_tiles32(&mK, h->KS, GP_OZ_SLICES * Np, Np))
         return false;
     int* err = tc_error_dev();
     if (!err) return false;
-    const int64_t nbn2 = (Np / 128 + 1) / 2, nbm2 = (ldm / 128 + 1) / 2;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(4 * nbn2 * nbm2));
-    cfg.blockDim = dim3(OZT_THREADS);
-    cfg.dynamicSmemBytes = OZT_SMEM;
-    cfg.stream = h->st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 4;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const bool p_ = h->prof_on && prof_begin(h, GP_PH_OZAKI);
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_ozaki_tc, mY, mK, ldm, Np, (const double*)h->mu,
-                                             (const double*)h->kappa, (const double*)h->R64, (const float*)h->R32,
-                                             h->Rr32, h->qpart, m, h->n, h->oz_lmax, err);
-    h->launches++;
-    if (p_) prof_end(h);
-    return e == cudaSuccess;
+    const int64_t tiles = (Np / 128) * (ldm / 128);
+    if (tiles >= (1ll << 31)) return false;
+    GPK_LAUNCH(h, GP_PH_OZAKI, k_ozaki_tc, (unsigned)tiles, OZT_THREADS, OZT_SMEM, mY, mK, ldm, Np,
+               (const double*)h->mu, (const double*)h->kappa, (const double*)h->R64, (const float*)h->R32, h->Rr32,
+               h->qpart, m, h->n, err);
+    return true;
 }
 
 // Reads the tensor-core wait-timeout word (stream-ordered; valid after a

@@ -71,14 +71,18 @@ __global__ void k_mean_reduce_noalloc(const double* part, int64_t chunks, int64_
     mean[i] = s;
 }
 
-bool on_device(const void* p)
+// True for device memory of the current device, or managed memory.  Device
+// memory of another GPU is refused: the kernels would dereference it
+// without peer access.
+bool on_device(const void* p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Device address of the scratch array on the current device, looked up once
@@ -109,7 +113,10 @@ extern "C" gp_status gp_predict_mean_noalloc(const double* X, const double* alph
     if (!X || !alpha || !Xs || !mean || n < 1 || d < 1 || d > 1024 || m < 1 || m > NOALLOC_MAX_M ||
         !(lengthscale > 0.0) || !(vertical > 0.0) || !isfinite(lengthscale) || !isfinite(vertical))
         return GP_ERR_ARG;
-    if (!on_device(X) || !on_device(alpha) || !on_device(Xs) || !on_device(mean)) return GP_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GP_ERR_CUDA;
+    if (!on_device(X, dev) || !on_device(alpha, dev) || !on_device(Xs, dev) || !on_device(mean, dev))
+        return GP_ERR_ARG;
     double* part = nullptr;
     if (scratch_for_current_device(&part) != cudaSuccess) return GP_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;

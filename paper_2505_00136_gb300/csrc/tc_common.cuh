@@ -113,42 +113,6 @@ __device__ __forceinline__ void tma_load_4d_hint(uint32_t dst, const CUtensorMap
         ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "r"(z), "r"(w), "l"(policy) : "memory");
 }
 
-// As tma_load_2d, the box written to the same shared-memory offset in every
-// CTA of the cluster named in mask, each of whose mbarrier at offset mbar
-// receives the completed bytes.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar,
-                                               uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;\n"
-        ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "h"(mask) : "memory");
-}
-
-// As tma_load_2d_mc with an L2 cache policy.
-__device__ __forceinline__ void tma_load_2d_mc_hint(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar,
-                                                    uint16_t mask, uint64_t policy)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint"
-        " [%0], [%1, {%3, %4}], [%2], %5, %6;\n"
-        ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "h"(mask), "l"(policy) : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-    return r;
-}
-
-// All threads of all CTAs in the cluster; orders earlier shared-memory writes
-// (barrier initialisation included) before everything after it.
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
 {
@@ -228,13 +192,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
                  ::"r"(mbar) : "memory");
 }
 
-// As mma_commit, arriving on the mbarrier at offset mbar in every CTA of the cluster named in mask.
-__device__ __forceinline__ void mma_commit_mc(uint32_t mbar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n"
-                 ::"r"(mbar), "h"(mask) : "memory");
-}
-
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
@@ -265,6 +222,47 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
                  : "memory");
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Whole warp: 8 columns at each of two TMEM addresses, both loads issued
+// before one completion wait (one round trip instead of two).
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float (&va)[8], float (&vb)[8])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(ta), "r"(tb)
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        va[q] = __uint_as_float(r[q]);
+        vb[q] = __uint_as_float(r[8 + q]);
+    }
+}
+
+// Whole warp: 16 columns at each of two TMEM addresses, one completion wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&va)[16], float (&vb)[16])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(ta), "r"(tb)
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        va[q] = __uint_as_float(r[q]);
+        vb[q] = __uint_as_float(r[16 + q]);
+    }
 }
 
 // Whole warp: 32 consecutive columns, as tmem_ld16.

@@ -96,6 +96,7 @@ _SIGS = {
     "gp_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, _vp]),
     "gp_learned_init": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, ctypes.POINTER(gp_hyper), _vp]),
+    "gp_measure_fp64_peaks": (ctypes.c_int, [_vp, _vp, _vp]),
     "gp_last_error_info": (_i64, [_H]),
     "gp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "gp_destroy": (None, [_H]),
@@ -146,6 +147,14 @@ def auto_tiles(n: int) -> int:
     """Tiles per dimension chosen for n training points (``gp_auto_tiles``);
     ``GP(..., n_tiles=0)`` uses it."""
     return int(_lib.gp_auto_tiles(int(n)))
+
+
+def measure_fp64_peaks(stream=None):
+    """(DMMA, DFMA) FP64 TFLOP/s of the current GPU (``gp_measure_fp64_peaks``)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.gp_measure_fp64_peaks(ctypes.addressof(a), ctypes.addressof(b), stream), None,
+           "gp_measure_fp64_peaks")
+    return a.value, b.value
 
 
 def default_options() -> gp_options:

@@ -1,8 +1,9 @@
 """Each pin must bite: plant a plausible mistake in a copy of the oracle, on the
 CPU, and check that the pin suite fails on it.
 
-Mutants cover a dropped term, a wrong sign, a transposed operand or index and a
-wrong factor in every oracle routine the GPU path is compared with.
+Mutants cover a dropped term, a wrong sign, a transposed operand or index, a
+wrong factor and a wrong parameterisation in every oracle routine the GPU path
+is compared with.
 """
 import os
 import subprocess
@@ -32,16 +33,27 @@ MUTANTS = {
     "mlp_relu_mask_dropped": ("d2[k] = h2[k] > 0.0 ? a : 0.0;", "d2[k] = a;"),
     "summary_lag_off_by_one": ("c += (y[i] - ybar) * (y[i + lag] - ybar);",
                                "c += (y[i] - ybar) * (y[i + lag - 1] - ybar);"),
+    # Adam on the natural scale instead of log theta: every site of the log/exp map replaced
+    "optimize_natural_scale": [
+        ("double theta[3] = {log(hyp[0]), log(hyp[1]), log(hyp[2])};", "double theta[3] = {hyp[0], hyp[1], hyp[2]};"),
+        ("double h[3] = {exp(theta[0]), exp(theta[1]), exp(theta[2])};", "double h[3] = {theta[0], theta[1], theta[2]};"),
+        ("hyp[0] = exp(theta[0]);\n    hyp[1] = exp(theta[1]);\n    hyp[2] = exp(theta[2]);",
+         "hyp[0] = theta[0];\n    hyp[1] = theta[1];\n    hyp[2] = theta[2];"),
+    ],
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    orig, repl = MUTANTS[name]
+    sites = MUTANTS[name]
+    if isinstance(sites, tuple):
+        sites = [sites]
     src = open(SRC).read()
-    assert src.count(orig) == 1, f"mutation site for {name} not unique/present"
+    for orig, repl in sites:
+        assert src.count(orig) == 1, f"mutation site for {name} not unique/present"
+        src = src.replace(orig, repl)
     mut_c = tmp_path / "oracle_mut.c"
-    mut_c.write_text(src.replace(orig, repl))
+    mut_c.write_text(src)
     (tmp_path / "oracle.h").write_text(open(os.path.join(os.path.dirname(SRC), "oracle.h")).read())
     lib = oracle_mod.build(str(mut_c), str(tmp_path / "liboracle_mut.so"))
     env = dict(os.environ, GPRAT_ORACLE_LIB=lib)

@@ -315,6 +315,30 @@ def test_adam_mask_and_scale_invariance(orc):
     assert th_m[1] == 1.0 and th_m[0] != 1.0 and th_m[2] != 1.0
 
 
+def test_optimize_matches_torch_adam_on_log_parameters(orc):
+    """orc_optimize against an independent Adam (torch.optim.Adam, float64) acting
+    on log theta, each step fed the oracle's own gradient (pinned above by finite
+    differences): the NLML history and the final hyperparameters agree step by
+    step.  Adam on the natural scale, a dropped bias correction or a wrong sign
+    would each move the trajectory by far more than the bound."""
+    torch = pytest.importorskip("torch")
+    X, y, _, _ = small_set(n=48, d=4, seed=1006)
+    hyp0, steps, lr = (0.9, 1.2, 0.07), 25, 0.1
+    h_o, hist_o = orc.optimize(X, y, hyp0, steps=steps, lr=lr)
+    th = torch.tensor(np.log(hyp0), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([th], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    hist = []
+    for _ in range(steps):
+        f, g = orc.nlml_grad(X, y, np.exp(th.detach().numpy()))
+        hist.append(f)
+        opt.zero_grad()
+        th.grad = torch.from_numpy(g.copy())
+        opt.step()
+    assert max_rel(hist, hist_o) < 1e-10
+    assert max_rel(np.exp(th.detach().numpy()), h_o) < 1e-10
+    assert hist_o[-1] < hist_o[0]
+
+
 def test_optimize_history_and_descent(orc):
     X, y, _, _ = small_set(n=64, d=4, seed=1004)
     h, hist = orc.optimize(X, y, HYP, steps=30, lr=0.1)

@@ -76,6 +76,13 @@ def test_noalloc_rejects_oversize_and_host_buffers(env):
     host_out = np.empty(8)
     assert gprat.gp_predict_mean_noalloc(Xd.data_ptr(), alpha.data_ptr(), 256, 3, Xsd.data_ptr(), 8, 1.0, 1.0,
                                          host_out.ctypes.data, None) == gprat.GP_ERR_ARG
+    pinned = torch.empty(8, dtype=torch.float64).pin_memory()
+    assert gprat.gp_predict_mean_noalloc(Xd.data_ptr(), alpha.data_ptr(), 256, 3, Xsd.data_ptr(), 8, 1.0, 1.0,
+                                         pinned.data_ptr(), None) == gprat.GP_ERR_ARG
+    if torch.cuda.device_count() > 1:   # a buffer on another GPU is refused before any launch
+        other = torch.empty(8, dtype=torch.float64, device="cuda:1")
+        assert gprat.gp_predict_mean_noalloc(Xd.data_ptr(), alpha.data_ptr(), 256, 3, Xsd.data_ptr(), 8, 1.0,
+                                             1.0, other.data_ptr(), None) == gprat.GP_ERR_ARG
 
 
 def gprat_max_test(gprat):
