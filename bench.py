@@ -39,9 +39,10 @@ sys.path.insert(0, ROOT)
 METRIC = "predict+variance ms & NLML+grad steps/s @n=32768; mixed vs FP64 at 1e-8 rel"
 # Exact digit-pair products of k_ozaki_tc: x~0 in 2 digits, K in 6, pairs (s, u) with s + u <= 7.
 OZAKI_PAIRS = 11
-# DRAM bytes (read + write) of one k_ozaki_tc launch at N = 32768, M = 8192, from an
-# ncu capture of the current kernel (None until one exists).
-OZAKI_TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) of one k_ozaki_tc launch at N = 32768, M = 8192: the ncu
+# capture of the current kernel at N = 8192, M = 2048 (1.645 GB) scaled by the operand
+# stream M N^2 (x 64); None for any other size.
+OZAKI_TRAFFIC_FULL = 1.645e9 * 64
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL_BF16_TFLOPS = 2250.0      # dense, per GPU
 NOMINAL_FP64_TFLOPS = 1.25
@@ -409,7 +410,9 @@ def roofline(args, prof, T, b):
         roof = {"bound": "tensor", "kernel": "k_ozaki_tc (K x~0 for the exact variance correction, "
                                              f"{OZAKI_PAIRS} BF16 digit-pair products on tcgen05)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_note": peak_note, "traffic": OZAKI_TRAFFIC_PER_LAUNCH,
+                "peak_note": peak_note,
+                "traffic": OZAKI_TRAFFIC_FULL if (args.n, args.m) == (32768, 8192) else None,
+                "traffic_note": "ncu DRAM bytes at N=8192, M=2048 scaled by M N^2 to N=32768, M=8192",
                 "algorithmic_flops_per_launch": method_flops,
                 "work_note": "achieved/frac count the method's own work, 2 M N^2 (K x~0); the emulation "
                              f"executes {OZAKI_PAIRS}x that on the BF16 tensor pipe (tensor_op_frac)",
