@@ -130,6 +130,9 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     dev_free(h, &h->mu, old);
     dev_free(h, &h->qpart, 2 * old * (h->Np / 64));
     dev_free(h, &h->vpart2, old * (h->Np / 64));
+    dev_free(h, &h->ZSS, 6 * old * h->dp);
+    dev_free(h, &h->zs_mu, old);
+    dev_free(h, &h->zs_nrm, old);
     h->m_cap = 0;
     gp_status s;
     if ((s = dev_alloc(h, &h->Xs, ldm * h->d)) != GP_OK) return s;
@@ -148,6 +151,11 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     if ((s = dev_alloc(h, &h->vpart, ldm * (h->Np / 64))) != GP_OK) return s;     // one slot per 64 columns
     if ((s = dev_alloc(h, &h->outm, ldm)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->outv, ldm)) != GP_OK) return s;
+    if (h->tc_dist) {
+        if ((s = dev_alloc(h, &h->ZSS, 6 * ldm * h->dp)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->zs_mu, ldm)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->zs_nrm, ldm)) != GP_OK) return s;
+    }
     h->m_cap = ldm;
     return GP_OK;
 }
@@ -297,7 +305,11 @@ gp_status read_info(gp_t h)
 gp_status factor_mixed_refined(gp_t h)
 {
     gpk::set_info_none(h);
-    gpk::assemble_train(h);
+    if (h->tc_dist) {
+        if (!gpk::dist_train_tc(h)) return GP_ERR_CUDA;
+    } else {
+        gpk::assemble_train(h);
+    }
     if (!gpk::factor_mixed(h)) return GP_ERR_CUDA;
     gp_status s = check_launch(h);
     if (s != GP_OK) return s;
@@ -497,7 +509,7 @@ void gp_destroy(gp_t h)
                     h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
-                    h->dag_upd, h->dag_fin};
+                    h->dag_upd, h->dag_fin, h->ZXS, h->zx_mu, h->zx_nrm, h->ZSS, h->zs_mu, h->zs_nrm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int64_t i = 0; i < h->ev_cap; ++i) cudaEventDestroy(h->ev_pool[i]);
@@ -576,6 +588,13 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(dev_alloc(h, &h->res, h->Np));
         TRY(dev_alloc(h, &h->norms, 2));
         TRY(dev_alloc(h, &h->kappa, 1));
+        h->tc_dist = gpk::use_tc_dist(h);
+        if (h->tc_dist) {   // digit slices of the training rows for the tensor-core distances
+            h->dp = round_up(d, 32);
+            TRY(dev_alloc(h, &h->ZXS, 6 * h->Np * h->dp));
+            TRY(dev_alloc(h, &h->zx_mu, h->Np));
+            TRY(dev_alloc(h, &h->zx_nrm, h->Np));
+        }
     }
     TRY(cuda_status(h, cudaMemsetAsync(h->X, 0, (size_t)(h->Np * d) * sizeof(double), h->st)));
     TRY(cuda_status(h, cudaMemsetAsync(h->y, 0, (size_t)h->Np * sizeof(double), h->st)));
@@ -583,6 +602,10 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     TRY(copy_any(h, h->X, X, n * d));
     TRY(copy_any(h, h->y, y, n));
     TRY(cuda_status(h, cudaMemcpyAsync(h->hyp, &h->h_hyp, sizeof(GpHyperDev), cudaMemcpyHostToDevice, h->st)));
+    if (h->tc_dist) {
+        gpk::zslices(h, h->X, h->Np, h->n, h->ZXS, h->zx_mu, h->zx_nrm, GP_PH_ASSEMBLE);
+        TRY(check_launch(h));
+    }
     TRY(sync(h));
 #undef TRY
     *out = h;

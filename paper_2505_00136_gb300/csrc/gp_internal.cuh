@@ -94,6 +94,13 @@ struct gp_handle {
     double* qpart;            // 2 x (Np/64) x m_cap partial sums (one per 64 columns)
     double* vpart2;           // (Np/64) x m_cap partial sums of ||L~^{-1} r0||^2
     bool ks_valid;            // KS matches the current K
+    // tensor-core squared distances (GP_MIXED, d >= GP_TC_DIST_MIN_D; kernels_dist.cu)
+    bool tc_dist;
+    int64_t dp;               // regressors padded to a multiple of 32
+    __nv_bfloat16* ZXS;       // digit slices of the training rows, 6 x Np x dp
+    double *zx_mu, *zx_nrm;   // their row scales and |zhat|^2 (Np)
+    __nv_bfloat16* ZSS;       // digit slices of the test rows, 6 x m_cap x dp
+    double *zs_mu, *zs_nrm;   // their row scales and |zhat|^2 (m_cap)
     bool tc_pending;          // a tensor-core kernel ran since its timeout word was last read
     int* solve_flags;         // grid barrier of the persistent FP32 solve: arrival count, generation
     __nv_bfloat16* ZP;        // T(T+1)/2 tiles x 3 planes of (L^{-1})^T tiles (gradient)
@@ -182,11 +189,19 @@ bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov);
 bool tg_trtri_fin(gp_t h, int64_t t);
 bool tg_trtri_acc(gp_t h, int t0, int t1, int i0, int ni, int nj);   // U_ij (+)= sum_t Z_tj L_it^T
 bool tg_lauum(gp_t h);
+// squared distances on the tensor cores (kernels_dist.cu, kernels_mixed.cu)
+bool use_tc_dist(gp_t h);
+void zslices(gp_t h, const double* Z, int64_t rows, int64_t valid, __nv_bfloat16* ZS, double* mu, double* nrm,
+             int phase);
+bool dist_train_tc(gp_t h);                                     // K tiles into L (FP64) and A32
+bool dist_cross_tc(gp_t h, int64_t m, int64_t ldm);             // R32, R64, mean partials
+bool dist_prior_tc(gp_t h, int64_t m, int64_t ldm, double* out);   // K_{Z*,Z*} (m x m)
 bool tg_bdiag(gp_t h, int64_t ldm, int64_t i);                  // Y_i = S_i Linv_ii (NN form)
 bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj);   // S_j -= sum Y_i L_ij (NN form)
 constexpr int GP_OZ_SLICES = 6;                                // digit slices of K (kernels_mixed.cu)
 constexpr int GP_OZ_YSLICES = 2;                               // digit slices of x~0: x0 rounded to 14 bits per row
 constexpr int GP_OZ_BITS = 7;                                   // bits per signed digit: |d| <= 2^7, exact in BF16
+constexpr int GP_TC_DIST_MIN_D = 32;                           // mixed path: tensor-core distances from this d up
 constexpr int GP_OZ_LMAX = 7;                                   // digit pairs (s, u) with s + u <= 7 enter K x~0
 }  // namespace gpk
 

@@ -912,6 +912,51 @@ __global__ void k_yslices(float* Y, int64_t Np, __nv_bfloat16* YS, int64_t ps, d
     }
 }
 
+// Rows of Z (row-major, d columns; rows at or beyond `valid` read as zero)
+// as digit slices for the tensor-core squared distances (kernels_dist.cu):
+// mu[row] = power of two >= max_k |z_k|, q = rint(z 2^(OZ_B OZ_S) / mu),
+// ZS[s][row][k] = s-th balanced digit of q (zero for d <= k < dp), and
+// nrm[row] = sum_k zhat_k^2 in FP64 for the quantised row zhat = q mu 2^-42,
+// so that |zhat_i|^2 + |zhat_j|^2 - 2 zhat_i . zhat_j is the squared distance
+// of the quantised rows.  One warp per row, eight rows per CTA.
+__global__ void k_zslices(const double* Z, int64_t rows, int64_t valid, int64_t d, int64_t dp, __nv_bfloat16* ZS,
+                          int64_t ps, double* mu, double* nrm)
+{
+    const int64_t row = (int64_t)blockIdx.x * (NTH / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const bool live = row < valid;
+    const double* z = Z + row * d;
+    double mx = 0.0;
+    if (live)
+        for (int64_t k = lane; k < d; k += 32) mx = fmax(mx, fabs(z[k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double m = mx > 0.0 ? pow2_ceil(mx) : 1.0;
+    const int sc = OZ_B * OZ_S - pow2_exp(m);   // z / m 2^(OZ_B OZ_S) = z 2^sc
+    double acc = 0.0;
+    for (int64_t k = lane; k < dp; k += 32) {
+        const long long q = (live && k < d) ? rint_scaled(z[k], sc) : 0ll;
+        __nv_bfloat16 dg[OZ_S];
+        oz_digits<OZ_S>(q, dg);
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) ZS[s * ps + row * dp + k] = dg[s];
+        const double zh = ldexp((double)q, -sc);   // exact: |q| <= 2^42
+        acc = fma(zh, zh, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        mu[row] = m;
+        nrm[row] = acc;
+    }
+}
+
+void zslices(gp_t h, const double* Z, int64_t rows, int64_t valid, __nv_bfloat16* ZS, double* mu, double* nrm,
+             int phase)
+{
+    GPK_LAUNCH(h, phase, k_zslices, (unsigned)((rows + NTH / 32 - 1) / (NTH / 32)), NTH, 0, Z, rows, valid, h->d,
+               h->dp, ZS, rows * h->dp, mu, nrm);
+}
+
 // Digits of the full symmetric K (from the lower FP64 tiles) scaled by
 // kappa = power of two >= max(nu + sigma^2, 1).  One CTA per 64 x 64 block of
 // K: the block at (max, min) of its block indices is read row-wise from the
@@ -1116,9 +1161,14 @@ bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
     ensure_attrs_mixed();
     const int64_t Np = h->Np;
     const int64_t nmp = Np / 64, nvp = Np / 64;   // variance partials: one slot per 64 columns
-    GPK_LAUNCH(h, GP_PH_CROSS, k_cross_mixed, dim3((unsigned)(Np / 64), (unsigned)(ldm / 64)), NTH, 0,
-               (const double*)h->Xs, m, (const double*)h->X, h->n, h->d, (const double*)h->alpha,
-               (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm, h->R64);
+    if (h->tc_dist) {   // squared distances on the tensor cores (kernels_dist.cu)
+        zslices(h, h->Xs, ldm, m, h->ZSS, h->zs_mu, h->zs_nrm, GP_PH_CROSS);
+        if (!dist_cross_tc(h, m, ldm)) return false;
+    } else {
+        GPK_LAUNCH(h, GP_PH_CROSS, k_cross_mixed, dim3((unsigned)(Np / 64), (unsigned)(ldm / 64)), NTH, 0,
+                   (const double*)h->Xs, m, (const double*)h->X, h->n, h->d, (const double*)h->alpha,
+                   (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm, h->R64);
+    }
     if (want_var && !forward_w(h, h->R32, ldm, h->vpart, GP_PH_VSOLVE)) return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_mixed_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->mpart,
                nmp, (const double*)h->vpart, want_var ? nvp : (int64_t)0, ldm, m, (const GpHyperDev*)h->hyp,
@@ -1161,7 +1211,11 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 bool full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)
 {
     ensure_attrs_mixed();
-    assemble_test_prior(h, m, cov);
+    if (h->tc_dist) {   // the test digits were sliced by predict_mixed
+        if (!dist_prior_tc(h, m, ldm, cov)) return false;
+    } else {
+        assemble_test_prior(h, m, cov);
+    }
     return tg_syrk_cov(h, m, ldm, cov);
 }
 

@@ -101,6 +101,34 @@ def test_mixed_tiles_of_256_against_oracle(g, orc, n, m, d, n_tiles, ls):
         assert errs["grad"] < 1e-3
 
 
+@pytest.mark.parametrize("n,m,d,n_tiles,ls,noisy", [(1000, 200, 40, 4, 4.0, False), (777, 130, 160, 3, 8.0, True),
+                                                    (2048, 256, 128, 8, 1.0, False)])
+def test_mixed_tensor_core_distances_against_oracle(g, orc, n, m, d, n_tiles, ls, noisy):
+    """From 32 regressors up the mixed path forms every squared distance as
+    |z_i|^2 + |z_j|^2 - 2 z_i . z_j with the inner products an exact digit
+    product on the tensor cores (K tiles, K_{Z*,Z}, K_{Z*,Z*}).  Padded
+    regressor counts (40 -> 64), two exact chunks along the regressors (160),
+    tiles of 384 (three 128-row blocks per tile edge), ragged n and m, the
+    noisy test prior and the degenerate l = 1 at 128 regressors."""
+    X, y, Xs, _ = dg.msd_dataset(n, m, d, seed=1031 + n + d)
+    hyp = (ls, 1.0, 0.1)
+    mu_o, va_o, cv_o = orc.predict(X, y, Xs, hyp, cov=True, noisy=noisy)
+    with g.GP(X, y, hyp, n_tiles=n_tiles, precision="mixed", noisy_test_var=noisy) as gp:
+        mu, va, cv = gp.predict(Xs, mean=True, var=True, cov=True)
+        alpha = gp.get_alpha()
+    K = orc.cov_train(X, hyp)
+    alpha_o = sla.cho_solve(sla.cho_factor(K, lower=True), y)
+    errs = {"alpha": rel(alpha, alpha_o), "mean": rel(mu, mu_o),
+            "mean_worst": max_rel(mu, mu_o, 1e-3 * np.abs(mu_o).max() + 1e-300),
+            "var": rel(va, va_o), "var_worst": max_rel(va, va_o, 1e-12), "cov": rel(cv, cv_o)}
+    print("mixed tensor-core distances vs oracle", n, m, d, errs)
+    assert errs["alpha"] < 1e-10
+    assert errs["mean"] < MEAN_TOL and errs["mean_worst"] < MEAN_TOL
+    assert errs["var"] < VAR_TOL and errs["var_worst"] < VAR_TOL
+    assert errs["cov"] < 1e-4
+    assert np.array_equal(cv, cv.T)
+
+
 def test_mixed_not_pd(g):
     X = np.zeros((300, 3))
     with pytest.raises(g.GPError) as e:
