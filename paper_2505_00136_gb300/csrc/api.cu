@@ -603,7 +603,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     TRY(copy_any(h, h->y, y, n));
     TRY(cuda_status(h, cudaMemcpyAsync(h->hyp, &h->h_hyp, sizeof(GpHyperDev), cudaMemcpyHostToDevice, h->st)));
     if (h->tc_dist) {
-        gpk::zslices(h, h->X, h->Np, h->n, h->ZXS, h->zx_mu, h->zx_nrm, GP_PH_ASSEMBLE);
+        gpk::zslices(h, h->X, h->X, h->Np, h->n, h->ZXS, h->zx_mu, h->zx_nrm, GP_PH_ASSEMBLE);
         TRY(check_launch(h));
     }
     TRY(sync(h));

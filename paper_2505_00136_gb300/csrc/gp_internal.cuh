@@ -191,8 +191,8 @@ bool tg_trtri_acc(gp_t h, int t0, int t1, int i0, int ni, int nj);   // U_ij (+)
 bool tg_lauum(gp_t h);
 // squared distances on the tensor cores (kernels_dist.cu, kernels_mixed.cu)
 bool use_tc_dist(gp_t h);
-void zslices(gp_t h, const double* Z, int64_t rows, int64_t valid, __nv_bfloat16* ZS, double* mu, double* nrm,
-             int phase);
+void zslices(gp_t h, const double* Z, const double* center, int64_t rows, int64_t valid, __nv_bfloat16* ZS,
+             double* mu, double* nrm, int phase);                 // digits of Z - center (one row of d)
 bool dist_train_tc(gp_t h);                                     // K tiles into L (FP64) and A32
 bool dist_cross_tc(gp_t h, int64_t m, int64_t ldm);             // R32, R64, mean partials
 bool dist_prior_tc(gp_t h, int64_t m, int64_t ldm, double* out);   // K_{Z*,Z*} (m x m)

@@ -8,7 +8,9 @@
 // product of rank d, taken here as an exact digit product on the BF16 tensor
 // cores (the scheme of the variance correction, kernels_tc.cu):
 //
-//  - each row z is scaled by mu = a power of two >= max_k |z_k| and rounded to
+//  - each row, shifted by a common origin (the first training row for the K
+//    tiles and K_{Z*,Z}, the first test row for K_{Z*,Z*}), is scaled by
+//    mu = a power of two >= max_k |z_k| and rounded to
 //    42 bits, zhat = q mu 2^-42 (k_zslices); q is split into six balanced
 //    7-bit digits (|d| <= 2^7, exact in BF16) and |zhat|^2 is summed in FP64;
 //  - zhat_i . zhat_j = mu_i mu_j sum over digit pairs (s, u), s + u <= 8, of

@@ -912,15 +912,18 @@ __global__ void k_yslices(float* Y, int64_t Np, __nv_bfloat16* YS, int64_t ps, d
     }
 }
 
-// Rows of Z (row-major, d columns; rows at or beyond `valid` read as zero)
-// as digit slices for the tensor-core squared distances (kernels_dist.cu):
+// Rows of Z - c (row-major, d columns, c a row of d values; rows at or
+// beyond `valid` read as zero) as digit slices for the tensor-core squared
+// distances (kernels_dist.cu).  Distances do not change under the shift, and
+// with the origin c inside the data the rows stay short, so the cancellation
+// in |z_i|^2 + |z_j|^2 - 2 z_i . z_j stays small.  With z the shifted row:
 // mu[row] = power of two >= max_k |z_k|, q = rint(z 2^(OZ_B OZ_S) / mu),
 // ZS[s][row][k] = s-th balanced digit of q (zero for d <= k < dp), and
 // nrm[row] = sum_k zhat_k^2 in FP64 for the quantised row zhat = q mu 2^-42,
 // so that |zhat_i|^2 + |zhat_j|^2 - 2 zhat_i . zhat_j is the squared distance
 // of the quantised rows.  One warp per row, eight rows per CTA.
-__global__ void k_zslices(const double* Z, int64_t rows, int64_t valid, int64_t d, int64_t dp, __nv_bfloat16* ZS,
-                          int64_t ps, double* mu, double* nrm)
+__global__ void k_zslices(const double* Z, const double* c, int64_t rows, int64_t valid, int64_t d, int64_t dp,
+                          __nv_bfloat16* ZS, int64_t ps, double* mu, double* nrm)
 {
     const int64_t row = (int64_t)blockIdx.x * (NTH / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -929,13 +932,13 @@ __global__ void k_zslices(const double* Z, int64_t rows, int64_t valid, int64_t 
     const double* z = Z + row * d;
     double mx = 0.0;
     if (live)
-        for (int64_t k = lane; k < d; k += 32) mx = fmax(mx, fabs(z[k]));
+        for (int64_t k = lane; k < d; k += 32) mx = fmax(mx, fabs(z[k] - c[k]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const double m = mx > 0.0 ? pow2_ceil(mx) : 1.0;
     const int sc = OZ_B * OZ_S - pow2_exp(m);   // z / m 2^(OZ_B OZ_S) = z 2^sc
     double acc = 0.0;
     for (int64_t k = lane; k < dp; k += 32) {
-        const long long q = (live && k < d) ? rint_scaled(z[k], sc) : 0ll;
+        const long long q = (live && k < d) ? rint_scaled(z[k] - c[k], sc) : 0ll;
         __nv_bfloat16 dg[OZ_S];
         oz_digits<OZ_S>(q, dg);
 #pragma unroll
@@ -950,11 +953,11 @@ __global__ void k_zslices(const double* Z, int64_t rows, int64_t valid, int64_t 
     }
 }
 
-void zslices(gp_t h, const double* Z, int64_t rows, int64_t valid, __nv_bfloat16* ZS, double* mu, double* nrm,
-             int phase)
+void zslices(gp_t h, const double* Z, const double* center, int64_t rows, int64_t valid, __nv_bfloat16* ZS,
+             double* mu, double* nrm, int phase)
 {
-    GPK_LAUNCH(h, phase, k_zslices, (unsigned)((rows + NTH / 32 - 1) / (NTH / 32)), NTH, 0, Z, rows, valid, h->d,
-               h->dp, ZS, rows * h->dp, mu, nrm);
+    GPK_LAUNCH(h, phase, k_zslices, (unsigned)((rows + NTH / 32 - 1) / (NTH / 32)), NTH, 0, Z, center, rows, valid,
+               h->d, h->dp, ZS, rows * h->dp, mu, nrm);
 }
 
 // Digits of the full symmetric K (from the lower FP64 tiles) scaled by
@@ -1161,8 +1164,8 @@ bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
     ensure_attrs_mixed();
     const int64_t Np = h->Np;
     const int64_t nmp = Np / 64, nvp = Np / 64;   // variance partials: one slot per 64 columns
-    if (h->tc_dist) {   // squared distances on the tensor cores (kernels_dist.cu)
-        zslices(h, h->Xs, ldm, m, h->ZSS, h->zs_mu, h->zs_nrm, GP_PH_CROSS);
+    if (h->tc_dist) {   // squared distances on the tensor cores, origin at the first training row
+        zslices(h, h->Xs, h->X, ldm, m, h->ZSS, h->zs_mu, h->zs_nrm, GP_PH_CROSS);
         if (!dist_cross_tc(h, m, ldm)) return false;
     } else {
         GPK_LAUNCH(h, GP_PH_CROSS, k_cross_mixed, dim3((unsigned)(Np / 64), (unsigned)(ldm / 64)), NTH, 0,
@@ -1211,7 +1214,8 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 bool full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)
 {
     ensure_attrs_mixed();
-    if (h->tc_dist) {   // the test digits were sliced by predict_mixed
+    if (h->tc_dist) {   // test digits again, origin at the first test row (test-test distances only)
+        zslices(h, h->Xs, h->Xs, ldm, m, h->ZSS, h->zs_mu, h->zs_nrm, GP_PH_COV);
         if (!dist_prior_tc(h, m, ldm, cov)) return false;
     } else {
         assemble_test_prior(h, m, cov);
