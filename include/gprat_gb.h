@@ -49,7 +49,14 @@ typedef enum {
     GP_ERR_STATE = 6    /* call not valid in the handle's current state */
 } gp_status;
 
-typedef enum { GP_FP64 = 0, GP_MIXED = 1 } gp_precision;
+/* GP_FP64: every step in FP64 arithmetic.  GP_MIXED: FP32-accurate factor on
+ * the BF16 tensor cores, alpha, mean and variances refined or corrected to
+ * FP64 level (the NLML, gradient and full covariance stay FP32-accurate).
+ * GP_FP64_OZAKI: the FP64 path with the factorisation's trailing updates taken
+ * as exact digit products on the BF16 tensor cores (the Ozaki scheme: operands
+ * rounded to 49 bits, every level of digit products summed exactly), FP64
+ * level throughout; no counterpart in the paper. */
+typedef enum { GP_FP64 = 0, GP_MIXED = 1, GP_FP64_OZAKI = 2 } gp_precision;
 
 typedef enum {
     GP_SCHED_STREAM = 0,     /* one launch per tile step, stream ordered */
@@ -68,8 +75,8 @@ typedef struct {
 typedef struct {
     int n_tiles;            /* tiles per dimension T (paper: 1, 4, 16); tile size is
                                ceil(n / T) rounded up to a multiple of 64 (128 for
-                               GP_MIXED); 0 chooses T = gp_auto_tiles(n) */
-    gp_precision prec;      /* GP_FP64 or GP_MIXED */
+                               GP_MIXED and GP_FP64_OZAKI); 0 chooses T = gp_auto_tiles(n) */
+    gp_precision prec;      /* GP_FP64, GP_MIXED or GP_FP64_OZAKI */
     int noisy_test_var;     /* 1: add sigma^2 to predictive (co)variances */
     double refine_tol;      /* GP_MIXED: stop refinement at ||r|| / ||y|| < tol */
     int refine_max_iter;    /* GP_MIXED: at most this many refinement sweeps */

@@ -35,6 +35,10 @@ gp_status cuda_status(gp_t h, cudaError_t e)
 
 gp_status check_launch(gp_t h)
 {
+    if (h->host_fail) {   // a launch that could not be set up on the host (tensor-map encoding)
+        h->host_fail = false;
+        return GP_ERR_CUDA;
+    }
     return cuda_status(h, cudaGetLastError());
 }
 
@@ -248,7 +252,7 @@ void launch_factor_body(gp_t h, bool reset_err)
 {
     gpk::assemble_train(h);
     if (h->opt.scheduler == GP_SCHED_PERSISTENT) gpk::factor_dag(h, reset_err);
-    else gpk::factor_fp64(h);
+    else if (!gpk::factor_fp64(h)) h->host_fail = true;
     gpk::solve_lower(h, h->y, h->beta);
     gpk::solve_upper(h, h->beta, h->alpha);
     gpk::nlml_reduce(h);
@@ -509,7 +513,7 @@ void gp_destroy(gp_t h)
                     h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
-                    h->dag_upd, h->dag_fin, h->ZXS, h->zx_mu, h->zx_nrm, h->ZSS, h->zs_mu, h->zs_nrm};
+                    h->dag_upd, h->dag_fin, h->OGP, h->og_mu, h->ZXS, h->zx_mu, h->zx_nrm, h->ZSS, h->zs_mu, h->zs_nrm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int64_t i = 0; i < h->ev_cap; ++i) cudaEventDestroy(h->ev_pool[i]);
@@ -527,7 +531,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     if (opt_in) opt = *opt_in;
     else gp_default_options(&opt);
     if (!X || !y || n < 1 || d < 1 || d > 1024 || !hyper_ok(hyper) || opt.n_tiles < 0 ||
-        (opt.prec != GP_FP64 && opt.prec != GP_MIXED) ||
+        (opt.prec != GP_FP64 && opt.prec != GP_MIXED && opt.prec != GP_FP64_OZAKI) ||
         (opt.scheduler != GP_SCHED_STREAM && opt.scheduler != GP_SCHED_PERSISTENT) ||
         (opt.scheduler == GP_SCHED_PERSISTENT && opt.prec != GP_FP64) || opt.dag_timeout_ms < 0)
         return GP_ERR_ARG;
@@ -547,7 +551,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     h->d = d;
     h->dag_stall = -1;
     int64_t per = (n + opt.n_tiles - 1) / opt.n_tiles;
-    h->b = round_up(per, opt.prec == GP_MIXED ? 2 * TB : TB);
+    h->b = round_up(per, opt.prec != GP_FP64 ? 2 * TB : TB);   // tensor-core paths: 128-row blocks
     h->T = (n + h->b - 1) / h->b;
     h->Np = h->T * h->b;
     for (int p = 0; p < 3; ++p) h->trainable[p] = hyper->trainable[p] ? 1 : 0;
@@ -573,6 +577,10 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     TRY(dev_alloc(h, &h->info, 1));
     TRY(dev_alloc(h, &h->scal, 16));
     if (opt.scheduler == GP_SCHED_PERSISTENT) TRY(build_dag(h));
+    if (opt.prec == GP_FP64_OZAKI && h->T > 1) {   // digit slices of one panel of the factorisation
+        TRY(dev_alloc(h, &h->OGP, (int64_t)gpk::GP_OG_SLICES * (h->Np - h->b) * h->b));
+        TRY(dev_alloc(h, &h->og_mu, h->Np - h->b));
+    }
     if (opt.prec == GP_MIXED) {
         const int64_t bb = h->b * h->b;
         TRY(dev_alloc(h, &h->A32, tiles));

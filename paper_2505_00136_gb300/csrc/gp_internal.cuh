@@ -96,6 +96,10 @@ struct gp_handle {
     bool ks_valid;            // KS matches the current K
     // tensor-core squared distances (GP_MIXED, d >= GP_TC_DIST_MIN_D; kernels_dist.cu)
     bool tc_dist;
+    bool host_fail;           // a launch could not be set up on the host; reported by the next check
+    // GP_FP64_OZAKI: digit slices of the current panel, 7 x (Np - b) x b, and their row scales
+    __nv_bfloat16* OGP;
+    double* og_mu;
     int64_t dp;               // regressors padded to a multiple of 32
     __nv_bfloat16* ZXS;       // digit slices of the training rows, 6 x Np x dp
     double *zx_mu, *zx_nrm;   // their row scales and |zhat|^2 (Np)
@@ -147,7 +151,8 @@ namespace gpk {
 void assemble_train(gp_t h);                                   // K tiles into h->L
 void assemble_cross(gp_t h, int64_t m, int64_t ldm);           // B = K_{Z*,Z}^T (Np x ldm)
 void assemble_test_prior(gp_t h, int64_t m, double* out);      // out = K_{Z*,Z*} (+ noise), m x m
-void factor_fp64(gp_t h);                                      // tiled Cholesky in place
+bool factor_fp64(gp_t h);                                      // tiled Cholesky in place (false: host set-up failed)
+bool og_chol_update(gp_t h, int64_t k);                        // GP_FP64_OZAKI trailing update of step k
 void solve_lower(gp_t h, const double* rhs, double* out);      // out = L^{-1} rhs
 void solve_upper(gp_t h, const double* rhs, double* out);      // out = L^{-T} rhs
 void nlml_reduce(gp_t h);                                      // scal[0] = NLML
@@ -201,6 +206,7 @@ bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj);   // S_j -=
 constexpr int GP_OZ_SLICES = 6;                                // digit slices of K (kernels_mixed.cu)
 constexpr int GP_OZ_YSLICES = 2;                               // digit slices of x~0: x0 rounded to 14 bits per row
 constexpr int GP_OZ_BITS = 7;                                   // bits per signed digit: |d| <= 2^7, exact in BF16
+constexpr int GP_OG_SLICES = 7;                                // GP_FP64_OZAKI: 7-bit digits per operand (49 bits)
 constexpr int GP_TC_DIST_MIN_D = 32;                           // mixed path: tensor-core distances from this d up
 constexpr int GP_OZ_LMAX = 7;                                   // digit pairs (s, u) with s + u <= 7 enter K x~0
 }  // namespace gpk

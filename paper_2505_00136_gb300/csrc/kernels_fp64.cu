@@ -960,7 +960,7 @@ void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, do
     GPK_LAUNCH(h, GP_PH_POTRF, k_potrf_diag, 1, NT, POTRF_SMEM, A, X, b, row0, logdet_slot, h->info);
 }
 
-void factor_fp64(gp_t h)
+bool factor_fp64(gp_t h)
 {
     ensure_attrs();
     const int64_t T = h->T, b = h->b;
@@ -972,10 +972,15 @@ void factor_fp64(gp_t h)
             GPK_LAUNCH(h, GP_PH_TRSM, k_panel, dim3((unsigned)P, (unsigned)(T - k - 1)), NT,
                        DG_SMEM_BYTES, h->L, (const double*)h->Linv, b, k, (const unsigned long long*)h->info);
             const int64_t tt = T - k - 1;
-            GPK_LAUNCH(h, GP_PH_UPDATE, k_update, dim3((unsigned)(tt * (tt + 1) / 2), (unsigned)(P * P)),
-                       NT, DG_SMEM_BYTES, h->L, b, k, (const unsigned long long*)h->info);
+            if (h->opt.prec == GP_FP64_OZAKI) {   // exact digit products on the tensor cores
+                if (!og_chol_update(h, k)) return false;
+            } else {
+                GPK_LAUNCH(h, GP_PH_UPDATE, k_update, dim3((unsigned)(tt * (tt + 1) / 2), (unsigned)(P * P)),
+                           NT, DG_SMEM_BYTES, h->L, b, k, (const unsigned long long*)h->info);
+            }
         }
     }
+    return true;
 }
 
 void solve_lower(gp_t h, const double* rhs, double* out)

@@ -1,0 +1,437 @@
+// FP64-accurate tile products on the BF16 tensor cores (the Ozaki scheme:
+// Ozaki, Ogita, Oishi & Rump 2012), for the GP_FP64_OZAKI precision.
+//
+// C -= A B^T with A (rows x k) and B (cols x k) given as digit slices: every
+// row r of an operand is scaled by a power of two mu_r >= max |row| and
+// rounded to 49 bits, q = rint(v 2^49 / mu_r), and q is split into seven
+// balanced 7-bit digits (|d| <= 2^7, exact in BF16) stored slice-major,
+// k contiguous (k_rowslices).  Then
+//   (A B^T)_ij ~ mu_i mu_j sum over digit pairs (s, u), s + u <= 8, of
+//                2^{-7(s+u)} (A_s B_u^T)_ij,
+// every digit product exact (<= 2^14) and every sum of one level l = s + u
+// exact in an FP32 TMEM accumulator over chunks of 256 k (at most seven
+// pairs, one of them with a leading digit: 7 x 256 x 2^13 <= 2^24).  Chunk
+// sums are scaled by 2^{-7l} and added into double-FP32 running sums held in
+// registers (about 48 bits); the epilogue forms the FP64 product and
+// subtracts it from the FP64 destination.  The rounding of the operands to
+// 49 bits bounds the error of one product by about 2^-49 mu_i mu_j k: FP64
+// level for the factorisation and solves of this path.
+//
+// Operand reuse: the levels run in four groups, (2, 3), (4, 5), (6, 7) and
+// (8); a 32-k stage of a group holds the A and B slices that the group's
+// pairs use (up to 2 x 7 slices of 128 x 32, 8 KB each, two stages), and all
+// of the group's 3 to 11 pair products are issued from it.  Two pairs of
+// 128-column level accumulators alternate between successive group chunks
+// while the epilogue warps flush the previous one.
+//
+// Roles (320 threads, one CTA per 128 x 128 output block of an Op): warp 0
+// TMA loads, warp 1 MMA issue, warps 2-9 flush and epilogue, with bounded
+// waits (tc_common.cuh) that end in GP_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "digits.cuh"
+#include "gp_internal.cuh"
+#include "se_common.cuh"
+#include "tc_common.cuh"
+
+namespace gpk {
+namespace {
+
+constexpr int OG_S = GP_OG_SLICES;                        // digit slices per operand (7)
+constexpr int OG_KS = 32;                                 // k per stage
+constexpr int OG_SLOT = 128 * OG_KS * 2;                  // one 128 x 32 BF16 tile (8 KB)
+constexpr int OG_STAGE_BYTES = 2 * OG_S * OG_SLOT;        // A slices 1..7, B slices 1..7
+constexpr int OG_STAGES = 2;
+constexpr int OG_CHUNK = 256;                             // k per exact chunk
+constexpr int OG_SPC = OG_CHUNK / OG_KS;                  // stages per chunk
+constexpr int OG_GROUPS = 4;
+constexpr int OG_THREADS = 320;
+constexpr int OG_EPI_WARPS = 8;
+constexpr int OG_BAR_OFF = OG_STAGES * OG_STAGE_BYTES;
+constexpr int OG_SMEM = 1024 + OG_BAR_OFF + 256;
+constexpr uint32_t OG_IDESC = tc::idesc_bf16(128, 128);
+static_assert(OG_S == 7, "the level groups below are laid out for seven slices and levels 2..8");
+static_assert(OG_SMEM <= 227 * 1024, "shared memory");
+static_assert(7 * OG_CHUNK * (1 << 13) <= (1 << 24), "a level's chunk sum must stay exact in FP32");
+
+// Levels of group g: (2, 3), (4, 5), (6, 7), (8).
+__host__ __device__ constexpr int og_l0(int g) { return 2 + 2 * g; }
+__host__ __device__ constexpr int og_nl(int g) { return g == 3 ? 1 : 2; }
+// Pairs (s, l - s) of level l: s = og_smin(l) .. og_smax(l).
+__host__ __device__ constexpr int og_smin(int l) { return l - OG_S > 1 ? l - OG_S : 1; }
+__host__ __device__ constexpr int og_smax(int l) { return l - 1 < OG_S ? l - 1 : OG_S; }
+// Slices 1 .. og_top(g) of each operand feed group g.
+__host__ __device__ constexpr int og_top(int g) { return og_smax(og_l0(g) + og_nl(g) - 1); }
+
+__device__ __forceinline__ bool og_drain(uint32_t mbar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!tc::mbar_try(mbar, parity))
+        if (clock64() - t0 > tc::WAIT_CYCLES) return false;
+    return true;
+}
+
+__device__ __forceinline__ void og_two_sum(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bv = s - hi;
+    const float er = (hi - (s - bv)) + (x - bv);
+    hi = s;
+    lo += er;
+}
+
+// Where one output block reads its operands and writes its result.
+struct OgUnit {
+    int a_row, b_row;      // first row of the block in the A / B slice arrays (slice 1)
+    int k0, k1;            // k range (multiple of 32)
+    double* dst;           // first element of the 128 x 128 destination block
+    int64_t ld;            // its row stride
+    const double* muA;     // row scales of the block's 128 A rows
+    const double* muB;     // row scales of its 128 B rows
+    int rows, cols;        // valid rows / columns of the block (others are not written)
+};
+
+template <class Op>
+__global__ __launch_bounds__(OG_THREADS, 1) void k_ozgemm(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapB, const Op op,
+                                                        int* err)
+{
+    OgUnit un;
+    if (!op.unit((int)blockIdx.x, un)) return;
+
+    extern __shared__ unsigned char dyn[];
+    unsigned char* base = dyn + ((1024 - (tc::su32(dyn) & 1023)) & 1023);
+    const uint32_t sbase = tc::su32(base);
+    const uint32_t bar = sbase + OG_BAR_OFF;   // full[S], empty[S], accf[2], acce[2], drain
+    auto full = [&](int s) { return bar + 8 * s; };
+    auto empty = [&](int s) { return bar + 8 * (OG_STAGES + s); };
+    auto accf = [&](int a) { return bar + 8 * (2 * OG_STAGES + a); };
+    auto acce = [&](int a) { return bar + 8 * (2 * OG_STAGES + 2 + a); };
+    const uint32_t drain = bar + 8 * (2 * OG_STAGES + 4);
+    uint32_t* tmem_slot = (uint32_t*)(base + OG_BAR_OFF + 8 * (2 * OG_STAGES + 5));
+    volatile int* abort = (volatile int*)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OG_STAGES; ++s) {
+            tc::mbar_init(full(s), 1);
+            tc::mbar_init(empty(s), 1);
+        }
+        tc::mbar_init(accf(0), 1);
+        tc::mbar_init(accf(1), 1);
+        tc::mbar_init(acce(0), OG_EPI_WARPS);
+        tc::mbar_init(acce(1), OG_EPI_WARPS);
+        tc::mbar_init(drain, 1);
+        *abort = 0;
+        tc::mbar_init_fence();
+    }
+    if (warp == 1) tc::tmem_alloc(tc::su32(tmem_slot), 512);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int ks0 = un.k0 / OG_KS, ks1 = un.k1 / OG_KS;       // 32-k stages of the unit
+    const int nch = (ks1 - ks0 + OG_SPC - 1) / OG_SPC;         // exact chunks
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int gs = 0;
+            bool ok = true;
+            const uint64_t pol = tc::policy_evict_last();
+            for (int c = 0; c < nch && ok; ++c)
+                for (int g = 0; g < OG_GROUPS && ok; ++g) {
+                    const int top = og_top(g);
+                    for (int k = ks0 + c * OG_SPC; k < min(ks1, ks0 + (c + 1) * OG_SPC); ++k, ++gs) {
+                        const int st = gs % OG_STAGES, use = gs / OG_STAGES;
+                        if (use > 0 && !tc::mbar_wait(empty(st), (uint32_t)((use - 1) & 1), abort, err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t dst = sbase + st * OG_STAGE_BYTES;
+                        tc::mbar_expect_tx(full(st), (uint32_t)(2 * top * OG_SLOT));
+                        for (int s = 0; s < top; ++s) {
+                            tc::tma_load_2d_hint(dst + s * OG_SLOT, &mapA, k * OG_KS, s * op.a_ps + un.a_row, full(st),
+                                                 pol);
+                            tc::tma_load_2d_hint(dst + (OG_S + s) * OG_SLOT, &mapB, k * OG_KS, s * op.b_ps + un.b_row,
+                                                 full(st), pol);
+                        }
+                    }
+                }
+            if (!ok)   // let the copies in flight land before the CTA exits
+                for (int q = gs - 1; q >= 0 && q >= gs - OG_STAGES; --q)
+                    og_drain(full(q % OG_STAGES), (uint32_t)((q / OG_STAGES) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int gs = 0, cu = 0;
+            bool ok = true;
+            constexpr uint64_t slot16 = (uint64_t)(OG_SLOT >> 4);
+            for (int c = 0; c < nch && ok; ++c)
+                for (int g = 0; g < OG_GROUPS && ok; ++g, ++cu) {
+                    const int a = cu & 1;
+                    if (cu >= 2 && !tc::mbar_wait(acce(a), (uint32_t)(((cu >> 1) - 1) & 1), abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const int l0 = og_l0(g), nl = og_nl(g);
+                    bool first[2] = {true, true};
+                    for (int k = ks0 + c * OG_SPC; k < min(ks1, ks0 + (c + 1) * OG_SPC); ++k, ++gs) {
+                        const int st = gs % OG_STAGES;
+                        if (!tc::mbar_wait(full(st), (uint32_t)((gs / OG_STAGES) & 1), abort, err)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after();
+                        const uint64_t d0 = tc::desc_sw64(sbase + st * OG_STAGE_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < OG_KS / 16; ++kk)
+                            for (int li = 0; li < nl; ++li) {
+                                const int l = l0 + li;
+                                const uint32_t d = tmem + (uint32_t)(a * 256 + li * 128);
+                                for (int s = og_smin(l); s <= og_smax(l); ++s) {
+                                    const uint64_t da = d0 + (uint64_t)(s - 1) * slot16 + 2 * kk;
+                                    const uint64_t db = d0 + (uint64_t)(OG_S + l - s - 1) * slot16 + 2 * kk;
+                                    if (first[li]) tc::mma_bf16(d, da, db, OG_IDESC, 0u);
+                                    else tc::mma_bf16_acc(d, da, db, OG_IDESC);
+                                    first[li] = false;
+                                }
+                            }
+                        tc::mma_commit(empty(st));
+                    }
+                    if (ok) tc::mma_commit(accf(a));
+                }
+            if (!ok) {   // MMAs in flight finish before TMEM is released
+                tc::mma_commit(drain);
+                og_drain(drain, 0);
+            }
+        }
+    } else {
+        const int wq = warp & 3, row = wq * 32 + lane, cq = ((warp - 2) >> 2) * 64;
+        const uint32_t tl = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)cq;
+        float hi[64], lo[64];
+#pragma unroll
+        for (int q = 0; q < 64; ++q) hi[q] = lo[q] = 0.f;
+        bool ok = true;
+        int cu = 0;
+        for (int c = 0; c < nch && ok; ++c)
+            for (int g = 0; g < OG_GROUPS; ++g, ++cu) {
+                const int a = cu & 1;
+                ok = __all_sync(0xffffffffu, tc::mbar_wait(accf(a), (uint32_t)((cu >> 1) & 1), abort, err));
+                if (!ok) break;
+                tc::fence_after();
+                const int l0 = og_l0(g);
+                const float sc0 = __int_as_float((127 - 7 * l0) << 23);         // 2^{-7 l0}
+                const float sc1 = __int_as_float((127 - 7 * (l0 + 1)) << 23);   // 2^{-7 (l0 + 1)}
+                const uint32_t ta = tl + (uint32_t)(a * 256);
+                // one code path for both group shapes (two flush paths spilled registers): a
+                // one-level group selects zero for the second accumulator, whose columns hold
+                // an earlier group's sums
+                const bool two = og_nl(g) == 2;
+#pragma unroll
+                for (int q8 = 0; q8 < 8; ++q8) {
+                    float v0[8], v1[8];
+                    tc::tmem_ld8x2(ta + 8 * q8, ta + 128 + 8 * q8, v0, v1);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        og_two_sum(hi[8 * q8 + e], lo[8 * q8 + e], v0[e] * sc0);
+                        og_two_sum(hi[8 * q8 + e], lo[8 * q8 + e], two ? v1[e] * sc1 : 0.f);
+                    }
+                }
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(acce(a));
+            }
+        // every MMA has completed (the last chunk's commit covers the earlier ones): the
+        // running sums go to tensor memory and the epilogue walks them in a rolled loop
+        if (ok) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float h16[16], l16[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    h16[e] = hi[16 * q + e];
+                    l16[e] = lo[16 * q + e];
+                }
+                tc::tmem_st16(tl + 16 * q, h16);
+                tc::tmem_st16(tl + 128 + 16 * q, l16);
+            }
+            tc::tmem_st_wait();
+        }
+        // the TMEM loads are warp-collective: every lane takes part, only live rows store
+        const bool live = row < un.rows;
+        const double mi = live ? un.muA[row] : 0.0;
+        double* drow = un.dst + (int64_t)row * un.ld + cq;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            float h[16], lw[16];
+            if (ok) tc::tmem_ld16x2(tl + 16 * q, tl + 128 + 16 * q, h, lw);
+            if (!live) continue;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int col = cq + 16 * q + e;
+                if (col >= un.cols) continue;
+                const double v = ok ? ((double)h[e] + (double)lw[e]) * (mi * un.muB[col]) : 0.0;
+                drow[16 * q + e] = ok ? drow[16 * q + e] - v : __longlong_as_double(0x7ff8000000000000ll);
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------- operand slicing
+// Row r of an operand = n consecutive FP64 values at src(r).  mu[r] = power
+// of two >= max |row|, q = rint(v 2^49 / mu), OS[s][r][c] = s-th balanced
+// digit of q (slice stride ps rows).  One warp per row, eight rows per CTA.
+template <class Src>
+__global__ void k_rowslices(Src src, int64_t rows, int64_t n, __nv_bfloat16* OS, int64_t ps, double* mu)
+{
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const double* v = src(r);
+    double mx = 0.0;
+    for (int64_t c = lane; c < n; c += 32) mx = fmax(mx, fabs(v[c]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double m = mx > 0.0 ? pow2_ceil(mx) : 1.0;
+    const int sc = GP_OZ_BITS * OG_S - pow2_exp(m);   // v / m 2^49 = v 2^sc
+    for (int64_t c = lane; c < n; c += 32) {
+        __nv_bfloat16 d[OG_S];
+        oz_digits<OG_S>(rint_scaled(v[c], sc), d);
+#pragma unroll
+        for (int s = 0; s < OG_S; ++s) OS[s * ps + r * n + c] = d[s];
+    }
+    if (lane == 0) mu[r] = m;
+}
+
+// Row r of the panel below the diagonal tile k: row r % b of tile (k + 1 + r / b, k).
+struct PanelRows {
+    const double* L;
+    int64_t b, k;
+    __device__ const double* operator()(int64_t r) const
+    {
+        return L + tri_index(k + 1 + r / b, k) * b * b + (r % b) * b;
+    }
+};
+
+// ---------------------------------------------------------------- operations
+// Cholesky trailing update of step k: A_ij -= L_ik L_jk^T for k < j <= i,
+// A and B both the digit slices of the panel (rows of tiles k+1 .. T-1).
+struct OgChol {
+    double* L;
+    const double* mu;
+    int64_t b;
+    int k, tt, P;
+    int a_ps, b_ps;
+    const unsigned long long* info;
+    __device__ bool unit(int u, OgUnit& o) const
+    {
+        if (failed(info)) return false;
+        const int per = P * P;
+        int64_t ii, jj;
+        tri_decode(u / per, ii, jj);
+        const int rb = (u % per) / P, cb = (u % per) % P;
+        if (ii == jj && cb > rb) return false;
+        const int64_t i = k + 1 + ii, j = k + 1 + jj;
+        o.a_row = (int)(ii * b + rb * 128);
+        o.b_row = (int)(jj * b + cb * 128);
+        o.k0 = 0;
+        o.k1 = (int)b;
+        o.dst = L + tri_index(i, j) * b * b + (int64_t)rb * 128 * b + cb * 128;
+        o.ld = b;
+        o.muA = mu + o.a_row;
+        o.muB = mu + o.b_row;
+        o.rows = o.cols = 128;
+        return true;
+    }
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 og_encode_fn()
+{
+    static std::mutex mu_;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::lock_guard<std::mutex> lock(mu_);
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// Digit slices (OG_S x rows x n BF16, slice-major) as one 2-D map of
+// 32-column x 128-row boxes, 64-byte swizzle.
+bool og_map(CUtensorMap* map, const void* p, int64_t rows, int64_t n)
+{
+    auto enc = og_encode_fn();
+    const int64_t all = OG_S * rows;
+    if (!enc || ((uintptr_t)p & 15) || n % OG_KS || rows % 128 || all >= (1ll << 31)) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)all};
+    cuuint64_t strides[1] = {(cuuint64_t)n * 2};
+    cuuint32_t box[2] = {(cuuint32_t)OG_KS, 128}, es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(p), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class Op>
+bool og_launch(gp_t h, int phase, const CUtensorMap& mA, const CUtensorMap& mB, const Op& op, int64_t units)
+{
+    static int done_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done_dev != dev) {
+        cudaFuncSetAttribute(k_ozgemm<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, OG_SMEM);
+        done_dev = dev;
+    }
+    if (units <= 0) return true;
+    if (units >= (1ll << 31)) return false;
+    int* err = tc_error_dev();
+    if (!err) return false;
+    GPK_LAUNCH(h, phase, k_ozgemm<Op>, (unsigned)units, OG_THREADS, OG_SMEM, mA, mB, op, err);
+    h->tc_pending = true;
+    return true;
+}
+
+}  // namespace
+
+// Step k of the FP64 factorisation's trailing update on the tensor cores:
+// slices the panel (tiles (k+1 .. T-1, k)), then A_ij -= L_ik L_jk^T.
+bool og_chol_update(gp_t h, int64_t k)
+{
+    const int64_t T = h->T, b = h->b, tt = T - k - 1;
+    if (tt <= 0) return true;
+    const int64_t rows = tt * b;
+    GPK_LAUNCH(h, GP_PH_UPDATE, k_rowslices<PanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
+               PanelRows{h->L, b, k}, rows, b, h->OGP, rows, h->og_mu);
+    CUtensorMap mP;
+    if (!og_map(&mP, h->OGP, rows, b)) return false;
+    OgChol op;
+    op.L = h->L;
+    op.mu = h->og_mu;
+    op.b = b;
+    op.k = (int)k;
+    op.tt = (int)tt;
+    op.P = (int)(b / 128);
+    op.a_ps = op.b_ps = (int)rows;
+    op.info = h->info;
+    return og_launch(h, GP_PH_UPDATE, mP, mP, op, tt * (tt + 1) / 2 * op.P * op.P);
+}
+
+}  // namespace gpk

@@ -24,7 +24,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 GP_OK, GP_ERR_ARG, GP_ERR_NOT_PD, GP_ERR_CUDA, GP_ERR_OOM, GP_ERR_TIMEOUT, GP_ERR_STATE = range(7)
-GP_FP64, GP_MIXED = 0, 1
+GP_FP64, GP_MIXED, GP_FP64_OZAKI = 0, 1, 2
 GP_SCHED_STREAM, GP_SCHED_PERSISTENT = 0, 1
 GP_MLP_NPARAM = 83203
 GP_MLP_MODEL_FLOATS = GP_MLP_NPARAM + 128
@@ -177,7 +177,7 @@ class GP:
         n, d = X.shape
         opt = default_options()
         opt.n_tiles = int(n_tiles)
-        opt.prec = GP_MIXED if precision == "mixed" else GP_FP64
+        opt.prec = {"fp64": GP_FP64, "mixed": GP_MIXED, "fp64_ozaki": GP_FP64_OZAKI}[precision]
         opt.noisy_test_var = int(bool(noisy_test_var))
         opt.scheduler = GP_SCHED_PERSISTENT if scheduler == "persistent" else GP_SCHED_STREAM
         if refine_tol is not None:
