@@ -295,7 +295,7 @@ __global__ __launch_bounds__(OG_THREADS, 1) void k_ozgemm(const __grid_constant_
 // ---------------------------------------------------------------- operand slicing
 // Row r of an operand = n consecutive FP64 values at src(r).  mu[r] = power
 // of two >= max |row|, q = rint(v 2^49 / mu), OS[s][r][c] = s-th balanced
-// digit of q (slice stride ps rows).  One warp per row, eight rows per CTA.
+// digit of q (slices ps elements apart).  One warp per row, eight rows per CTA.
 template <class Src>
 __global__ void k_rowslices(Src src, int64_t rows, int64_t n, __nv_bfloat16* OS, int64_t ps, double* mu)
 {
@@ -419,7 +419,7 @@ bool og_chol_update(gp_t h, int64_t k)
     if (tt <= 0) return true;
     const int64_t rows = tt * b;
     GPK_LAUNCH(h, GP_PH_UPDATE, k_rowslices<PanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
-               PanelRows{h->L, b, k}, rows, b, h->OGP, rows, h->og_mu);
+               PanelRows{h->L, b, k}, rows, b, h->OGP, rows * b, h->og_mu);
     CUtensorMap mP;
     if (!og_map(&mP, h->OGP, rows, b)) return false;
     OgChol op;
