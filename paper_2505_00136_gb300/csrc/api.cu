@@ -109,6 +109,14 @@ gp_status ensure_grad_buffers(gp_t h)
         return dev_alloc(h, &h->gpart, h->gpart_cap);
     }
     if (h->Xinv) return GP_OK;
+    if (h->opt.prec == GP_FP64_OZAKI) {   // column digit slices of L^{-1} for the emulated inverse
+        const int64_t Np = h->Np;
+        if ((s = dev_alloc(h, &h->OGT, (int64_t)gpk::GP_OG_SLICES * Np * h->b)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->ogt_mu, Np)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->OGX, (int64_t)gpk::GP_OG_SLICES * Np * Np)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->ogx_mu, Np)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->ogx_bits, Np)) != GP_OK) return s;
+    }
     if ((s = dev_alloc(h, &h->Xinv, tiles)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->Kinv, tiles)) != GP_OK) return s;
     h->gpart_cap = ntri(h) * P * P * 3;
@@ -174,10 +182,13 @@ gp_status ensure_kslices(gp_t h)
 gp_status ensure_predict_space(gp_t h, int64_t m)
 {
     if (h->opt.prec == GP_MIXED) return ensure_predict_space_mixed(h, m);
-    const int64_t ldm = round_up(m, TB);
+    const bool emu = h->opt.prec == GP_FP64_OZAKI;   // 128-column blocks of test points
+    const int64_t ldm = round_up(m, emu ? 2 * TB : TB);
     if (ldm <= h->m_cap) return GP_OK;
     const int64_t old = h->m_cap;
     const int64_t old_part = old ? (2 * (h->Np / TB) > 64 ? 2 * (h->Np / TB) : 64) * old : 0;
+    dev_free(h, &h->OGV, (int64_t)gpk::GP_OG_SLICES * old * h->b);
+    dev_free(h, &h->ogv_mu, old);
     dev_free(h, &h->Xs, old * h->d);
     dev_free(h, &h->B, old * h->Np);
     dev_free(h, &h->V, old * h->Np);
@@ -193,7 +204,27 @@ gp_status ensure_predict_space(gp_t h, int64_t m)
     if ((s = dev_alloc(h, &h->part, rows_part * ldm)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->outm, ldm)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->outv, ldm)) != GP_OK) return s;
+    if (emu) {
+        if ((s = dev_alloc(h, &h->OGV, (int64_t)gpk::GP_OG_SLICES * ldm * h->b)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->ogv_mu, ldm)) != GP_OK) return s;
+    }
     h->m_cap = ldm;
+    return GP_OK;
+}
+
+// GP_FP64_OZAKI full covariance: digit slices of all of V (7 x m_cap x Np).
+gp_status ensure_cov_slices(gp_t h)
+{
+    if (h->ogc_cap >= h->m_cap) return GP_OK;
+    dev_free(h, &h->OGC, (int64_t)gpk::GP_OG_SLICES * h->ogc_cap * h->Np);
+    dev_free(h, &h->ogc_mu, h->ogc_cap);
+    dev_free(h, &h->ogc_bits, h->ogc_cap);
+    h->ogc_cap = 0;
+    gp_status s;
+    if ((s = dev_alloc(h, &h->OGC, (int64_t)gpk::GP_OG_SLICES * h->m_cap * h->Np)) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->ogc_mu, h->m_cap)) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->ogc_bits, h->m_cap)) != GP_OK) return s;
+    h->ogc_cap = h->m_cap;
     return GP_OK;
 }
 
@@ -365,7 +396,7 @@ gp_status predict_common(gp_t h, const double* Xs, int64_t m, int64_t* ldm_out)
     gp_status s;
     if ((s = ensure_factored(h)) != GP_OK) return s;
     if ((s = ensure_predict_space(h, m)) != GP_OK) return s;
-    *ldm_out = round_up(m, h->opt.prec == GP_MIXED ? 2 * TB : TB);
+    *ldm_out = round_up(m, h->opt.prec != GP_FP64 ? 2 * TB : TB);
     if ((s = copy_any(h, h->Xs, Xs, m * h->d)) != GP_OK) return s;
     if (h->opt.prec != GP_MIXED) gpk::assemble_cross(h, m, *ldm_out);
     return check_launch(h);
@@ -513,7 +544,8 @@ void gp_destroy(gp_t h)
                     h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
-                    h->dag_upd, h->dag_fin, h->OGP, h->og_mu, h->ZXS, h->zx_mu, h->zx_nrm, h->ZSS, h->zs_mu, h->zs_nrm};
+                    h->dag_upd, h->dag_fin, h->OGP, h->og_mu, h->OGT, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->ogv_mu,
+                    h->OGC, h->ogc_mu, h->ogc_bits, h->ZXS, h->zx_mu, h->zx_nrm, h->ZSS, h->zs_mu, h->zs_nrm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int64_t i = 0; i < h->ev_cap; ++i) cudaEventDestroy(h->ev_pool[i]);
@@ -638,7 +670,7 @@ gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* 
     } else if (!var && !cov) {  // Eq. 3 alone: one pass K_{Z*,Z} alpha, no solve
         gpk::predict_mean_only(h, m, ldm);
     } else {
-        gpk::predict_solve(h, m, ldm);
+        if (!gpk::predict_solve(h, m, ldm)) return GP_ERR_CUDA;
         gpk::predict_finish(h, m, ldm, var != nullptr);
     }
     if (cov) {
@@ -648,7 +680,10 @@ gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* 
             if ((s = ensure_cov_space(h, m)) != GP_OK) return s;
             target = h->cov;
         }
-        if (h->opt.prec != GP_MIXED) gpk::full_cov(h, m, ldm, target);
+        if (h->opt.prec != GP_MIXED) {
+            if (h->opt.prec == GP_FP64_OZAKI && (s = ensure_cov_slices(h)) != GP_OK) return s;
+            if (!gpk::full_cov(h, m, ldm, target)) return GP_ERR_CUDA;
+        }
         else if (!gpk::full_cov_mixed(h, m, ldm, target)) return GP_ERR_CUDA;
         if (!cov_dev) {
             if ((s = copy_any(h, cov, target, m * m)) != GP_OK) return s;
@@ -704,7 +739,9 @@ gp_status gp_nlml_grad(gp_t h, double* nlml, double grad[3])
     gp_status s = ensure_factored(h);
     if (s != GP_OK) return s;
     if ((s = ensure_grad_buffers(h)) != GP_OK) return s;
-    if (h->opt.prec != GP_MIXED) gpk::inverse_tiles(h);
+    if (h->opt.prec != GP_MIXED) {
+        if (!gpk::inverse_tiles(h)) return GP_ERR_CUDA;
+    }
     else if (!gpk::inverse_mixed(h)) return GP_ERR_CUDA;
     gpk::adjoint_grad(h);
     if ((s = check_launch(h)) != GP_OK) return s;
@@ -750,7 +787,10 @@ gp_status gp_optimize(gp_t h, int steps, double lr, double* nlml_hist)
             }
         }
         if (!mixed) {
-            gpk::inverse_tiles(h);
+            if (!gpk::inverse_tiles(h)) {
+                s = GP_ERR_CUDA;
+                break;
+            }
         } else if (!gpk::inverse_mixed(h)) {
             s = GP_ERR_CUDA;
             break;

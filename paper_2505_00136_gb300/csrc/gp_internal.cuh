@@ -100,6 +100,17 @@ struct gp_handle {
     // GP_FP64_OZAKI: digit slices of the current panel, 7 x (Np - b) x b, and their row scales
     __nv_bfloat16* OGP;
     double* og_mu;
+    // GP_FP64_OZAKI gradient: column slices of one row block of L^{-1} (7 x Np x b), of all
+    // of L^{-1} (7 x Np x Np), their column scales and the column maxima
+    __nv_bfloat16 *OGT, *OGX;
+    double *ogt_mu, *ogx_mu;
+    unsigned long long* ogx_bits;
+    // GP_FP64_OZAKI prediction: test columns of one row block of V (7 x m_cap x b), all of V
+    // (7 x m_cap x Np, allocated with the full covariance), their scales and column maxima
+    __nv_bfloat16 *OGV, *OGC;
+    double *ogv_mu, *ogc_mu;
+    unsigned long long* ogc_bits;
+    int64_t ogc_cap;
     int64_t dp;               // regressors padded to a multiple of 32
     __nv_bfloat16* ZXS;       // digit slices of the training rows, 6 x Np x dp
     double *zx_mu, *zx_nrm;   // their row scales and |zhat|^2 (Np)
@@ -153,14 +164,18 @@ void assemble_cross(gp_t h, int64_t m, int64_t ldm);           // B = K_{Z*,Z}^T
 void assemble_test_prior(gp_t h, int64_t m, double* out);      // out = K_{Z*,Z*} (+ noise), m x m
 bool factor_fp64(gp_t h);                                      // tiled Cholesky in place (false: host set-up failed)
 bool og_chol_update(gp_t h, int64_t k);                        // GP_FP64_OZAKI trailing update of step k
+bool og_trtri_accum(gp_t h, int64_t t);                        // GP_FP64_OZAKI inverse: S_ij += L_it X_tj
+bool og_lauum(gp_t h);                                         // GP_FP64_OZAKI K^{-1} = X^T X
+bool og_vsolve_update(gp_t h, int64_t j, int64_t ldm);          // GP_FP64_OZAKI V solve: B_i -= L_ij V_j
+bool og_full_cov(gp_t h, int64_t m, int64_t ldm, double* cov);  // GP_FP64_OZAKI cov -= V^T V
 void solve_lower(gp_t h, const double* rhs, double* out);      // out = L^{-1} rhs
 void solve_upper(gp_t h, const double* rhs, double* out);      // out = L^{-T} rhs
 void nlml_reduce(gp_t h);                                      // scal[0] = NLML
-void predict_solve(gp_t h, int64_t m, int64_t ldm);            // V, partial sums
+bool predict_solve(gp_t h, int64_t m, int64_t ldm);            // V, partial sums (false: host set-up failed)
 void predict_finish(gp_t h, int64_t m, int64_t ldm, bool want_var);  // outm, outv
 void predict_mean_only(gp_t h, int64_t m, int64_t ldm);      // outm = K_{Z*,Z} alpha
-void full_cov(gp_t h, int64_t m, int64_t ldm, double* cov);    // cov -= V^T V (mirrored)
-void inverse_tiles(gp_t h);                                    // Xinv = L^{-1}, Kinv = K^{-1}
+bool full_cov(gp_t h, int64_t m, int64_t ldm, double* cov);    // cov -= V^T V (mirrored; false: host set-up failed)
+bool inverse_tiles(gp_t h);                                    // Xinv = L^{-1}, Kinv = K^{-1} (false: host set-up failed)
 void adjoint_grad(gp_t h);                                     // scal[1..3] = grad
 void adam_step(gp_t h, double lr, double* hist_slot);          // Adam on log theta
 void copy_factor_dense(gp_t h, double* out);                   // L as dense n x n

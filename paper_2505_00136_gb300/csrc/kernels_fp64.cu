@@ -1016,7 +1016,7 @@ void nlml_reduce(gp_t h)
                (const double*)h->logdet_part, h->T, h->scal);
 }
 
-void predict_solve(gp_t h, int64_t m, int64_t ldm)
+bool predict_solve(gp_t h, int64_t m, int64_t ldm)
 {
     (void)m;
     const int64_t T = h->T, b = h->b;
@@ -1026,10 +1026,16 @@ void predict_solve(gp_t h, int64_t m, int64_t ldm)
         GPK_LAUNCH(h, GP_PH_VSOLVE, k_diagV, dim3((unsigned)P, (unsigned)(ldm / TB)), NT, DG_SMEM_BYTES,
                    (const double*)h->Linv, (const double*)h->B, h->V, (const double*)h->beta, h->part,
                    b, j, ldm, nq);
-        if (j + 1 < T)
-            GPK_LAUNCH(h, GP_PH_VSOLVE, k_updV, dim3((unsigned)((T - j - 1) * P), (unsigned)(ldm / TB)),
-                       NT, DG_SMEM_BYTES, (const double*)h->L, h->B, (const double*)h->V, b, j, ldm);
+        if (j + 1 < T) {
+            if (h->opt.prec == GP_FP64_OZAKI) {   // exact digit products on the tensor cores
+                if (!og_vsolve_update(h, j, ldm)) return false;
+            } else {
+                GPK_LAUNCH(h, GP_PH_VSOLVE, k_updV, dim3((unsigned)((T - j - 1) * P), (unsigned)(ldm / TB)),
+                           NT, DG_SMEM_BYTES, (const double*)h->L, h->B, (const double*)h->V, b, j, ldm);
+            }
+        }
     }
+    return true;
 }
 
 void predict_finish(gp_t h, int64_t m, int64_t ldm, bool want_var)
@@ -1049,30 +1055,40 @@ void predict_mean_only(gp_t h, int64_t m, int64_t ldm)
                (const double*)h->part, chunks, ldm, m, h->outm);
 }
 
-void full_cov(gp_t h, int64_t m, int64_t ldm, double* cov)
+bool full_cov(gp_t h, int64_t m, int64_t ldm, double* cov)
 {
     assemble_test_prior(h, m, cov);
+    if (h->opt.prec == GP_FP64_OZAKI) return og_full_cov(h, m, ldm, cov);
     const int64_t nb = (m + TB - 1) / TB;
     GPK_LAUNCH(h, GP_PH_COV, k_syrk_cov, (unsigned)(nb * (nb + 1) / 2), NT, DG_SMEM_BYTES,
                (const double*)h->V, h->Np, ldm, m, cov);
+    return true;
 }
 
-void inverse_tiles(gp_t h)
+bool inverse_tiles(gp_t h)
 {
     const int64_t T = h->T, b = h->b;
     const int P = (int)(b / TB);
+    const bool emu = h->opt.prec == GP_FP64_OZAKI;   // accumulations as exact digit products
     GPK_LAUNCH(h, GP_PH_TRTRI, k_copy_diag, grid_for(T * b * b), NT, 0, (const double*)h->Linv,
                h->Xinv, b, T);
     for (int64_t t = 0; t < T; ++t) {
         if (t > 0)
             GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_scale, dim3((unsigned)P, (unsigned)t), NT, DG_SMEM_BYTES,
                        (const double*)h->Linv, h->Xinv, b, t);
-        if (t + 1 < T)
-            GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_accum, dim3((unsigned)((T - t - 1) * (t + 1)), (unsigned)(P * P)),
-                       NT, DG_SMEM_BYTES, (const double*)h->L, h->Xinv, b, t);
+        if (t + 1 < T) {
+            if (emu) {
+                if (!og_trtri_accum(h, t)) return false;
+            } else {
+                GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_accum, dim3((unsigned)((T - t - 1) * (t + 1)), (unsigned)(P * P)),
+                           NT, DG_SMEM_BYTES, (const double*)h->L, h->Xinv, b, t);
+            }
+        }
     }
+    if (emu) return og_lauum(h);
     GPK_LAUNCH(h, GP_PH_LAUUM, k_lauum, dim3((unsigned)(T * (T + 1) / 2), (unsigned)(P * P)), NT,
                DG_SMEM_BYTES, (const double*)h->Xinv, h->Kinv, b, T);
+    return true;
 }
 
 void adjoint_grad(gp_t h)

@@ -1,7 +1,7 @@
 // FP64-accurate tile products on the BF16 tensor cores (the Ozaki scheme:
 // Ozaki, Ogita, Oishi & Rump 2012), for the GP_FP64_OZAKI precision.
 //
-// C -= A B^T with A (rows x k) and B (cols x k) given as digit slices: every
+// C = (C or 0) +- A B^T with A (rows x k) and B (cols x k) given as digit slices: every
 // row r of an operand is scaled by a power of two mu_r >= max |row| and
 // rounded to 49 bits, q = rint(v 2^49 / mu_r), and q is split into seven
 // balanced 7-bit digits (|d| <= 2^7, exact in BF16) stored slice-major,
@@ -12,8 +12,8 @@
 // exact in an FP32 TMEM accumulator over chunks of 256 k (at most seven
 // pairs, one of them with a leading digit: 7 x 256 x 2^13 <= 2^24).  Chunk
 // sums are scaled by 2^{-7l} and added into double-FP32 running sums held in
-// registers (about 48 bits); the epilogue forms the FP64 product and
-// subtracts it from the FP64 destination.  The rounding of the operands to
+// registers (about 48 bits); the epilogue forms the FP64 product and adds it
+// to (or subtracts it from, or stores it over) the FP64 destination.  The rounding of the operands to
 // 49 bits bounds the error of one product by about 2^-49 mu_i mu_j k: FP64
 // level for the factorisation and solves of this path.
 //
@@ -95,6 +95,8 @@ struct OgUnit {
     const double* muA;     // row scales of the block's 128 A rows
     const double* muB;     // row scales of its 128 B rows
     int rows, cols;        // valid rows / columns of the block (others are not written)
+    double sign;           // dst = (overwrite ? 0 : dst) + sign * A B^T
+    bool overwrite;
 };
 
 template <class Op>
@@ -279,7 +281,8 @@ __global__ __launch_bounds__(OG_THREADS, 1) void k_ozgemm(const __grid_constant_
                 const int col = cq + 16 * q + e;
                 if (col >= un.cols) continue;
                 const double v = ok ? ((double)h[e] + (double)lw[e]) * (mi * un.muB[col]) : 0.0;
-                drow[16 * q + e] = ok ? drow[16 * q + e] - v : __longlong_as_double(0x7ff8000000000000ll);
+                const double base = un.overwrite ? 0.0 : drow[16 * q + e];
+                drow[16 * q + e] = ok ? fma(un.sign, v, base) : __longlong_as_double(0x7ff8000000000000ll);
             }
         }
     }
@@ -315,6 +318,148 @@ __global__ void k_rowslices(Src src, int64_t rows, int64_t n, __nv_bfloat16* OS,
         for (int s = 0; s < OG_S; ++s) OS[s * ps + r * n + c] = d[s];
     }
     if (lane == 0) mu[r] = m;
+}
+
+// Columns of the tiles (t, 0 .. t) of X = L^{-1} as B-operand rows: row
+// n = j b + c holds column c of tile (t, j) over the tile's b rows (k), scaled
+// by mu[n] = power of two >= its max |.|; entries above the diagonal of the
+// diagonal tile (t, t) are taken as zero.  One CTA per 32 columns.
+__global__ __launch_bounds__(256) void k_colslices_tile(const double* X, int64_t b, int64_t t, __nv_bfloat16* OS,
+                                                        int64_t ps, double* mu)
+{
+    __shared__ double red[8][32];
+    __shared__ double smu[32];
+    const int64_t n0 = (int64_t)blockIdx.x * 32, j = n0 / b, c0 = n0 % b;
+    const double* tile = X + tri_index(t, j) * b * b;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double mx = 0.0;
+    for (int64_t r = w; r < b; r += 8)
+        if (!(j == t && r < c0 + lane)) mx = fmax(mx, fabs(tile[r * b + c0 + lane]));
+    red[w][lane] = mx;
+    __syncthreads();
+    if (w == 0) {
+        for (int q = 1; q < 8; ++q) mx = fmax(mx, red[q][lane]);
+        smu[lane] = mx > 0.0 ? pow2_ceil(mx) : 1.0;
+        mu[n0 + lane] = smu[lane];
+    }
+    __syncthreads();
+    for (int64_t r = threadIdx.x; r < b; r += 256)
+        for (int c = 0; c < 32; ++c) {
+            const double v = (j == t && r < c0 + c) ? 0.0 : tile[r * b + c0 + c];
+            __nv_bfloat16 d[OG_S];
+            oz_digits<OG_S>(rint_scaled(v, GP_OZ_BITS * OG_S - pow2_exp(smu[c])), d);
+#pragma unroll
+            for (int s = 0; s < OG_S; ++s) OS[s * ps + (n0 + c) * b + r] = d[s];
+        }
+}
+
+// Column maxima of the lower-triangular X = L^{-1} (tiles (t, j), t >= j),
+// as the bit patterns of non-negative doubles (ordered like the values):
+// bits[n] = max over rows of |X_{.,n}|.  Grid: (column groups of 32, row tiles).
+__global__ __launch_bounds__(256) void k_colmax_x(const double* X, int64_t b, unsigned long long* bits)
+{
+    __shared__ double red[8][32];
+    const int64_t n0 = (int64_t)blockIdx.x * 32, j = n0 / b, c0 = n0 % b, t = blockIdx.y;
+    if (t < j) return;
+    const double* tile = X + tri_index(t, j) * b * b;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double mx = 0.0;
+    for (int64_t r = w; r < b; r += 8)
+        if (!(j == t && r < c0 + lane)) mx = fmax(mx, fabs(tile[r * b + c0 + lane]));
+    red[w][lane] = mx;
+    __syncthreads();
+    if (w == 0) {
+        for (int q = 1; q < 8; ++q) mx = fmax(mx, red[q][lane]);
+        atomicMax(bits + n0 + lane, (unsigned long long)__double_as_longlong(mx));
+    }
+}
+
+// X^T as digit slices for the LAUUM product: row n (column n of X), k = row
+// of X, one power-of-two scale per column over all its rows (mu[n], from the
+// column maxima); rows of X above the column's tile are never read and are
+// not written.  Grid: (column groups of 32, row tiles t >= column tile).
+__global__ __launch_bounds__(256) void k_colslices_x(const double* X, int64_t b, int64_t Np,
+                                                     const unsigned long long* bits, __nv_bfloat16* OS, double* mu)
+{
+    __shared__ double smu[32];
+    const int64_t n0 = (int64_t)blockIdx.x * 32, j = n0 / b, c0 = n0 % b, t = blockIdx.y;
+    if (t < j) return;
+    const double* tile = X + tri_index(t, j) * b * b;
+    if (threadIdx.x < 32) {
+        const double mx = __longlong_as_double((long long)bits[n0 + threadIdx.x]);
+        smu[threadIdx.x] = mx > 0.0 ? pow2_ceil(mx) : 1.0;
+        if (t == j) mu[n0 + threadIdx.x] = smu[threadIdx.x];
+    }
+    __syncthreads();
+    const int64_t ps = Np * Np;
+    for (int64_t r = threadIdx.x; r < b; r += 256)
+        for (int c = 0; c < 32; ++c) {
+            const double v = (j == t && r < c0 + c) ? 0.0 : tile[r * b + c0 + c];
+            __nv_bfloat16 d[OG_S];
+            oz_digits<OG_S>(rint_scaled(v, GP_OZ_BITS * OG_S - pow2_exp(smu[c])), d);
+#pragma unroll
+            for (int s = 0; s < OG_S; ++s) OS[s * ps + (n0 + c) * Np + t * b + r] = d[s];
+        }
+}
+
+// Column maxima of a dense row-major block (nrows x 32 per CTA column group,
+// row stride ld) as ordered bit patterns: bits[n] = max |src[., n]|.  Grid:
+// (column groups of 32, row chunks of 256).
+__global__ __launch_bounds__(256) void k_colmax_dense(const double* src, int64_t ld, int64_t nrows,
+                                                      unsigned long long* bits)
+{
+    __shared__ double red[8][32];
+    const int64_t n0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 256;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double mx = 0.0;
+    for (int64_t r = r0 + w; r < nrows && r < r0 + 256; r += 8) mx = fmax(mx, fabs(src[r * ld + n0 + lane]));
+    red[w][lane] = mx;
+    __syncthreads();
+    if (w == 0) {
+        for (int q = 1; q < 8; ++q) mx = fmax(mx, red[q][lane]);
+        atomicMax(bits + n0 + lane, (unsigned long long)__double_as_longlong(mx));
+    }
+}
+
+// Columns of a dense row-major block as B-operand rows: row n holds column n
+// over rows r0 .. r0 + 255 of src (k = r), scale mu[n] from bits[n] (column
+// maxima); when bits is null, over all nrows rows with the scale from their
+// own maximum (then one row chunk).  Grid: (column groups of 32, row chunks).
+__global__ __launch_bounds__(256) void k_colslices_dense(const double* src, int64_t ld, int64_t nrows,
+                                                         const unsigned long long* bits, __nv_bfloat16* OS,
+                                                         int64_t ps, int64_t kstride, double* mu)
+{
+    __shared__ double red[8][32];
+    __shared__ double smu[32];
+    const int64_t n0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 256;
+    // one chunk of 256 rows with given maxima; all rows of the block without
+    const int64_t r1 = bits ? (r0 + 256 < nrows ? r0 + 256 : nrows) : nrows;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (bits) {
+        if (threadIdx.x < 32) {
+            const double mx = __longlong_as_double((long long)bits[n0 + threadIdx.x]);
+            smu[threadIdx.x] = mx > 0.0 ? pow2_ceil(mx) : 1.0;
+            if (blockIdx.y == 0) mu[n0 + threadIdx.x] = smu[threadIdx.x];
+        }
+    } else {
+        double mx = 0.0;
+        for (int64_t r = r0 + w; r < r1; r += 8) mx = fmax(mx, fabs(src[r * ld + n0 + lane]));
+        red[w][lane] = mx;
+        __syncthreads();
+        if (w == 0) {
+            for (int q = 1; q < 8; ++q) mx = fmax(mx, red[q][lane]);
+            smu[lane] = mx > 0.0 ? pow2_ceil(mx) : 1.0;
+            mu[n0 + lane] = smu[lane];
+        }
+    }
+    __syncthreads();
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += 256)
+        for (int c = 0; c < 32; ++c) {
+            __nv_bfloat16 d[OG_S];
+            oz_digits<OG_S>(rint_scaled(src[r * ld + n0 + c], GP_OZ_BITS * OG_S - pow2_exp(smu[c])), d);
+#pragma unroll
+            for (int s = 0; s < OG_S; ++s) OS[s * ps + (n0 + c) * kstride + r] = d[s];
+        }
 }
 
 // Row r of the panel below the diagonal tile k: row r % b of tile (k + 1 + r / b, k).
@@ -355,6 +500,125 @@ struct OgChol {
         o.muA = mu + o.a_row;
         o.muB = mu + o.b_row;
         o.rows = o.cols = 128;
+        o.sign = -1.0;
+        o.overwrite = false;
+        return true;
+    }
+};
+
+// Step t of the triangular inverse: S_ij (+)= L_it X_tj for i > t >= j (the
+// first contribution, t == j, stores), A = panel slices of column t, B =
+// column slices of the tiles (t, 0 .. t) of X.
+struct OgTrtri {
+    double* Xinv;
+    const double *muA, *muB;
+    int64_t b;
+    int t, P;
+    int a_ps, b_ps;
+    __device__ bool unit(int u, OgUnit& o) const
+    {
+        const int per = P * P, q = u / per;
+        const int ii = q / (t + 1), j = q % (t + 1);
+        const int rb = (u % per) / P, cb = (u % per) % P;
+        const int64_t i = t + 1 + ii;
+        o.a_row = (int)(ii * b + rb * 128);
+        o.b_row = (int)(j * b + cb * 128);
+        o.k0 = 0;
+        o.k1 = (int)b;
+        o.dst = Xinv + tri_index(i, j) * b * b + (int64_t)rb * 128 * b + cb * 128;
+        o.ld = b;
+        o.muA = muA + o.a_row;
+        o.muB = muB + o.b_row;
+        o.rows = o.cols = 128;
+        o.sign = 1.0;
+        o.overwrite = (j == t);
+        return true;
+    }
+};
+
+// K^{-1}_ij = sum_{k >= i b} X_ki X_kj on lower tiles (LAUUM): A and B are
+// rows of the column slices of all of X (one scale per column).
+struct OgLauum {
+    double* Kinv;
+    const double* mu;
+    int64_t b, Np;
+    int P;
+    int a_ps, b_ps;
+    __device__ bool unit(int u, OgUnit& o) const
+    {
+        const int per = P * P;
+        int64_t i, j;
+        tri_decode(u / per, i, j);
+        const int rb = (u % per) / P, cb = (u % per) % P;
+        if (i == j && cb > rb) return false;
+        o.a_row = (int)(i * b + rb * 128);
+        o.b_row = (int)(j * b + cb * 128);
+        o.k0 = (int)(i * b);
+        o.k1 = (int)Np;
+        o.dst = Kinv + tri_index(i, j) * b * b + (int64_t)rb * 128 * b + cb * 128;
+        o.ld = b;
+        o.muA = mu + o.a_row;
+        o.muB = mu + o.b_row;
+        o.rows = o.cols = 128;
+        o.sign = 1.0;
+        o.overwrite = true;
+        return true;
+    }
+};
+
+// Step j of the multi-right-hand-side solve V = L^{-1} K_{Z*,Z}^T:
+// B_i -= L_ij V_j for i > j, A = panel slices of column j, B = the test
+// columns of V_j (rows j b .. j b + b - 1 of V) as rows.
+struct OgVsolve {
+    double* B;
+    const double *muA, *muB;
+    int64_t b, ldm;
+    int j, P, nmb;
+    int a_ps, b_ps;
+    __device__ bool unit(int u, OgUnit& o) const
+    {
+        const int mb = u % nmb, rest = u / nmb;
+        const int rb = rest % P, ii = rest / P;
+        const int64_t i = j + 1 + ii;
+        o.a_row = (int)(ii * b + rb * 128);
+        o.b_row = mb * 128;
+        o.k0 = 0;
+        o.k1 = (int)b;
+        o.dst = B + (i * b + (int64_t)rb * 128) * ldm + (int64_t)mb * 128;
+        o.ld = ldm;
+        o.muA = muA + o.a_row;
+        o.muB = muB + o.b_row;
+        o.rows = o.cols = 128;
+        o.sign = -1.0;
+        o.overwrite = false;
+        return true;
+    }
+};
+
+// Full posterior covariance: cov (m x m, row stride m) -= V^T V, every
+// 128 x 128 block (both triangles: the blocks are computed independently and
+// come out exactly symmetric), A = B = the columns of V as rows.
+struct OgCov {
+    double* cov;
+    const double* mu;
+    int64_t m, Np;
+    int nmb;
+    int a_ps, b_ps;
+    __device__ bool unit(int u, OgUnit& o) const
+    {
+        const int ra = u / nmb, cb = u % nmb;
+        o.a_row = ra * 128;
+        o.b_row = cb * 128;
+        o.k0 = 0;
+        o.k1 = (int)Np;
+        o.dst = cov + (int64_t)ra * 128 * m + (int64_t)cb * 128;
+        o.ld = m;
+        o.muA = mu + o.a_row;
+        o.muB = mu + o.b_row;
+        o.rows = (int)(m - ra * 128 < 128 ? m - ra * 128 : 128);
+        o.cols = (int)(m - cb * 128 < 128 ? m - cb * 128 : 128);
+        o.sign = -1.0;
+        o.overwrite = false;
         return true;
     }
 };
@@ -432,6 +696,103 @@ bool og_chol_update(gp_t h, int64_t k)
     op.a_ps = op.b_ps = (int)rows;
     op.info = h->info;
     return og_launch(h, GP_PH_UPDATE, mP, mP, op, tt * (tt + 1) / 2 * op.P * op.P);
+}
+
+// Step t of the triangular inverse on the tensor cores (after the native
+// scaling X_tj = -Linv_tt S_tj of the row block): slices the panel of column t
+// and the row block (t, 0 .. t) of X, then S_ij (+)= L_it X_tj for i > t.
+bool og_trtri_accum(gp_t h, int64_t t)
+{
+    const int64_t T = h->T, b = h->b, tt = T - t - 1;
+    if (tt <= 0) return true;
+    const int64_t rows = tt * b, cols = (t + 1) * b;
+    GPK_LAUNCH(h, GP_PH_TRTRI, k_rowslices<PanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
+               PanelRows{h->L, b, t}, rows, b, h->OGP, rows * b, h->og_mu);
+    GPK_LAUNCH(h, GP_PH_TRTRI, k_colslices_tile, (unsigned)(cols / 32), 256, 0, (const double*)h->Xinv, b, t,
+               h->OGT, cols * b, h->ogt_mu);
+    CUtensorMap mA, mB;
+    if (!og_map(&mA, h->OGP, rows, b) || !og_map(&mB, h->OGT, cols, b)) return false;
+    OgTrtri op;
+    op.Xinv = h->Xinv;
+    op.muA = h->og_mu;
+    op.muB = h->ogt_mu;
+    op.b = b;
+    op.t = (int)t;
+    op.P = (int)(b / 128);
+    op.a_ps = (int)rows;
+    op.b_ps = (int)cols;
+    return og_launch(h, GP_PH_TRTRI, mA, mB, op, tt * (t + 1) * op.P * op.P);
+}
+
+// K^{-1} = X^T X (lower tiles) on the tensor cores from X = L^{-1}.
+bool og_lauum(gp_t h)
+{
+    const int64_t T = h->T, b = h->b, Np = h->Np;
+    cudaMemsetAsync(h->ogx_bits, 0, (size_t)Np * sizeof(unsigned long long), h->st);
+    GPK_LAUNCH(h, GP_PH_LAUUM, k_colmax_x, dim3((unsigned)(Np / 32), (unsigned)T), 256, 0, (const double*)h->Xinv,
+               b, h->ogx_bits);
+    GPK_LAUNCH(h, GP_PH_LAUUM, k_colslices_x, dim3((unsigned)(Np / 32), (unsigned)T), 256, 0,
+               (const double*)h->Xinv, b, Np, (const unsigned long long*)h->ogx_bits, h->OGX, h->ogx_mu);
+    CUtensorMap mX;
+    if (!og_map(&mX, h->OGX, Np, Np)) return false;
+    OgLauum op;
+    op.Kinv = h->Kinv;
+    op.mu = h->ogx_mu;
+    op.b = b;
+    op.Np = Np;
+    op.P = (int)(b / 128);
+    op.a_ps = op.b_ps = (int)Np;
+    return og_launch(h, GP_PH_LAUUM, mX, mX, op, T * (T + 1) / 2 * op.P * op.P);
+}
+
+// Step j of the V solve on the tensor cores (after the native V_j =
+// Linv_jj B_j): B_i -= L_ij V_j for every tile i > j.
+bool og_vsolve_update(gp_t h, int64_t j, int64_t ldm)
+{
+    const int64_t T = h->T, b = h->b, tt = T - j - 1;
+    if (tt <= 0) return true;
+    const int64_t rows = tt * b;
+    GPK_LAUNCH(h, GP_PH_VSOLVE, k_rowslices<PanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
+               PanelRows{h->L, b, j}, rows, b, h->OGP, rows * b, h->og_mu);
+    GPK_LAUNCH(h, GP_PH_VSOLVE, k_colslices_dense, dim3((unsigned)(ldm / 32), 1), 256, 0,
+               (const double*)(h->V + j * b * ldm), ldm, b, (const unsigned long long*)nullptr, h->OGV, ldm * b, b,
+               h->ogv_mu);
+    CUtensorMap mA, mB;
+    if (!og_map(&mA, h->OGP, rows, b) || !og_map(&mB, h->OGV, ldm, b)) return false;
+    OgVsolve op;
+    op.B = h->B;
+    op.muA = h->og_mu;
+    op.muB = h->ogv_mu;
+    op.b = b;
+    op.ldm = ldm;
+    op.j = (int)j;
+    op.P = (int)(b / 128);
+    op.nmb = (int)(ldm / 128);
+    op.a_ps = (int)rows;
+    op.b_ps = (int)ldm;
+    return og_launch(h, GP_PH_VSOLVE, mA, mB, op, tt * op.P * op.nmb);
+}
+
+// cov -= V^T V on the tensor cores (cov holds the test prior K_{Z*,Z*}).
+bool og_full_cov(gp_t h, int64_t m, int64_t ldm, double* cov)
+{
+    const int64_t Np = h->Np;
+    cudaMemsetAsync(h->ogc_bits, 0, (size_t)ldm * sizeof(unsigned long long), h->st);
+    const unsigned chunks = (unsigned)((Np + 255) / 256);
+    GPK_LAUNCH(h, GP_PH_COV, k_colmax_dense, dim3((unsigned)(ldm / 32), chunks), 256, 0, (const double*)h->V, ldm,
+               Np, h->ogc_bits);
+    GPK_LAUNCH(h, GP_PH_COV, k_colslices_dense, dim3((unsigned)(ldm / 32), chunks), 256, 0, (const double*)h->V,
+               ldm, Np, (const unsigned long long*)h->ogc_bits, h->OGC, ldm * Np, Np, h->ogc_mu);
+    CUtensorMap mV;
+    if (!og_map(&mV, h->OGC, ldm, Np)) return false;
+    OgCov op;
+    op.cov = cov;
+    op.mu = h->ogc_mu;
+    op.m = m;
+    op.Np = Np;
+    op.nmb = (int)((m + 127) / 128);
+    op.a_ps = op.b_ps = (int)ldm;
+    return og_launch(h, GP_PH_COV, mV, mV, op, (int64_t)op.nmb * op.nmb);
 }
 
 }  // namespace gpk

@@ -1,7 +1,9 @@
-"""GP_FP64_OZAKI: the FP64 path with the factorisation's trailing updates as
+"""GP_FP64_OZAKI: the FP64 path with its O(n^3) and O(n^2 m) products (the
+factorisation's trailing updates, the V solve's updates, the triangular
+inverse's accumulations, K^{-1} = L^{-T} L^{-1} and the full covariance) as
 exact digit products on the BF16 tensor cores, against the FP64 oracle at the
-FP64 path's tolerance (1e-9 relative on mean, variance, NLML, gradient and
-factor) and against the native FP64 GPU path.
+FP64 path's tolerance (1e-9 relative on mean, variance, covariance, NLML,
+gradient and factor) and against the native FP64 GPU path.
 """
 import numpy as np
 import pytest
@@ -32,21 +34,22 @@ def test_fp64_ozaki_against_oracle(g, orc, n, m, d, n_tiles, ls):
     384 (three 128-row blocks per tile edge), 128 regressors, one tile."""
     X, y, Xs, _ = dg.msd_dataset(n, m, d, seed=1041 + n + d)
     hyp = (ls, 1.0, 0.1)
-    mu_o, va_o, _ = orc.predict(X, y, Xs, hyp)
+    mu_o, va_o, cv_o = orc.predict(X, y, Xs, hyp, cov=True)
     f_o, g_o = orc.nlml_grad(X, y, hyp)
     K = orc.cov_train(X, hyp)
     L_o = orc.cholesky(K)
     with g.GP(X, y, hyp, n_tiles=n_tiles, precision="fp64_ozaki") as gp:
-        mu, va = gp.predict_var(Xs)
+        mu, va, cv = gp.predict(Xs, mean=True, var=True, cov=True)
         f, gr = gp.nlml_grad()
         L = gp.get_factor()
         info = gp.info()
     errs = {"mean": rel(mu, mu_o), "mean_worst": max_rel(mu, mu_o, 1e-3 * np.abs(mu_o).max()),
             "var": rel(va, va_o), "var_worst": max_rel(va, va_o, 1e-12), "nlml": abs(f - f_o) / abs(f_o),
-            "grad": rel(gr, g_o), "factor": rel(L, L_o), "tile": info["tile"]}
+            "grad": rel(gr, g_o), "factor": rel(L, L_o), "cov": rel(cv, cv_o), "tile": info["tile"]}
     print("fp64_ozaki vs oracle", n, m, d, errs)
     assert info["tile"] % 128 == 0
-    for k in ("mean", "var", "nlml", "grad", "factor"):
+    assert np.array_equal(cv, cv.T)
+    for k in ("mean", "var", "nlml", "grad", "factor", "cov"):
         assert errs[k] < TOL, (k, errs[k])
     assert errs["mean_worst"] < 10 * TOL and errs["var_worst"] < 10 * TOL
 
@@ -59,12 +62,12 @@ def test_fp64_ozaki_matches_native_fp64_path(g):
     out = {}
     for prec in ("fp64", "fp64_ozaki"):
         with g.GP(X, y, hyp, n_tiles=32, precision=prec) as gp:
-            mu, va = gp.predict_var(Xs)
+            mu, va, cv = gp.predict(Xs, mean=True, var=True, cov=True)
             f, gr = gp.nlml_grad()
-            out[prec] = (mu, va, f, gr, gp.get_alpha())
+            out[prec] = (mu, va, f, gr, gp.get_alpha(), cv)
     a, b = out["fp64_ozaki"], out["fp64"]
     errs = {"mean": rel(a[0], b[0]), "var": rel(a[1], b[1]), "nlml": abs(a[2] - b[2]) / abs(b[2]),
-            "grad": rel(a[3], b[3]), "alpha": rel(a[4], b[4])}
+            "grad": rel(a[3], b[3]), "alpha": rel(a[4], b[4]), "cov": rel(a[5], b[5])}
     print("fp64_ozaki vs fp64 @8192", errs)
     for k, v in errs.items():
         assert v < TOL, (k, v)
