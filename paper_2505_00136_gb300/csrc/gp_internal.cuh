@@ -102,7 +102,8 @@ struct gp_handle {
     double* og_mu;
     // GP_FP64_OZAKI gradient: column slices of one row block of L^{-1} (7 x Np x b), of all
     // of L^{-1} (7 x Np x Np), their column scales and the column maxima
-    __nv_bfloat16 *OGT, *OGX;
+    __nv_bfloat16 *OGT, *OGX, *OGL;   // OGL: row slices of one diagonal-tile inverse (7 x b x b)
+    double* ogl_mu;
     double *ogt_mu, *ogx_mu;
     unsigned long long* ogx_bits;
     // GP_FP64_OZAKI prediction: test columns of one row block of V (7 x m_cap x b), all of V
@@ -167,6 +168,9 @@ bool og_chol_update(gp_t h, int64_t k);                        // GP_FP64_OZAKI 
 bool og_trtri_accum(gp_t h, int64_t t);                        // GP_FP64_OZAKI inverse: S_ij += L_it X_tj
 bool og_lauum(gp_t h);                                         // GP_FP64_OZAKI K^{-1} = X^T X
 bool og_vsolve_update(gp_t h, int64_t j, int64_t ldm);          // GP_FP64_OZAKI V solve: B_i -= L_ij V_j
+bool og_vsolve_diag(gp_t h, int64_t j, int64_t ldm);            // GP_FP64_OZAKI V solve: V_j = Linv_jj B_j
+bool og_panel(gp_t h, int64_t k);                              // GP_FP64_OZAKI panel: L_ik = A_ik Linv_kk^T
+bool og_trtri_scale(gp_t h, int64_t t);                        // GP_FP64_OZAKI inverse: X_tj = -Linv_tt S_tj
 bool og_full_cov(gp_t h, int64_t m, int64_t ldm, double* cov);  // GP_FP64_OZAKI cov -= V^T V
 void solve_lower(gp_t h, const double* rhs, double* out);      // out = L^{-1} rhs
 void solve_upper(gp_t h, const double* rhs, double* out);      // out = L^{-T} rhs

@@ -969,12 +969,12 @@ bool factor_fp64(gp_t h)
         potrf_diag_launch(h, h->L + tri_index(k, k) * b * b, h->Linv + k * b * b, b, k * b,
                           h->logdet_part + k);
         if (k + 1 < T) {
-            GPK_LAUNCH(h, GP_PH_TRSM, k_panel, dim3((unsigned)P, (unsigned)(T - k - 1)), NT,
-                       DG_SMEM_BYTES, h->L, (const double*)h->Linv, b, k, (const unsigned long long*)h->info);
             const int64_t tt = T - k - 1;
             if (h->opt.prec == GP_FP64_OZAKI) {   // exact digit products on the tensor cores
-                if (!og_chol_update(h, k)) return false;
+                if (!og_panel(h, k) || !og_chol_update(h, k)) return false;
             } else {
+                GPK_LAUNCH(h, GP_PH_TRSM, k_panel, dim3((unsigned)P, (unsigned)(T - k - 1)), NT,
+                           DG_SMEM_BYTES, h->L, (const double*)h->Linv, b, k, (const unsigned long long*)h->info);
                 GPK_LAUNCH(h, GP_PH_UPDATE, k_update, dim3((unsigned)(tt * (tt + 1) / 2), (unsigned)(P * P)),
                            NT, DG_SMEM_BYTES, h->L, b, k, (const unsigned long long*)h->info);
             }
@@ -1023,9 +1023,13 @@ bool predict_solve(gp_t h, int64_t m, int64_t ldm)
     const int P = (int)(b / TB);
     const int64_t nq = h->Np / TB;
     for (int64_t j = 0; j < T; ++j) {
-        GPK_LAUNCH(h, GP_PH_VSOLVE, k_diagV, dim3((unsigned)P, (unsigned)(ldm / TB)), NT, DG_SMEM_BYTES,
-                   (const double*)h->Linv, (const double*)h->B, h->V, (const double*)h->beta, h->part,
-                   b, j, ldm, nq);
+        if (h->opt.prec == GP_FP64_OZAKI) {
+            if (!og_vsolve_diag(h, j, ldm)) return false;
+        } else {
+            GPK_LAUNCH(h, GP_PH_VSOLVE, k_diagV, dim3((unsigned)P, (unsigned)(ldm / TB)), NT, DG_SMEM_BYTES,
+                       (const double*)h->Linv, (const double*)h->B, h->V, (const double*)h->beta, h->part,
+                       b, j, ldm, nq);
+        }
         if (j + 1 < T) {
             if (h->opt.prec == GP_FP64_OZAKI) {   // exact digit products on the tensor cores
                 if (!og_vsolve_update(h, j, ldm)) return false;
@@ -1073,9 +1077,14 @@ bool inverse_tiles(gp_t h)
     GPK_LAUNCH(h, GP_PH_TRTRI, k_copy_diag, grid_for(T * b * b), NT, 0, (const double*)h->Linv,
                h->Xinv, b, T);
     for (int64_t t = 0; t < T; ++t) {
-        if (t > 0)
-            GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_scale, dim3((unsigned)P, (unsigned)t), NT, DG_SMEM_BYTES,
-                       (const double*)h->Linv, h->Xinv, b, t);
+        if (t > 0) {
+            if (emu) {
+                if (!og_trtri_scale(h, t)) return false;
+            } else {
+                GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_scale, dim3((unsigned)P, (unsigned)t), NT, DG_SMEM_BYTES,
+                           (const double*)h->Linv, h->Xinv, b, t);
+            }
+        }
         if (t + 1 < T) {
             if (emu) {
                 if (!og_trtri_accum(h, t)) return false;

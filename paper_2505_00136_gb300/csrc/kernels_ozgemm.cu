@@ -472,6 +472,32 @@ struct PanelRows {
     }
 };
 
+// Row r of the inverse Linv_kk of the diagonal tile k (upper triangle zero).
+struct LinvRows {
+    const double* Linv;
+    int64_t b, k;
+    __device__ const double* operator()(int64_t r) const { return Linv + k * b * b + r * b; }
+};
+
+// Partial sums of the V solve over 64-row blocks of V_j (rows j b ..):
+// part[0][q][c] = sum V^2, part[1][q][c] = sum V beta, q = j P + block.
+__global__ void k_vparts(const double* V, const double* beta, double* part, int64_t b, int64_t j, int64_t ldm,
+                         int64_t nq)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ldm) return;
+    const int64_t rb = blockIdx.y, row0 = j * b + rb * 64;
+    double sq = 0.0, sb = 0.0;
+    for (int r = 0; r < 64; ++r) {
+        const double v = V[(row0 + r) * ldm + c];
+        sq = fma(v, v, sq);
+        sb = fma(v, beta[row0 + r], sb);
+    }
+    const int64_t q = j * (b / 64) + rb;
+    part[q * ldm + c] = sq;
+    part[(nq + q) * ldm + c] = sb;
+}
+
 // ---------------------------------------------------------------- operations
 // Cholesky trailing update of step k: A_ij -= L_ik L_jk^T for k < j <= i,
 // A and B both the digit slices of the panel (rows of tiles k+1 .. T-1).
@@ -619,6 +645,65 @@ struct OgCov {
         o.cols = (int)(m - cb * 128 < 128 ? m - cb * 128 : 128);
         o.sign = -1.0;
         o.overwrite = false;
+        return true;
+    }
+};
+
+// Panel solve of step k: L_ik = A_ik Linv_kk^T over the tiles (i, k), i > k
+// (A = panel slices, B = rows of Linv_kk).
+struct OgPanel {
+    double* L;
+    const double *muA, *muB;
+    int64_t b;
+    int k, P;
+    int a_ps, b_ps;
+    const unsigned long long* info;
+    __device__ bool unit(int u, OgUnit& o) const
+    {
+        if (failed(info)) return false;   // a failed pivot: the factor is abandoned
+        const int per = P * P, ii = u / per, rb = (u % per) / P, cb = (u % per) % P;
+        o.a_row = (int)(ii * b + rb * 128);
+        o.b_row = cb * 128;
+        o.k0 = 0;
+        o.k1 = (int)b;
+        o.dst = L + tri_index(k + 1 + ii, k) * b * b + (int64_t)rb * 128 * b + cb * 128;
+        o.ld = b;
+        o.muA = muA + o.a_row;
+        o.muB = muB + o.b_row;
+        o.rows = o.cols = 128;
+        o.sign = 1.0;
+        o.overwrite = true;
+        return true;
+    }
+};
+
+// C = sign * A B^T stored over evenly spaced destination blocks, one k range
+// of b: the inverse's scaling X_tj = -Linv_tt S_tj (A = rows of Linv_tt, B =
+// columns of S_tj) and the V solve's V_j = Linv_jj B_j (A = rows of Linv_jj,
+// B = test columns of B_j).
+struct OgStore {
+    double* base;            // destination of unit (blk, rb, cb): base + blk * bstride + rb 128 ld + cb 128
+    int64_t bstride, ld;
+    const double *muA, *muB;
+    int nrb, ncb;            // 128-blocks per destination block along rows / columns
+    int a_blk, b_blk;        // A / B row offset per destination block (0 when shared)
+    int64_t b;
+    double sign;
+    int a_ps, b_ps;
+    __device__ bool unit(int u, OgUnit& o) const
+    {
+        const int per = nrb * ncb, blk = u / per, rb = (u % per) / ncb, cb = (u % per) % ncb;
+        o.a_row = blk * a_blk + rb * 128;
+        o.b_row = blk * b_blk + cb * 128;
+        o.k0 = 0;
+        o.k1 = (int)b;
+        o.dst = base + (int64_t)blk * bstride + (int64_t)rb * 128 * ld + (int64_t)cb * 128;
+        o.ld = ld;
+        o.muA = muA + o.a_row;
+        o.muB = muB + o.b_row;
+        o.rows = o.cols = 128;
+        o.sign = sign;
+        o.overwrite = true;
         return true;
     }
 };
@@ -793,6 +878,96 @@ bool og_full_cov(gp_t h, int64_t m, int64_t ldm, double* cov)
     op.nmb = (int)((m + 127) / 128);
     op.a_ps = op.b_ps = (int)ldm;
     return og_launch(h, GP_PH_COV, mV, mV, op, (int64_t)op.nmb * op.nmb);
+}
+
+// Row slices of the diagonal-tile inverse Linv_kk (b rows) into OGL.
+static void og_linv_slices(gp_t h, int64_t k, int phase)
+{
+    const int64_t b = h->b;
+    GPK_LAUNCH(h, phase, k_rowslices<LinvRows>, (unsigned)((b + 7) / 8), 256, 0, LinvRows{h->Linv, b, k}, b, b,
+               h->OGL, b * b, h->ogl_mu);
+}
+
+// Panel solve of step k on the tensor cores: L_ik = A_ik Linv_kk^T, i > k.
+bool og_panel(gp_t h, int64_t k)
+{
+    const int64_t T = h->T, b = h->b, tt = T - k - 1;
+    if (tt <= 0) return true;
+    const int64_t rows = tt * b;
+    GPK_LAUNCH(h, GP_PH_TRSM, k_rowslices<PanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
+               PanelRows{h->L, b, k}, rows, b, h->OGP, rows * b, h->og_mu);
+    og_linv_slices(h, k, GP_PH_TRSM);
+    CUtensorMap mA, mB;
+    if (!og_map(&mA, h->OGP, rows, b) || !og_map(&mB, h->OGL, b, b)) return false;
+    OgPanel op;
+    op.L = h->L;
+    op.muA = h->og_mu;
+    op.muB = h->ogl_mu;
+    op.b = b;
+    op.k = (int)k;
+    op.P = (int)(b / 128);
+    op.a_ps = (int)rows;
+    op.b_ps = (int)b;
+    op.info = h->info;
+    return og_launch(h, GP_PH_TRSM, mA, mB, op, tt * op.P * op.P);
+}
+
+// Scaling of step t of the triangular inverse on the tensor cores:
+// X_tj = -Linv_tt S_tj for j < t, over S_tj.
+bool og_trtri_scale(gp_t h, int64_t t)
+{
+    const int64_t b = h->b, cols = t * b;
+    if (t <= 0) return true;
+    og_linv_slices(h, t, GP_PH_TRTRI);
+    GPK_LAUNCH(h, GP_PH_TRTRI, k_colslices_tile, (unsigned)(cols / 32), 256, 0, (const double*)h->Xinv, b, t,
+               h->OGT, cols * b, h->ogt_mu);
+    CUtensorMap mA, mB;
+    if (!og_map(&mA, h->OGL, b, b) || !og_map(&mB, h->OGT, cols, b)) return false;
+    OgStore op;
+    op.base = h->Xinv + tri_index(t, 0) * b * b;   // tiles (t, 0 .. t-1) are consecutive
+    op.bstride = b * b;
+    op.ld = b;
+    op.muA = h->ogl_mu;
+    op.muB = h->ogt_mu;
+    op.nrb = op.ncb = (int)(b / 128);
+    op.a_blk = 0;
+    op.b_blk = (int)b;
+    op.b = b;
+    op.sign = -1.0;
+    op.a_ps = (int)b;
+    op.b_ps = (int)cols;
+    return og_launch(h, GP_PH_TRTRI, mA, mB, op, t * op.nrb * op.ncb);
+}
+
+// Diagonal step j of the V solve on the tensor cores: V_j = Linv_jj B_j (rows
+// j b .. of V), then its partial sums of V^2 and V beta.
+bool og_vsolve_diag(gp_t h, int64_t j, int64_t ldm)
+{
+    const int64_t b = h->b;
+    og_linv_slices(h, j, GP_PH_VSOLVE);
+    GPK_LAUNCH(h, GP_PH_VSOLVE, k_colslices_dense, dim3((unsigned)(ldm / 32), 1), 256, 0,
+               (const double*)(h->B + j * b * ldm), ldm, b, (const unsigned long long*)nullptr, h->OGV, ldm * b, b,
+               h->ogv_mu);
+    CUtensorMap mA, mB;
+    if (!og_map(&mA, h->OGL, b, b) || !og_map(&mB, h->OGV, ldm, b)) return false;
+    OgStore op;
+    op.base = h->V + j * b * ldm;
+    op.bstride = 128;   // one destination block per 128 test columns
+    op.ld = ldm;
+    op.muA = h->ogl_mu;
+    op.muB = h->ogv_mu;
+    op.nrb = (int)(b / 128);
+    op.ncb = 1;
+    op.a_blk = 0;
+    op.b_blk = 128;
+    op.b = b;
+    op.sign = 1.0;
+    op.a_ps = (int)b;
+    op.b_ps = (int)ldm;
+    if (!og_launch(h, GP_PH_VSOLVE, mA, mB, op, (ldm / 128) * op.nrb)) return false;
+    GPK_LAUNCH(h, GP_PH_VSOLVE, k_vparts, dim3((unsigned)((ldm + 255) / 256), (unsigned)(b / 64)), 256, 0,
+               (const double*)h->V, (const double*)h->beta, h->part, b, j, ldm, h->Np / 64);
+    return true;
 }
 
 }  // namespace gpk
