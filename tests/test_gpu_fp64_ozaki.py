@@ -71,3 +71,11 @@ def test_fp64_ozaki_matches_native_fp64_path(g):
     print("fp64_ozaki vs fp64 @8192", errs)
     for k, v in errs.items():
         assert v < TOL, (k, v)
+
+
+def test_fp64_ozaki_not_pd_reports_pivot(g):
+    X = np.zeros((300, 3))
+    with pytest.raises(g.GPError) as e:
+        with g.GP(X, np.ones(300), (1.0, 1.0, 0.0), n_tiles=3, precision="fp64_ozaki") as gp:
+            gp.factor()
+    assert e.value.status == g.GP_ERR_NOT_PD and e.value.info == 1
