@@ -64,6 +64,14 @@ def load(path: str | None = None):
                             ctypes.c_double, ctypes.c_double, _I]),
         "orc_optimize": (_i64, [_D, _D, _i64, _i64, _D, _I, _i64, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]),
+        "orc_kernel_cross": (None, [ctypes.c_int, _D, _i64, _D, _i64, _i64, ctypes.c_double, ctypes.c_double,
+                                    _D]),
+        "orc_cov_train_k": (None, [ctypes.c_int, _D, _i64, _i64, _D, _D]),
+        "orc_predict_k": (_i64, [ctypes.c_int, _D, _D, _i64, _i64, _D, _i64, _D, ctypes.c_int, _D, _D, _D]),
+        "orc_nlml_k": (_i64, [ctypes.c_int, _D, _D, _i64, _i64, _D, _D]),
+        "orc_nlml_grad_k": (_i64, [ctypes.c_int, _D, _D, _i64, _i64, _D, _D, _D]),
+        "orc_optimize_k": (_i64, [ctypes.c_int, _D, _D, _i64, _i64, _D, _I, _i64, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]),
         "orc_summary": (None, [_D, _D, _i64, _i64, _D, _D]),
         "orc_mlp_forward": (None, [_D, _i64, _D, _D]),
         "orc_mlp_loss_grad": (ctypes.c_double, [_D, _i64, _D, _D, _D]),
@@ -93,8 +101,14 @@ class OracleNotPD(RuntimeError):
         self.row = int(row)
 
 
+KERNELS = {"se": 0, "matern12": 1, "matern32": 2, "matern52": 3}
+
+
 class Oracle:
-    """Numpy-facing view of one oracle library (the default, or a test-built variant)."""
+    """Numpy-facing view of one oracle library (the default, or a test-built variant).
+
+    ``kernel`` selects the covariance function: "se" (Eq. 2, the default) or
+    the Matern kernels "matern12", "matern32", "matern52"."""
 
     MLP_NPARAM = 256 * 64 + 256 + 256 * 256 + 256 + 3 * 256 + 3
 
@@ -111,11 +125,18 @@ class Oracle:
         self.lib.orc_se_cross(_p(A), A.shape[0], _p(B), B.shape[0], A.shape[1], l, nu, _p(out))
         return out
 
-    def cov_train(self, X, hyp):
+    def kernel_cross(self, A, B, l, nu, kernel="se"):
+        A, B = _f64(A), _f64(B)
+        out = np.empty((A.shape[0], B.shape[0]))
+        self.lib.orc_kernel_cross(KERNELS[kernel], _p(A), A.shape[0], _p(B), B.shape[0], A.shape[1], l, nu,
+                                  _p(out))
+        return out
+
+    def cov_train(self, X, hyp, kernel="se"):
         X = _f64(X)
         n = X.shape[0]
         K = np.empty((n, n))
-        self.lib.orc_cov_train(_p(X), n, X.shape[1], _p(self._hyp(hyp)), _p(K))
+        self.lib.orc_cov_train_k(KERNELS[kernel], _p(X), n, X.shape[1], _p(self._hyp(hyp)), _p(K))
         return K
 
     def cholesky(self, K):
@@ -149,33 +170,34 @@ class Oracle:
         self.lib.orc_chol_inverse(_p(L), L.shape[0], _p(out))
         return out
 
-    def predict(self, X, y, Xs, hyp, noisy=False, mean=True, var=True, cov=False):
+    def predict(self, X, y, Xs, hyp, noisy=False, mean=True, var=True, cov=False, kernel="se"):
         X, y, Xs = _f64(X), _f64(y), _f64(Xs)
         n, d = X.shape
         m = Xs.shape[0]
         mu = np.empty(m) if mean else None
         va = np.empty(m) if var else None
         cv = np.empty((m, m)) if cov else None
-        info = self.lib.orc_predict(_p(X), _p(y), n, d, _p(Xs), m, _p(self._hyp(hyp)),
-                                    int(bool(noisy)), _p(mu), _p(va), _p(cv))
+        info = self.lib.orc_predict_k(KERNELS[kernel], _p(X), _p(y), n, d, _p(Xs), m, _p(self._hyp(hyp)),
+                                      int(bool(noisy)), _p(mu), _p(va), _p(cv))
         if info >= 0:
             raise OracleNotPD(info)
         return mu, va, cv
 
-    def nlml(self, X, y, hyp):
+    def nlml(self, X, y, hyp, kernel="se"):
         X, y = _f64(X), _f64(y)
         out = np.zeros(1)
-        info = self.lib.orc_nlml(_p(X), _p(y), X.shape[0], X.shape[1], _p(self._hyp(hyp)), _p(out))
+        info = self.lib.orc_nlml_k(KERNELS[kernel], _p(X), _p(y), X.shape[0], X.shape[1], _p(self._hyp(hyp)),
+                                   _p(out))
         if info >= 0:
             raise OracleNotPD(info)
         return float(out[0])
 
-    def nlml_grad(self, X, y, hyp):
+    def nlml_grad(self, X, y, hyp, kernel="se"):
         X, y = _f64(X), _f64(y)
         f = np.zeros(1)
         g = np.zeros(3)
-        info = self.lib.orc_nlml_grad(_p(X), _p(y), X.shape[0], X.shape[1],
-                                      _p(self._hyp(hyp)), _p(f), _p(g))
+        info = self.lib.orc_nlml_grad_k(KERNELS[kernel], _p(X), _p(y), X.shape[0], X.shape[1],
+                                        _p(self._hyp(hyp)), _p(f), _p(g))
         if info >= 0:
             raise OracleNotPD(info)
         return float(f[0]), g
@@ -189,13 +211,13 @@ class Oracle:
         return th, mo, ve
 
     def optimize(self, X, y, hyp, steps, lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8,
-                 trainable=(1, 1, 1)):
+                 trainable=(1, 1, 1), kernel="se"):
         X, y = _f64(X), _f64(y)
         h = self._hyp(hyp).copy()
         hist = np.empty(steps)
         tr = np.ascontiguousarray(trainable, dtype=np.int32)
-        info = self.lib.orc_optimize(_p(X), _p(y), X.shape[0], X.shape[1], _p(h),
-                                     tr.ctypes.data_as(_I), steps, lr, beta1, beta2, eps, _p(hist))
+        info = self.lib.orc_optimize_k(KERNELS[kernel], _p(X), _p(y), X.shape[0], X.shape[1], _p(h),
+                                       tr.ctypes.data_as(_I), steps, lr, beta1, beta2, eps, _p(hist))
         if info >= 0:
             raise OracleNotPD(info)
         return h, hist

@@ -33,11 +33,61 @@ void orc_se_cross(const double* A, int64_t na, const double* B, int64_t nb, int6
             out[i * nb + j] = nu * exp(-sqdist(A + i * d, B + j * d, d) / (2.0 * l * l));
 }
 
+/*
+ * Matern kernels of half-integer order (Rasmussen & Williams 2006, Eq. 4.17;
+ * the paper lists them as future work, Section 6), nu * m(r) with
+ * s = sqrt(2 p) r / l for order p = 1/2, 3/2, 5/2:
+ *   p = 1/2: m = exp(-s),  p = 3/2: m = (1 + s) exp(-s),
+ *   p = 5/2: m = (1 + s + s^2 / 3) exp(-s).
+ * kind: 1, 2, 3 for p = 1/2, 3/2, 5/2 (0 is the squared exponential of Eq. 2).
+ */
+static double matern_s(int kind, double r, double l)
+{
+    double c = kind == 1 ? 1.0 : (kind == 2 ? sqrt(3.0) : sqrt(5.0));
+    return c * r / l;
+}
+
+static double matern(int kind, double r, double l, double nu)
+{
+    double s = matern_s(kind, r, l);
+    if (kind == 1) return nu * exp(-s);
+    if (kind == 2) return nu * (1.0 + s) * exp(-s);
+    return nu * (1.0 + s + s * s / 3.0) * exp(-s);
+}
+
+/* d/d(log l) of the Matern kernel: ds/dlog l = -s, so with dm/ds
+ * p = 1/2: s exp(-s),  p = 3/2: s^2 exp(-s),  p = 5/2: s^2 (1 + s) exp(-s) / 3. */
+static double matern_dlogl(int kind, double r, double l, double nu)
+{
+    double s = matern_s(kind, r, l);
+    if (kind == 1) return nu * s * exp(-s);
+    if (kind == 2) return nu * s * s * exp(-s);
+    return nu * s * s * (1.0 + s) * exp(-s) / 3.0;
+}
+
+/* out[i*nb+j] = kernel `kind` between a_i and b_j, no delta term. */
+void orc_kernel_cross(int kind, const double* A, int64_t na, const double* B, int64_t nb, int64_t d,
+                      double l, double nu, double* out)
+{
+    if (kind == 0) {
+        orc_se_cross(A, na, B, nb, d, l, nu, out);
+        return;
+    }
+    for (int64_t i = 0; i < na; ++i)
+        for (int64_t j = 0; j < nb; ++j)
+            out[i * nb + j] = matern(kind, sqrt(sqdist(A + i * d, B + j * d, d)), l, nu);
+}
+
 /* Eq. 2 over all training pairs; the Kronecker delta adds sigma^2 when i == j. */
+void orc_cov_train_k(int kind, const double* X, int64_t n, int64_t d, const double* hyp, double* K)
+{
+    orc_kernel_cross(kind, X, n, X, n, d, hyp[0], hyp[1], K);
+    for (int64_t i = 0; i < n; ++i) K[i * n + i] += hyp[2];
+}
+
 void orc_cov_train(const double* X, int64_t n, int64_t d, const double* hyp, double* K)
 {
-    orc_se_cross(X, n, X, n, d, hyp[0], hyp[1], K);
-    for (int64_t i = 0; i < n; ++i) K[i * n + i] += hyp[2];
+    orc_cov_train_k(0, X, n, d, hyp, K);
 }
 
 /* Cholesky-Banachiewicz: row i, column j <= i, L_ij = (K_ij - sum_{k<j} L_ik L_jk) / L_jj. */
@@ -107,13 +157,13 @@ void orc_chol_inverse(const double* L, int64_t n, double* Kinv)
 }
 
 /* Shared first stage of prediction and likelihood: K, L, beta = L^{-1} y, alpha = K^{-1} y. */
-static int64_t factor_and_solve(const double* X, const double* y, int64_t n, int64_t d,
+static int64_t factor_and_solve(int kind, const double* X, const double* y, int64_t n, int64_t d,
                                 const double* hyp, double** L_out, double** beta_out,
                                 double** alpha_out)
 {
     double* K = (double*)malloc((size_t)(n * n) * sizeof(double));
     double* L = (double*)malloc((size_t)(n * n) * sizeof(double));
-    orc_cov_train(X, n, d, hyp, K);
+    orc_cov_train_k(kind, X, n, d, hyp, K);
     int64_t info = orc_cholesky(K, n, L);
     free(K);
     if (info >= 0) {
@@ -132,15 +182,15 @@ static int64_t factor_and_solve(const double* X, const double* y, int64_t n, int
     return -1;
 }
 
-int64_t orc_predict(const double* X, const double* y, int64_t n, int64_t d,
-                    const double* Xs, int64_t m, const double* hyp, int noisy,
-                    double* mean, double* var, double* cov)
+int64_t orc_predict_k(int kind, const double* X, const double* y, int64_t n, int64_t d,
+                      const double* Xs, int64_t m, const double* hyp, int noisy,
+                      double* mean, double* var, double* cov)
 {
     double *L, *beta, *alpha;
-    int64_t info = factor_and_solve(X, y, n, d, hyp, &L, &beta, &alpha);
+    int64_t info = factor_and_solve(kind, X, y, n, d, hyp, &L, &beta, &alpha);
     if (info >= 0) return info;
     double* Kc = (double*)malloc((size_t)(m * n) * sizeof(double)); /* K_{Z*,Z}, m x n */
-    orc_se_cross(Xs, m, X, n, d, hyp[0], hyp[1], Kc);
+    orc_kernel_cross(kind, Xs, m, X, n, d, hyp[0], hyp[1], Kc);
 
     /* Eq. 3: mean = K_{Z*,Z} K^{-1} y = K_{Z*,Z} alpha. */
     if (mean)
@@ -163,7 +213,7 @@ int64_t orc_predict(const double* X, const double* y, int64_t n, int64_t d,
                 var[i] = prior - s;
             }
         if (cov) {
-            orc_se_cross(Xs, m, Xs, m, d, hyp[0], hyp[1], cov); /* K_{Z*,Z*} */
+            orc_kernel_cross(kind, Xs, m, Xs, m, d, hyp[0], hyp[1], cov); /* K_{Z*,Z*} */
             for (int64_t i = 0; i < m; ++i) {
                 if (noisy) cov[i * m + i] += hyp[2];
                 for (int64_t k = 0; k < m; ++k) {
@@ -181,6 +231,13 @@ int64_t orc_predict(const double* X, const double* y, int64_t n, int64_t d,
     return -1;
 }
 
+int64_t orc_predict(const double* X, const double* y, int64_t n, int64_t d,
+                    const double* Xs, int64_t m, const double* hyp, int noisy,
+                    double* mean, double* var, double* cov)
+{
+    return orc_predict_k(0, X, y, n, d, Xs, m, hyp, noisy, mean, var, cov);
+}
+
 /* log|K| = 2 sum log L_ii and y^T K^{-1} y = beta^T beta give -(Eq. 5). */
 static double nlml_from(const double* L, const double* beta, int64_t n)
 {
@@ -192,11 +249,11 @@ static double nlml_from(const double* L, const double* beta, int64_t n)
     return 0.5 * fit + logdet_half + 0.5 * (double)n * log(2.0 * M_PI);
 }
 
-int64_t orc_nlml(const double* X, const double* y, int64_t n, int64_t d,
-                 const double* hyp, double* nlml)
+int64_t orc_nlml_k(int kind, const double* X, const double* y, int64_t n, int64_t d,
+                   const double* hyp, double* nlml)
 {
     double *L, *beta, *alpha;
-    int64_t info = factor_and_solve(X, y, n, d, hyp, &L, &beta, &alpha);
+    int64_t info = factor_and_solve(kind, X, y, n, d, hyp, &L, &beta, &alpha);
     if (info >= 0) return info;
     *nlml = nlml_from(L, beta, n);
     free(L);
@@ -205,18 +262,25 @@ int64_t orc_nlml(const double* X, const double* y, int64_t n, int64_t d,
     return -1;
 }
 
+int64_t orc_nlml(const double* X, const double* y, int64_t n, int64_t d,
+                 const double* hyp, double* nlml)
+{
+    return orc_nlml_k(0, X, y, n, d, hyp, nlml);
+}
+
 /*
  * dNLML/dtheta_p = 1/2 tr((K^{-1} - alpha alpha^T) dK/dtheta_p)
  * (Rasmussen & Williams 2006, Eq. 5.9, sign flipped for the negative), with
  *   dK/dlog l      = K_f .* r^2 / l^2,
  *   dK/dlog nu     = K_f,
- *   dK/dlog sigma2 = sigma^2 I.
+ *   dK/dlog sigma2 = sigma^2 I
+ * for the squared exponential, and dK/dlog l = matern_dlogl for a Matern kernel.
  */
-int64_t orc_nlml_grad(const double* X, const double* y, int64_t n, int64_t d,
-                      const double* hyp, double* nlml, double* grad)
+int64_t orc_nlml_grad_k(int kind, const double* X, const double* y, int64_t n, int64_t d,
+                        const double* hyp, double* nlml, double* grad)
 {
     double *L, *beta, *alpha;
-    int64_t info = factor_and_solve(X, y, n, d, hyp, &L, &beta, &alpha);
+    int64_t info = factor_and_solve(kind, X, y, n, d, hyp, &L, &beta, &alpha);
     if (info >= 0) return info;
     *nlml = nlml_from(L, beta, n);
     double* Kinv = (double*)malloc((size_t)(n * n) * sizeof(double));
@@ -227,8 +291,14 @@ int64_t orc_nlml_grad(const double* X, const double* y, int64_t n, int64_t d,
         for (int64_t j = 0; j < n; ++j) {
             double w = Kinv[i * n + j] - alpha[i] * alpha[j];
             double r2 = sqdist(X + i * d, X + j * d, d);
-            double kf = nu * exp(-r2 / (2.0 * l * l));
-            g_l += w * kf * r2 / (l * l);
+            double kf;
+            if (kind == 0) {
+                kf = nu * exp(-r2 / (2.0 * l * l));
+                g_l += w * kf * r2 / (l * l);
+            } else {
+                kf = matern(kind, sqrt(r2), l, nu);
+                g_l += w * matern_dlogl(kind, sqrt(r2), l, nu);
+            }
             g_nu += w * kf;
             if (i == j) g_s2 += w * s2;
         }
@@ -240,6 +310,12 @@ int64_t orc_nlml_grad(const double* X, const double* y, int64_t n, int64_t d,
     free(beta);
     free(alpha);
     return -1;
+}
+
+int64_t orc_nlml_grad(const double* X, const double* y, int64_t n, int64_t d,
+                      const double* hyp, double* nlml, double* grad)
+{
+    return orc_nlml_grad_k(0, X, y, n, d, hyp, nlml, grad);
 }
 
 /* Adam (Kingma & Ba 2015, Algorithm 1), only on trainable components. */
@@ -256,16 +332,16 @@ void orc_adam(double* theta, double* mom, double* vel, const double* g, int64_t 
     }
 }
 
-int64_t orc_optimize(const double* X, const double* y, int64_t n, int64_t d, double* hyp,
-                     const int* trainable, int64_t steps, double lr, double beta1,
-                     double beta2, double eps, double* nlml_hist)
+int64_t orc_optimize_k(int kind, const double* X, const double* y, int64_t n, int64_t d, double* hyp,
+                       const int* trainable, int64_t steps, double lr, double beta1,
+                       double beta2, double eps, double* nlml_hist)
 {
     double theta[3] = {log(hyp[0]), log(hyp[1]), log(hyp[2])};
     double mom[3] = {0, 0, 0}, vel[3] = {0, 0, 0};
     for (int64_t s = 0; s < steps; ++s) {
         double h[3] = {exp(theta[0]), exp(theta[1]), exp(theta[2])};
         double f, g[3];
-        int64_t info = orc_nlml_grad(X, y, n, d, h, &f, g);
+        int64_t info = orc_nlml_grad_k(kind, X, y, n, d, h, &f, g);
         if (info >= 0) return info;
         if (nlml_hist) nlml_hist[s] = f;
         orc_adam(theta, mom, vel, g, s + 1, lr, beta1, beta2, eps, trainable);
@@ -274,6 +350,13 @@ int64_t orc_optimize(const double* X, const double* y, int64_t n, int64_t d, dou
     hyp[1] = exp(theta[1]);
     hyp[2] = exp(theta[2]);
     return -1;
+}
+
+int64_t orc_optimize(const double* X, const double* y, int64_t n, int64_t d, double* hyp,
+                     const int* trainable, int64_t steps, double lr, double beta1,
+                     double beta2, double eps, double* nlml_hist)
+{
+    return orc_optimize_k(0, X, y, n, d, hyp, trainable, steps, lr, beta1, beta2, eps, nlml_hist);
 }
 
 /* ------------------------------------------------------------------------ */

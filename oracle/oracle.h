@@ -64,6 +64,23 @@ int64_t orc_optimize(const double* X, const double* y, int64_t n, int64_t d, dou
                      const int* trainable, int64_t steps, double lr, double beta1,
                      double beta2, double eps, double* nlml_hist);
 
+/* The same with a choice of kernel: kind 0 = squared exponential (Eq. 2),
+ * 1 / 2 / 3 = Matern of order 1/2, 3/2, 5/2 (nu * m(r), Rasmussen & Williams
+ * Eq. 4.17; the paper's future work, Section 6). */
+void orc_kernel_cross(int kind, const double* A, int64_t na, const double* B, int64_t nb, int64_t d,
+                      double l, double nu, double* out);
+void orc_cov_train_k(int kind, const double* X, int64_t n, int64_t d, const double* hyp, double* K);
+int64_t orc_predict_k(int kind, const double* X, const double* y, int64_t n, int64_t d,
+                      const double* Xs, int64_t m, const double* hyp, int noisy,
+                      double* mean, double* var, double* cov);
+int64_t orc_nlml_k(int kind, const double* X, const double* y, int64_t n, int64_t d,
+                   const double* hyp, double* nlml);
+int64_t orc_nlml_grad_k(int kind, const double* X, const double* y, int64_t n, int64_t d,
+                        const double* hyp, double* nlml, double* grad);
+int64_t orc_optimize_k(int kind, const double* X, const double* y, int64_t n, int64_t d, double* hyp,
+                       const int* trainable, int64_t steps, double lr, double beta1,
+                       double beta2, double eps, double* nlml_hist);
+
 /* 64-d data summary for the learned initialiser (not in the paper). */
 void orc_summary(const double* X, const double* y, int64_t n, int64_t d,
                  const double* omega, double* s);

@@ -33,6 +33,11 @@ MUTANTS = {
     "mlp_relu_mask_dropped": ("d2[k] = h2[k] > 0.0 ? a : 0.0;", "d2[k] = a;"),
     "summary_lag_off_by_one": ("c += (y[i] - ybar) * (y[i + lag] - ybar);",
                                "c += (y[i] - ybar) * (y[i + lag - 1] - ybar);"),
+    "matern32_linear_term_dropped": ("return nu * (1.0 + s) * exp(-s);", "return nu * exp(-s);"),
+    "matern52_dlogl_factor": ("return nu * s * s * (1.0 + s) * exp(-s) / 3.0;",
+                              "return nu * s * s * (1.0 + s) * exp(-s);"),
+    "matern_squared_distance": ("out[i * nb + j] = matern(kind, sqrt(sqdist(A + i * d, B + j * d, d)), l, nu);",
+                                "out[i * nb + j] = matern(kind, sqdist(A + i * d, B + j * d, d), l, nu);"),
     # Adam on the natural scale instead of log theta: every site of the log/exp map replaced
     "optimize_natural_scale": [
         ("double theta[3] = {log(hyp[0]), log(hyp[1]), log(hyp[2])};", "double theta[3] = {hyp[0], hyp[1], hyp[2]};"),

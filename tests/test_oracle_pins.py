@@ -404,3 +404,99 @@ def test_mlp_forward_against_matrix_products_and_backward_against_fd(orc):
         Wm[i] -= h
         fd = (orc.mlp_loss_grad(Wp, S, T)[0] - orc.mlp_loss_grad(Wm, S, T)[0]) / (2 * h)
         assert abs(g[i] - fd) < 1e-7 * max(1.0, abs(fd))
+
+
+# --------------------------------------------------------------------------- Matern kernels
+
+MATERN = {"matern12": 0.5, "matern32": 1.5, "matern52": 2.5}
+
+
+def _matern_bessel(r, l, nu, p):
+    """Matern kernel from its general definition with the modified Bessel function
+    (Rasmussen & Williams Eq. 4.14), independent of the half-integer closed forms."""
+    from scipy.special import gamma, kv
+    z = np.sqrt(2.0 * p) * np.asarray(r, dtype=np.float64) / l
+    out = np.full(z.shape, nu)
+    nz = z > 0
+    out[nz] = nu * 2.0 ** (1.0 - p) / gamma(p) * z[nz] ** p * kv(p, z[nz])
+    return out
+
+
+@pytest.mark.parametrize("kernel", sorted(MATERN))
+def test_matern_against_bessel_definition(orc, kernel):
+    A = dg.random_points(7, 4, seed=11)
+    B = dg.random_points(9, 4, seed=12)
+    l, nu = 0.7, 1.3
+    K = orc.kernel_cross(A, B, l, nu, kernel)
+    r = cdist(A, B)
+    assert max_rel(K, _matern_bessel(r, l, nu, MATERN[kernel])) < 1e-12
+    assert np.allclose(np.diag(orc.kernel_cross(A, A, l, nu, kernel)), nu, rtol=0, atol=0)
+
+
+def test_matern12_is_markov_in_one_dimension(orc):
+    """The order-1/2 Matern kernel in one dimension is the Ornstein-Uhlenbeck
+    covariance: for sorted inputs and no noise its inverse is tridiagonal."""
+    x = np.sort(dg.uniform(21, 0, 40, 0.0, 6.0)).reshape(-1, 1)
+    K = orc.cov_train(x, (0.8, 1.1, 0.0), kernel="matern12")
+    Kinv = orc.chol_inverse(orc.cholesky(K))
+    off = np.abs(np.triu(Kinv, 2))
+    assert off.max() < 1e-9 * np.abs(Kinv).max()
+    assert np.abs(np.diag(Kinv, 1)).min() > 1e-3 * np.abs(Kinv).max()
+
+
+@pytest.mark.parametrize("kernel", sorted(MATERN))
+def test_matern_n2_closed_forms_and_gradient(orc, kernel):
+    l, nu, s2 = 1.3, 0.9, 0.2
+    X = np.array([[0.0, 0.5], [0.75, -0.25]])
+    y = np.array([0.4, -1.1])
+    xs = np.array([[0.25, 0.25]])
+    r = np.sqrt(2 * 0.75 ** 2)
+    a, c = nu + s2, _matern_bessel([r], l, nu, MATERN[kernel])[0]
+    det = a * a - c * c
+    Kinv = np.array([[a, -c], [-c, a]]) / det
+    alpha = Kinv @ y
+    kh = _matern_bessel(np.sqrt([2 * 0.25 ** 2, 2 * 0.5 ** 2]), l, nu, MATERN[kernel])
+    mu, va, _ = orc.predict(X, y, xs, (l, nu, s2), kernel=kernel)
+    assert abs(mu[0] - kh @ alpha) < 1e-13
+    assert abs(va[0] - (nu - kh @ Kinv @ kh)) < 1e-13
+    f = orc.nlml(X, y, (l, nu, s2), kernel=kernel)
+    assert abs(f - (0.5 * y @ alpha + 0.5 * np.log(det) + np.log(2 * np.pi))) < 1e-13
+    # the length-scale derivative of c by a central difference of the Bessel form
+    h = 1e-6
+    dc = (_matern_bessel([r], l * np.exp(h), nu, MATERN[kernel])[0]
+          - _matern_bessel([r], l * np.exp(-h), nu, MATERN[kernel])[0]) / (2 * h)
+    W = Kinv - np.outer(alpha, alpha)
+    g_expect = [0.5 * 2 * W[0, 1] * dc, 0.5 * (W[0, 0] * nu + W[1, 1] * nu + 2 * W[0, 1] * c),
+                0.5 * s2 * (W[0, 0] + W[1, 1])]
+    _, g = orc.nlml_grad(X, y, (l, nu, s2), kernel=kernel)
+    assert max_rel(g, g_expect) < 1e-8
+
+
+@pytest.mark.parametrize("kernel", sorted(MATERN))
+def test_matern_gradient_against_central_differences(orc, kernel):
+    X, y, _, _ = small_set(n=40, d=4, seed=1014)
+    hyp = (0.8, 1.2, 0.07)
+    f, g = orc.nlml_grad(X, y, hyp, kernel=kernel)
+    assert abs(f - orc.nlml(X, y, hyp, kernel=kernel)) == 0.0
+    h = 1e-5
+    th = np.log(hyp)
+    fd = np.empty(3)
+    for p in range(3):
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd[p] = (orc.nlml(X, y, np.exp(tp), kernel=kernel) - orc.nlml(X, y, np.exp(tm), kernel=kernel)) / (2 * h)
+    assert max_rel(g, fd, floor=1e-8 * np.linalg.norm(fd)) < 1e-7
+
+
+@pytest.mark.parametrize("kernel", sorted(MATERN))
+def test_matern_long_length_scale_limit(orc, kernel):
+    X = dg.random_points(30, 3, seed=8)
+    Xs = dg.random_points(5, 3, seed=9)
+    y = dg.uniform(10, 0, 30, -1, 1)
+    nu, s2, n = 0.8, 0.25, 30
+    one = np.ones(n)
+    alpha = (y - nu * one * (one @ y) / (s2 + n * nu)) / s2
+    mu, va, _ = orc.predict(X, y, Xs, (1e9, nu, s2), kernel=kernel)
+    assert max_rel(mu, np.full(5, nu * one @ alpha), 1e-3) < 1e-6
+    assert np.all(np.abs(va - (nu - nu * nu * n / (s2 + n * nu))) < 1e-6)
