@@ -58,6 +58,18 @@ typedef enum {
  * level throughout; no counterpart in the paper. */
 typedef enum { GP_FP64 = 0, GP_MIXED = 1, GP_FP64_OZAKI = 2 } gp_precision;
 
+/* Covariance function.  GP_KERNEL_SE is Eq. 2, nu exp(-r^2 / (2 l^2)); the
+ * Matern kernels (the paper's future work, Section 6; Rasmussen & Williams
+ * Eq. 4.17) are nu m(r) with s = sqrt(2p) r / l for order p:
+ * p = 1/2: exp(-s), p = 3/2: (1 + s) exp(-s), p = 5/2: (1 + s + s^2/3) exp(-s).
+ * All share the hyperparameters (l, nu, sigma^2) and their gradients. */
+typedef enum {
+    GP_KERNEL_SE = 0,
+    GP_KERNEL_MATERN12 = 1,
+    GP_KERNEL_MATERN32 = 2,
+    GP_KERNEL_MATERN52 = 3
+} gp_kernel;
+
 typedef enum {
     GP_SCHED_STREAM = 0,     /* one launch per tile step, stream ordered */
     GP_SCHED_PERSISTENT = 1  /* one persistent launch walking the tile DAG (GP_FP64 only) */
@@ -87,11 +99,13 @@ typedef struct {
                                (see gp_predict_var), 0 returns the mixed-factor variances */
     int dag_timeout_ms;     /* GP_SCHED_PERSISTENT: bound on any single dependency wait of
                                the persistent kernel; expiry ends the call with GP_ERR_TIMEOUT */
+    gp_kernel kernel;       /* covariance function (default GP_KERNEL_SE) */
 } gp_options;
 
 /* Fills defaults: n_tiles 16, FP64, latent variance, refine_tol 1e-14,
  * refine_max_iter 20, Adam (0.9, 0.999, 1e-8), default stream, stream
- * scheduler, variance correction on, DAG wait bound 10000 ms. */
+ * scheduler, variance correction on, DAG wait bound 10000 ms, squared
+ * exponential kernel. */
 void gp_default_options(gp_options* opt);
 
 /* Automatic tile count (the tile-size selection the paper leaves to future
@@ -266,7 +280,8 @@ gp_status gp_info(gp_t h, gp_info_t* out);
  * servers whose device memory belongs to a pool fixed at start-up, plug-ins of
  * hosts that forbid allocation - this computes mean = K_{Z*,Z} alpha (Eq. 3)
  * from trained weights (alpha from gp_get_alpha) without a handle and without
- * any cudaMalloc, cudaFree or allocating library call.
+ * any cudaMalloc, cudaFree or allocating library call.  The kernel is the
+ * squared exponential of Eq. 2.
  *   X (n x d), alpha (n), Xs (m x d) and mean (m): caller-owned DEVICE memory,
  *   row-major float64; lengthscale l and vertical nu as in Eq. 2; cuda_stream
  *   as in gp_options (NULL: legacy default stream).  Stream-ordered, no sync.

@@ -516,6 +516,7 @@ void gp_default_options(gp_options* opt)
     opt->scheduler = GP_SCHED_STREAM;
     opt->var_correction = 1;
     opt->dag_timeout_ms = 10000;
+    opt->kernel = GP_KERNEL_SE;
 }
 
 const char* gp_status_str(gp_status s)
@@ -565,7 +566,8 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     if (!X || !y || n < 1 || d < 1 || d > 1024 || !hyper_ok(hyper) || opt.n_tiles < 0 ||
         (opt.prec != GP_FP64 && opt.prec != GP_MIXED && opt.prec != GP_FP64_OZAKI) ||
         (opt.scheduler != GP_SCHED_STREAM && opt.scheduler != GP_SCHED_PERSISTENT) ||
-        (opt.scheduler == GP_SCHED_PERSISTENT && opt.prec != GP_FP64) || opt.dag_timeout_ms < 0)
+        (opt.scheduler == GP_SCHED_PERSISTENT && opt.prec != GP_FP64) || opt.dag_timeout_ms < 0 ||
+        opt.kernel < GP_KERNEL_SE || opt.kernel > GP_KERNEL_MATERN52)
         return GP_ERR_ARG;
     if (opt.dag_timeout_ms == 0) opt.dag_timeout_ms = 10000;
     if (opt.n_tiles == 0) {
@@ -588,6 +590,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     h->Np = h->T * h->b;
     for (int p = 0; p < 3; ++p) h->trainable[p] = hyper->trainable[p] ? 1 : 0;
     hyper_to_dev(hyper, &h->h_hyp);
+    h->h_hyp.kernel = opt.kernel;
 
     gp_status s = GP_OK;
     const int64_t tiles = ntri(h) * h->b * h->b;
@@ -833,6 +836,7 @@ gp_status gp_set_hyper(gp_t h, const gp_hyper* hyper)
 {
     if (!h || !hyper_ok(hyper)) return GP_ERR_ARG;
     hyper_to_dev(hyper, &h->h_hyp);
+    h->h_hyp.kernel = h->opt.kernel;
     for (int p = 0; p < 3; ++p) h->trainable[p] = hyper->trainable[p] ? 1 : 0;
     gp_status s = cuda_status(h, cudaMemcpyAsync(h->hyp, &h->h_hyp, sizeof(GpHyperDev), cudaMemcpyHostToDevice, h->st));
     if (s == GP_OK) s = sync(h);

@@ -17,6 +17,7 @@ struct GpHyperDev {
     double l, nu, s2;         // natural scale (Eq. 2)
     double inv2l2;            // 1 / (2 l^2)
     double log_theta[3];      // (log l, log nu, log sigma^2)
+    int kernel;               // gp_kernel (fixed per handle)
 };
 
 struct GpAdamDev {

@@ -20,7 +20,8 @@
 //    running sums in registers;
 //  - the epilogue forms r^2 = |zhat_i|^2 + |zhat_j|^2 - 2 zhat_i . zhat_j
 //    (clamped at 0, exactly 0 on the diagonal of K), the kernel value
-//    nu exp(-r^2 / (2 l^2)) in FP64 and writes the output of its mode.
+//    (Eq. 2 or a Matern kernel, kfun.cuh) in FP64 and writes the output of
+//    its mode.
 //
 // The rounding of z to 42 bits moves r^2 by about 2^-42 |z| |z_i - z_j| and
 // the dropped digit pairs by about d 2^-56 mu_i mu_j: both far below the FP64
@@ -41,6 +42,7 @@
 #include <mutex>
 
 #include "gp_internal.cuh"
+#include "kfun.cuh"
 #include "se_common.cuh"
 #include "tc_common.cuh"
 
@@ -280,7 +282,7 @@ __global__ __launch_bounds__(ZD_THREADS, 1) void k_dist_tc(const __grid_constant
             }
             tc::tmem_st_wait();
         }
-        const double nu = op.hyp->nu, s2 = op.hyp->s2, c2 = op.hyp->inv2l2;
+        const double nu = op.hyp->nu, s2 = op.hyp->s2;
         const double nanv = __longlong_as_double(0x7ff8000000000000ll);
         const int64_t gi = r0 + row;
         const double mi = op.muA[gi], ni = op.nA[gi];
@@ -297,13 +299,13 @@ __global__ __launch_bounds__(ZD_THREADS, 1) void k_dist_tc(const __grid_constant
                 const double r2 = fmax(ni + op.nB[gj] - 2.0 * G, 0.0);
                 double kv;
                 if (op.mode == ZD_TRAIN) {
-                    if (gi < op.na && gj < op.na) kv = gi == gj ? nu + s2 : nu * exp(-r2 * c2);
+                    if (gi < op.na && gj < op.na) kv = gi == gj ? nu + s2 : kval(r2, op.hyp);
                     else kv = gi == gj ? 1.0 : 0.0;
                 } else if (op.mode == ZD_CROSS) {
-                    kv = (gi < op.na && gj < op.nb) ? nu * exp(-r2 * c2) : 0.0;
+                    kv = (gi < op.na && gj < op.nb) ? kval(r2, op.hyp) : 0.0;
                     if (gj < op.nb) msum = fma(kv, op.alpha[gj], msum);
                 } else {
-                    kv = gi == gj ? nu + (op.noisy ? s2 : 0.0) : nu * exp(-r2 * c2);
+                    kv = gi == gj ? nu + (op.noisy ? s2 : 0.0) : kval(r2, op.hyp);
                 }
                 v[e] = ok ? kv : nanv;
             }

@@ -11,6 +11,7 @@
 #include "dgemm_block.cuh"
 #include "gp_internal.cuh"
 #include "se_common.cuh"
+#include "kfun.cuh"
 
 namespace gpk {
 
@@ -64,7 +65,7 @@ __global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, float* o
     }
     double r2[4][4];
     dist_block(r2, Pp, r0, np, Qp, c0, nq, d, sm);
-    const double nu = hyp->nu, s2 = hyp->s2, c2 = hyp->inv2l2;
+    const double s2 = hyp->s2;
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -74,13 +75,13 @@ __global__ __launch_bounds__(NT) void k_se_block(int mode, double* out, float* o
             int64_t gi = r0 + rr, gj = c0 + cc;
             double v;
             if (mode == SE_TRAIN) {
-                if (gi < n && gj < n) v = nu * exp(-r2[a][c] * c2) + (gi == gj ? s2 : 0.0);
+                if (gi < n && gj < n) v = kval(r2[a][c], hyp) + (gi == gj ? s2 : 0.0);
                 else v = (gi == gj) ? 1.0 : 0.0;
             } else if (mode == SE_CROSS) {
-                v = (gi < n && gj < m) ? nu * exp(-r2[a][c] * c2) : 0.0;
+                v = (gi < n && gj < m) ? kval(r2[a][c], hyp) : 0.0;
             } else {
                 if (gi >= m || gj >= m) continue;
-                v = nu * exp(-r2[a][c] * c2) + ((noisy && gi == gj) ? s2 : 0.0);
+                v = kval(r2[a][c], hyp) + ((noisy && gi == gj) ? s2 : 0.0);
             }
             dst[(int64_t)rr * ld + cc] = v;
             if (dst32) dst32[(int64_t)rr * ld + cc] = (float)v;
@@ -695,7 +696,6 @@ __global__ __launch_bounds__(NT) void k_adjoint(const KT* Kinv, const double* al
         const int64_t r0 = i * b + (int64_t)rb * TB, c0 = j * b + (int64_t)cb * TB;
         double r2[4][4];
         dist_block(r2, X, r0, n, X, c0, n, d, sm);
-        const double nu = hyp->nu, c2 = hyp->inv2l2;
         const KT* tile = Kinv + tri_index(i, j) * b * b + (int64_t)rb * TB * b + cb * TB;
         const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
@@ -706,9 +706,9 @@ __global__ __launch_bounds__(NT) void k_adjoint(const KT* Kinv, const double* al
                 int64_t gi = r0 + rr, gj = c0 + cc;
                 if (gi >= n || gj >= n || gj > gi) continue;
                 double w = (double)tile[(int64_t)rr * b + cc] - alpha[gi] * alpha[gj];
-                double kf = nu * exp(-r2[a][c] * c2);
+                double kf = kval(r2[a][c], hyp);
                 double wt = (gi == gj) ? 1.0 : 2.0;
-                s_l = fma(wt * w * kf, r2[a][c], s_l);
+                s_l = fma(wt * w, kdl_term(r2[a][c], kf, hyp), s_l);
                 s_nu = fma(wt * w, kf, s_nu);
                 if (gi == gj) s_s2 += w;
             }
@@ -791,6 +791,8 @@ __global__ __launch_bounds__(NT) void k_adjoint_k(const float* Kinv, const doubl
     float s_l = 0.f, s_nu = 0.f, s_s2 = 0.f;
     if (live) {
         const double s2 = hyp->s2;
+        const int kind = hyp->kernel;
+        const float lf = (float)hyp->l;
         const int64_t off = tri_index(i, j) * b * b + (int64_t)rb * TB * b + cb * TB;
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -803,7 +805,7 @@ __global__ __launch_bounds__(NT) void k_adjoint_k(const float* Kinv, const doubl
                 const float w = __ldcs(Kinv + e) - sa[0][rr] * sa[1][cc];
                 const float kf = (float)(gi == gj ? __ldcs(K64 + e) - s2 : __ldcs(K64 + e));
                 const float wt = (gi == gj) ? 1.f : 2.f;
-                s_l = fmaf(wt * w * kf, r2[a][c], s_l);
+                s_l = fmaf(wt * w, kdl_term_f(r2[a][c], kf, kind, lf), s_l);
                 s_nu = fmaf(wt * w, kf, s_nu);
                 if (gi == gj) s_s2 += w;
             }
@@ -823,7 +825,7 @@ __global__ __launch_bounds__(NT) void k_adjoint_k(const float* Kinv, const doubl
     }
 }
 
-// grad = 1/2 (sum_l / l^2, sum_nu, sigma^2 sum_s2), deterministic single-CTA reduction.
+// grad = 1/2 (sum_l kdl_scale, sum_nu, sigma^2 sum_s2), deterministic single-CTA reduction.
 __global__ void k_grad_finish(const double* gpart, int64_t nblk, const GpHyperDev* hyp, double* scal)
 {
     __shared__ double red[3][NT];
@@ -838,7 +840,7 @@ __global__ void k_grad_finish(const double* gpart, int64_t nblk, const GpHyperDe
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        scal[1] = 0.5 * red[0][0] / (hyp->l * hyp->l);
+        scal[1] = 0.5 * red[0][0] * kdl_scale(hyp);
         scal[2] = 0.5 * red[1][0];
         scal[3] = 0.5 * hyp->s2 * red[2][0];
     }

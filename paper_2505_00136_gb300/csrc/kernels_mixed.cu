@@ -29,6 +29,7 @@
 #include "split_bf16.cuh"
 #include "gp_internal.cuh"
 #include "se_common.cuh"
+#include "kfun.cuh"
 
 namespace gpk {
 
@@ -705,7 +706,6 @@ __global__ __launch_bounds__(NTH) void k_cross_mixed(const double* Xs, int64_t m
     const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
     double r2[4][4];
     dist_block(r2, Xs, m0, m, X, n0, n, d, sm);
-    const double nu = hyp->nu, c2 = hyp->inv2l2;
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -714,7 +714,7 @@ __global__ __launch_bounds__(NTH) void k_cross_mixed(const double* Xs, int64_t m
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int64_t gn = n0 + tx + 16 * c;
-            double kv = (gm < m && gn < n) ? nu * exp(-r2[a][c] * c2) : 0.0;
+            double kv = (gm < m && gn < n) ? kval(r2[a][c], hyp) : 0.0;
             R32[gm * ldr + gn] = (float)kv;
             if (R64) R64[gm * ldr + gn] = kv;
             if (gn < n) s = fma(kv, alpha[gn], s);

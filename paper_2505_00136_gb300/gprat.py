@@ -26,6 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 GP_OK, GP_ERR_ARG, GP_ERR_NOT_PD, GP_ERR_CUDA, GP_ERR_OOM, GP_ERR_TIMEOUT, GP_ERR_STATE = range(7)
 GP_FP64, GP_MIXED, GP_FP64_OZAKI = 0, 1, 2
 GP_SCHED_STREAM, GP_SCHED_PERSISTENT = 0, 1
+KERNELS = {"se": 0, "matern12": 1, "matern32": 2, "matern52": 3}   # gp_kernel
 GP_MLP_NPARAM = 83203
 GP_MLP_MODEL_FLOATS = GP_MLP_NPARAM + 128
 GP_LEARNED_INIT_SCRATCH = 72
@@ -44,7 +45,7 @@ class gp_options(ctypes.Structure):
                 ("adam_beta1", ctypes.c_double), ("adam_beta2", ctypes.c_double),
                 ("adam_eps", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("scheduler", ctypes.c_int), ("var_correction", ctypes.c_int),
-                ("dag_timeout_ms", ctypes.c_int)]
+                ("dag_timeout_ms", ctypes.c_int), ("kernel", ctypes.c_int)]
 
 
 class gp_state(ctypes.Structure):
@@ -169,7 +170,7 @@ class GP:
 
     def __init__(self, X, y, hyper=(1.0, 1.0, 0.1), trainable=(1, 1, 1), n_tiles=16,
                  precision="fp64", noisy_test_var=False, stream=None, scheduler="stream",
-                 refine_tol=None, refine_max_iter=None, var_correction=True, dag_timeout_ms=None):
+                 refine_tol=None, refine_max_iter=None, var_correction=True, dag_timeout_ms=None, kernel="se"):
         if not _is_torch(X):
             X = np.ascontiguousarray(X, dtype=np.float64)
             y = np.ascontiguousarray(y, dtype=np.float64)
@@ -187,6 +188,7 @@ class GP:
         opt.var_correction = int(bool(var_correction))
         if dag_timeout_ms is not None:
             opt.dag_timeout_ms = int(dag_timeout_ms)
+        opt.kernel = KERNELS[kernel]
         if stream is None and self._torch_dev is not None:
             import torch
             stream = torch.cuda.current_stream(self._torch_dev).cuda_stream

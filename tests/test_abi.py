@@ -87,3 +87,19 @@ def test_auto_tiles_gives_tiles_of_256(lib):
         t = g.auto_tiles(n)
         b = -(-n // t)                      # tile edge gp_create derives before rounding up
         assert b <= 256 and (t == 1 or -(-n // (t - 1)) > 256)
+
+
+def test_kernel_and_precision_options_are_validated(lib):
+    """An unknown kernel or precision is refused by gp_create before any CUDA call."""
+    from paper_2505_00136_gb300 import gprat
+    X = np.zeros((64, 2))
+    y = np.zeros(64)
+    hp = gprat.gp_hyper(1.0, 1.0, 0.1, (ctypes.c_int * 3)(1, 1, 1))
+    for field, bad in (("kernel", 7), ("kernel", -1), ("prec", 3)):
+        opt = gprat.default_options()
+        assert opt.kernel == gprat.KERNELS["se"]
+        setattr(opt, field, bad)
+        h = ctypes.c_void_p()
+        st = gprat.gp_create(X.ctypes.data, y.ctypes.data, 64, 2, ctypes.byref(hp), ctypes.byref(opt),
+                             ctypes.byref(h))
+        assert st == gprat.GP_ERR_ARG and not h.value
