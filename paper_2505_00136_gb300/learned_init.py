@@ -38,7 +38,7 @@ def corpus(first_seed: int, count: int, n: int, d: int):
     return torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), prm
 
 
-def optimise_runs(X, y, steps, lr=0.1, init=None, n_tiles=2, workers=8, precision="fp64"):
+def optimise_runs(X, y, steps, lr=0.1, init=None, n_tiles=4, workers=8, precision="fp64"):
     """Adam runs (one GP handle per system, several CUDA streams in flight).
 
     Returns (final log theta (B,3) numpy, NLML histories (B, steps) numpy).
@@ -131,13 +131,21 @@ def steps_to_reach(hist, target, rtol):
     return int(idx + 1) if ok[idx] else len(hist) + 1
 
 
-def run(n_train_sys=256, n_eval_sys=32, n=256, n_eval=256, d=32, label_steps=300, eval_steps=300,
-        epochs=600, lr=1e-3, rtol=1e-6, first_seed=20000, precision="fp64", workers=8):
-    """Corpus -> labels -> training -> evaluation; returns a dict of results."""
+def run(n_train_sys=256, n_eval_sys=32, n=256, n_eval=256, d=32, label_steps=600, eval_steps=2000,
+        epochs=600, lr=1e-3, rtol=1e-6, first_seed=20000, precision="fp64", workers=8, n_tiles=4):
+    """Corpus -> labels -> training -> evaluation; returns a dict of results.
+
+    The judge of convergence is the default run's own optimum: NLML* = the
+    minimum over eval_steps Adam steps (lr 0.1) from the default start.  Steps
+    to converge = the first step whose NLML is within rtol of NLML* (or below
+    it), for the default and the learned start alike; a learned run that never
+    gets there counts eval_steps + 1 (reported as capped).  Whether the default
+    run has itself settled is reported as the relative NLML change over its
+    last 100 steps."""
     t0 = time.perf_counter()
     omega = torch.from_numpy(dg.rff_frequencies()).cuda()
     Xtr, ytr, _ = corpus(first_seed, n_train_sys, n, d)
-    labels, _ = optimise_runs(Xtr, ytr, label_steps, precision=precision, workers=workers)
+    labels, _ = optimise_runs(Xtr, ytr, label_steps, precision=precision, workers=workers, n_tiles=n_tiles)
     t_label = time.perf_counter() - t0
     S = summaries(Xtr, ytr, omega)
     t1 = time.perf_counter()
@@ -145,14 +153,18 @@ def run(n_train_sys=256, n_eval_sys=32, n=256, n_eval=256, d=32, label_steps=300
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     Xev, yev, _ = corpus(first_seed + n_train_sys, n_eval_sys, n_eval, d)
-    _, h_def = optimise_runs(Xev, yev, eval_steps, workers=workers)
+    _, h_def = optimise_runs(Xev, yev, eval_steps, workers=workers, n_tiles=n_tiles)
     init = predict_init(model, Xev, yev, omega)
-    _, h_lrn = optimise_runs(Xev, yev, eval_steps, init=init, workers=workers)
-    best = h_def.min(axis=1)      # the default initialisation's optimum over its run
+    _, h_lrn = optimise_runs(Xev, yev, eval_steps, init=init, workers=workers, n_tiles=n_tiles)
+    best = h_def.min(axis=1)      # NLML*: the default initialisation's optimum over its run
     s_def = np.array([steps_to_reach(h_def[b], best[b], rtol) for b in range(n_eval_sys)])
     s_lrn = np.array([steps_to_reach(h_lrn[b], best[b], rtol) for b in range(n_eval_sys)])
+    tail = min(100, eval_steps - 1)
+    settle = np.abs(h_def[:, -1] - h_def[:, -1 - tail]) / np.abs(h_def[:, -1])
     return {"median_steps_default": float(np.median(s_def)), "median_steps_learned": float(np.median(s_lrn)),
             "steps_default": s_def.tolist(), "steps_learned": s_lrn.tolist(),
+            "cap": eval_steps, "learned_capped": int(np.sum(s_lrn > eval_steps)),
+            "default_last100_rel_change_median": float(np.median(settle)),
             "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
             "label_s": t_label, "train_s": t_train, "total_s": time.perf_counter() - t0,
             "corpus": {"train_systems": n_train_sys, "eval_systems": n_eval_sys, "n_train": n,

@@ -99,13 +99,15 @@ def test_weight_adam_matches_torch_adam(env):
 
 
 def test_learned_initialiser_cuts_adam_steps(env):
-    """Small corpus (256 systems, n=256, 32 lagged inputs, labels = log theta
-    after 300 Adam steps from the default): the trained network's
-    initialisation reaches the default run's optimum (within 1e-6 relative) in
-    fewer Adam steps, in the median over 32 held-out systems."""
+    """Small corpus (192 systems, n=256, 32 lagged inputs, labels = log theta
+    after 600 Adam steps from the default): the trained network's
+    initialisation reaches the default run's optimum over 2000 steps (within
+    1e-6 relative) in fewer Adam steps, in the median over 24 held-out
+    systems, and the default runs have settled by their end."""
     torch, gprat, li = env
-    res = li.run(n_train_sys=256, n_eval_sys=32, n=256, n_eval=256, d=32, label_steps=300, eval_steps=300,
+    res = li.run(n_train_sys=192, n_eval_sys=24, n=256, n_eval=256, d=32, label_steps=600, eval_steps=2000,
                  epochs=600)
     print("learned init", {k: v for k, v in res.items() if not k.startswith("steps_")})
     assert res["loss_last"] < 0.5 * res["loss_first"]
+    assert res["median_steps_default"] < res["cap"]
     assert res["median_steps_learned"] < res["median_steps_default"]
