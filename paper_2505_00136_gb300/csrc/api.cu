@@ -545,7 +545,7 @@ void gp_destroy(gp_t h)
                     h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
-                    h->dag_upd, h->dag_fin, h->OGP, h->og_mu, h->OGL, h->ogl_mu, h->OGT, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->ogv_mu,
+                    h->dag_upd, h->dag_fin, h->OGP, h->OGS, h->og_mu, h->OGL, h->ogl_mu, h->OGT, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->ogv_mu,
                     h->OGC, h->ogc_mu, h->ogc_bits, h->ZXS, h->zx_mu, h->zx_nrm, h->ZSS, h->zs_mu, h->zs_nrm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -615,6 +615,7 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     if (opt.prec == GP_FP64_OZAKI) {   // digit slices of one panel and of one diagonal-tile inverse
         if (h->T > 1) {
             TRY(dev_alloc(h, &h->OGP, (int64_t)gpk::GP_OG_SLICES * (h->Np - h->b) * h->b));
+            TRY(dev_alloc(h, &h->OGS, (int64_t)gpk::GP_OG_SLICES * (h->Np - h->b) * gpk::GP_OG_SP * h->b));
             TRY(dev_alloc(h, &h->og_mu, h->Np - h->b));
         }
         TRY(dev_alloc(h, &h->OGL, (int64_t)gpk::GP_OG_SLICES * h->b * h->b));

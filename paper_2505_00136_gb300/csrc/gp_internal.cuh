@@ -99,7 +99,7 @@ struct gp_handle {
     bool tc_dist;
     bool host_fail;           // a launch could not be set up on the host; reported by the next check
     // GP_FP64_OZAKI: digit slices of the current panel, 7 x (Np - b) x b, and their row scales
-    __nv_bfloat16* OGP;
+    __nv_bfloat16 *OGP, *OGS;   // OGS: slices of one super-panel, 7 x (Np - b) x (GP_OG_SP b)
     double* og_mu;
     // GP_FP64_OZAKI gradient: column slices of one row block of L^{-1} (7 x Np x b), of all
     // of L^{-1} (7 x Np x Np), their column scales and the column maxima
@@ -165,7 +165,9 @@ void assemble_train(gp_t h);                                   // K tiles into h
 void assemble_cross(gp_t h, int64_t m, int64_t ldm);           // B = K_{Z*,Z}^T (Np x ldm)
 void assemble_test_prior(gp_t h, int64_t m, double* out);      // out = K_{Z*,Z*} (+ noise), m x m
 bool factor_fp64(gp_t h);                                      // tiled Cholesky in place (false: host set-up failed)
-bool og_chol_update(gp_t h, int64_t k);                        // GP_FP64_OZAKI trailing update of step k
+bool og_chol_update_cols(gp_t h, int64_t k, int64_t e);         // GP_FP64_OZAKI: columns k+1..e-1 by column k
+bool og_chol_update_sp(gp_t h, int64_t K0, int64_t e);          // GP_FP64_OZAKI: trailing update by a super-panel
+constexpr int GP_OG_SP = 4;                                     // GP_FP64_OZAKI super-panel width (tile columns)
 bool og_trtri_accum(gp_t h, int64_t t);                        // GP_FP64_OZAKI inverse: S_ij += L_it X_tj
 bool og_lauum(gp_t h);                                         // GP_FP64_OZAKI K^{-1} = X^T X
 bool og_vsolve_update(gp_t h, int64_t j, int64_t ldm);          // GP_FP64_OZAKI V solve: B_i -= L_ij V_j

@@ -962,9 +962,30 @@ void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, do
     GPK_LAUNCH(h, GP_PH_POTRF, k_potrf_diag, 1, NT, POTRF_SMEM, A, X, b, row0, logdet_slot, h->info);
 }
 
+// GP_FP64_OZAKI: right-looking in super-panels of GP_OG_SP tile columns (as
+// the mixed path): each column of a super-panel is factored, solved and
+// applied to the super-panel's later columns; one update with a k range of
+// the whole super-panel then reaches the trailing triangle, so each trailing
+// tile is read and written once per super-panel instead of once per column.
+static bool factor_fp64_ozaki(gp_t h)
+{
+    const int64_t T = h->T, b = h->b;
+    for (int64_t K0 = 0; K0 < T; K0 += GP_OG_SP) {
+        const int64_t e = K0 + GP_OG_SP < T ? K0 + GP_OG_SP : T;
+        for (int64_t k = K0; k < e; ++k) {
+            potrf_diag_launch(h, h->L + tri_index(k, k) * b * b, h->Linv + k * b * b, b, k * b,
+                              h->logdet_part + k);
+            if (k + 1 < T && (!og_panel(h, k) || !og_chol_update_cols(h, k, e))) return false;
+        }
+        if (e < T && !og_chol_update_sp(h, K0, e)) return false;
+    }
+    return true;
+}
+
 bool factor_fp64(gp_t h)
 {
     ensure_attrs();
+    if (h->opt.prec == GP_FP64_OZAKI) return factor_fp64_ozaki(h);
     const int64_t T = h->T, b = h->b;
     const int P = (int)(b / TB);
     for (int64_t k = 0; k < T; ++k) {
@@ -972,9 +993,7 @@ bool factor_fp64(gp_t h)
                           h->logdet_part + k);
         if (k + 1 < T) {
             const int64_t tt = T - k - 1;
-            if (h->opt.prec == GP_FP64_OZAKI) {   // exact digit products on the tensor cores
-                if (!og_panel(h, k) || !og_chol_update(h, k)) return false;
-            } else {
+            {
                 GPK_LAUNCH(h, GP_PH_TRSM, k_panel, dim3((unsigned)P, (unsigned)(T - k - 1)), NT,
                            DG_SMEM_BYTES, h->L, (const double*)h->Linv, b, k, (const unsigned long long*)h->info);
                 GPK_LAUNCH(h, GP_PH_UPDATE, k_update, dim3((unsigned)(tt * (tt + 1) / 2), (unsigned)(P * P)),

@@ -267,12 +267,20 @@ __global__ __launch_bounds__(OG_THREADS, 1) void k_ozgemm(const __grid_constant_
             }
             tc::tmem_st_wait();
         }
-        // the TMEM loads are warp-collective: every lane takes part, only live rows store
+        // The TMEM loads are warp-collective: every lane takes part, only live rows store.
+        // sign mu_i mu_j is a power of two: when it is a normal FP32 number the scaling of hi and
+        // lo is exact in FP32 and the FP64 work per element is two conversions and two adds
+        // (the destination's loads are issued before the TMEM loads); otherwise FP64 throughout.
         const bool live = row < un.rows;
+        const int ea = live ? pow2_exp(un.muA[row]) : 0;
         const double mi = live ? un.muA[row] : 0.0;
         double* drow = un.dst + (int64_t)row * un.ld + cq;
 #pragma unroll 1
         for (int q = 0; q < 4; ++q) {
+            double base[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                base[e] = (live && !un.overwrite && cq + 16 * q + e < un.cols) ? drow[16 * q + e] : 0.0;
             float h[16], lw[16];
             if (ok) tc::tmem_ld16x2(tl + 16 * q, tl + 128 + 16 * q, h, lw);
             if (!live) continue;
@@ -280,9 +288,22 @@ __global__ __launch_bounds__(OG_THREADS, 1) void k_ozgemm(const __grid_constant_
             for (int e = 0; e < 16; ++e) {
                 const int col = cq + 16 * q + e;
                 if (col >= un.cols) continue;
-                const double v = ok ? ((double)h[e] + (double)lw[e]) * (mi * un.muB[col]) : 0.0;
-                const double base = un.overwrite ? 0.0 : drow[16 * q + e];
-                drow[16 * q + e] = ok ? fma(un.sign, v, base) : __longlong_as_double(0x7ff8000000000000ll);
+                double out;
+                if (!ok) {
+                    out = __longlong_as_double(0x7ff8000000000000ll);
+                } else {
+                    const double mj = un.muB[col];
+                    const int ex = ea + pow2_exp(mj);
+                    double v;
+                    if (ex >= -126 && ex <= 127) {
+                        const float sf = __int_as_float((un.sign < 0.0 ? (int)0x80000000 : 0) | ((127 + ex) << 23));
+                        v = (double)(h[e] * sf) + (double)(lw[e] * sf);
+                    } else {
+                        v = ((double)h[e] + (double)lw[e]) * (un.sign * mi * mj);
+                    }
+                    out = base[e] + v;
+                }
+                drow[16 * q + e] = out;
             }
         }
     }
@@ -462,6 +483,39 @@ __global__ __launch_bounds__(256) void k_colslices_dense(const double* src, int6
         }
 }
 
+// As k_rowslices with the row given element by element (src(r, c)).
+template <class Src>
+__global__ void k_rowslices_v(Src src, int64_t rows, int64_t n, __nv_bfloat16* OS, int64_t ps, double* mu)
+{
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    double mx = 0.0;
+    for (int64_t c = lane; c < n; c += 32) mx = fmax(mx, fabs(src(r, c)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double m = mx > 0.0 ? pow2_ceil(mx) : 1.0;
+    const int sc = GP_OZ_BITS * OG_S - pow2_exp(m);
+    for (int64_t c = lane; c < n; c += 32) {
+        __nv_bfloat16 d[OG_S];
+        oz_digits<OG_S>(rint_scaled(src(r, c), sc), d);
+#pragma unroll
+        for (int s = 0; s < OG_S; ++s) OS[s * ps + r * n + c] = d[s];
+    }
+    if (lane == 0) mu[r] = m;
+}
+
+// Rows of the tiles r0t, r0t + 1, .. over the tile columns K0 .. K0 + w - 1
+// (a super-panel): element (r, c) is row r % b, column c % b of tile
+// (r0t + r / b, K0 + c / b).
+struct SuperPanelRows {
+    const double* L;
+    int64_t b, K0, r0t;
+    __device__ double operator()(int64_t r, int64_t c) const
+    {
+        return L[tri_index(r0t + r / b, K0 + c / b) * b * b + (r % b) * b + (c % b)];
+    }
+};
+
 // Row r of the panel below the diagonal tile k: row r % b of tile (k + 1 + r / b, k).
 struct PanelRows {
     const double* L;
@@ -499,28 +553,40 @@ __global__ void k_vparts(const double* V, const double* beta, double* part, int6
 }
 
 // ---------------------------------------------------------------- operations
-// Cholesky trailing update of step k: A_ij -= L_ik L_jk^T for k < j <= i,
-// A and B both the digit slices of the panel (rows of tiles k+1 .. T-1).
+// Cholesky updates A_ij -= sum_k L_ik L_jk^T over the k range of one slice set:
+// rows of the tiles r0t .. T-1 of one panel column (width b) or of one
+// super-panel (SP tile columns, width SP b); A and B are both those slices.
+// tri: every tile i >= j >= j0 (tt (tt+1) / 2 of them, tt = T - j0); else the
+// columns j0 .. j0 + ncol - 1 with i >= j (a rectangle with its upper part skipped).
 struct OgChol {
     double* L;
     const double* mu;
     int64_t b;
-    int k, tt, P;
+    int T, j0, ncol, r0t, width, P;
+    bool tri;
     int a_ps, b_ps;
     const unsigned long long* info;
     __device__ bool unit(int u, OgUnit& o) const
     {
         if (failed(info)) return false;
         const int per = P * P;
-        int64_t ii, jj;
-        tri_decode(u / per, ii, jj);
+        int64_t i, j;
+        if (tri) {
+            tri_decode(u / per, i, j);
+            i += j0;
+            j += j0;
+        } else {
+            const int q = u / per;
+            j = j0 + q % ncol;
+            i = j0 + q / ncol;
+            if (i < j) return false;
+        }
         const int rb = (u % per) / P, cb = (u % per) % P;
-        if (ii == jj && cb > rb) return false;
-        const int64_t i = k + 1 + ii, j = k + 1 + jj;
-        o.a_row = (int)(ii * b + rb * 128);
-        o.b_row = (int)(jj * b + cb * 128);
+        if (i == j && cb > rb) return false;
+        o.a_row = (int)((i - r0t) * b + rb * 128);
+        o.b_row = (int)((j - r0t) * b + cb * 128);
         o.k0 = 0;
-        o.k1 = (int)b;
+        o.k1 = width;
         o.dst = L + tri_index(i, j) * b * b + (int64_t)rb * 128 * b + cb * 128;
         o.ld = b;
         o.muA = mu + o.a_row;
@@ -760,12 +826,12 @@ bool og_launch(gp_t h, int phase, const CUtensorMap& mA, const CUtensorMap& mB, 
 
 }  // namespace
 
-// Step k of the FP64 factorisation's trailing update on the tensor cores:
-// slices the panel (tiles (k+1 .. T-1, k)), then A_ij -= L_ik L_jk^T.
-bool og_chol_update(gp_t h, int64_t k)
+// Update of the super-panel's own later columns by its column k: A_ij -= L_ik
+// L_jk^T for k < j < e, i >= j, from the panel slices of column k.
+bool og_chol_update_cols(gp_t h, int64_t k, int64_t e)
 {
     const int64_t T = h->T, b = h->b, tt = T - k - 1;
-    if (tt <= 0) return true;
+    if (tt <= 0 || e <= k + 1) return true;
     const int64_t rows = tt * b;
     GPK_LAUNCH(h, GP_PH_UPDATE, k_rowslices<PanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
                PanelRows{h->L, b, k}, rows, b, h->OGP, rows * b, h->og_mu);
@@ -775,9 +841,40 @@ bool og_chol_update(gp_t h, int64_t k)
     op.L = h->L;
     op.mu = h->og_mu;
     op.b = b;
-    op.k = (int)k;
-    op.tt = (int)tt;
+    op.T = (int)T;
+    op.j0 = (int)(k + 1);
+    op.ncol = (int)(e - k - 1);
+    op.r0t = (int)(k + 1);
+    op.width = (int)b;
     op.P = (int)(b / 128);
+    op.tri = false;
+    op.a_ps = op.b_ps = (int)rows;
+    op.info = h->info;
+    return og_launch(h, GP_PH_UPDATE, mP, mP, op, (T - k - 1) * op.ncol * op.P * op.P);
+}
+
+// Trailing update by a whole super-panel (tile columns K0 .. e-1): A_ij -=
+// sum_{k in K0..e-1} L_ik L_jk^T for i >= j >= e, one k range of (e - K0) b.
+bool og_chol_update_sp(gp_t h, int64_t K0, int64_t e)
+{
+    const int64_t T = h->T, b = h->b, tt = T - e;
+    if (tt <= 0) return true;
+    const int64_t rows = tt * b, width = (e - K0) * b;
+    GPK_LAUNCH(h, GP_PH_UPDATE, k_rowslices_v<SuperPanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
+               SuperPanelRows{h->L, b, K0, e}, rows, width, h->OGS, rows * width, h->og_mu);
+    CUtensorMap mP;
+    if (!og_map(&mP, h->OGS, rows, width)) return false;
+    OgChol op;
+    op.L = h->L;
+    op.mu = h->og_mu;
+    op.b = b;
+    op.T = (int)T;
+    op.j0 = (int)e;
+    op.ncol = (int)tt;
+    op.r0t = (int)e;
+    op.width = (int)width;
+    op.P = (int)(b / 128);
+    op.tri = true;
     op.a_ps = op.b_ps = (int)rows;
     op.info = h->info;
     return og_launch(h, GP_PH_UPDATE, mP, mP, op, tt * (tt + 1) / 2 * op.P * op.P);
