@@ -113,6 +113,7 @@ gp_status ensure_grad_buffers(gp_t h)
         const int64_t Np = h->Np;
         if ((s = dev_alloc(h, &h->OGT, (int64_t)gpk::GP_OG_SLICES * Np * h->b)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->ogt_mu, Np)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->OGTS, (int64_t)gpk::GP_OG_SLICES * Np * gpk::GP_OG_SP * h->b)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->OGX, (int64_t)gpk::GP_OG_SLICES * Np * Np)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->ogx_mu, Np)) != GP_OK) return s;
         if ((s = dev_alloc(h, &h->ogx_bits, Np)) != GP_OK) return s;
@@ -188,6 +189,7 @@ gp_status ensure_predict_space(gp_t h, int64_t m)
     const int64_t old = h->m_cap;
     const int64_t old_part = old ? (2 * (h->Np / TB) > 64 ? 2 * (h->Np / TB) : 64) * old : 0;
     dev_free(h, &h->OGV, (int64_t)gpk::GP_OG_SLICES * old * h->b);
+    dev_free(h, &h->OGVS, (int64_t)gpk::GP_OG_SLICES * old * gpk::GP_OG_SP * h->b);
     dev_free(h, &h->ogv_mu, old);
     dev_free(h, &h->Xs, old * h->d);
     dev_free(h, &h->B, old * h->Np);
@@ -206,6 +208,8 @@ gp_status ensure_predict_space(gp_t h, int64_t m)
     if ((s = dev_alloc(h, &h->outv, ldm)) != GP_OK) return s;
     if (emu) {
         if ((s = dev_alloc(h, &h->OGV, (int64_t)gpk::GP_OG_SLICES * ldm * h->b)) != GP_OK) return s;
+        if ((s = dev_alloc(h, &h->OGVS, (int64_t)gpk::GP_OG_SLICES * ldm * gpk::GP_OG_SP * h->b)) != GP_OK)
+            return s;
         if ((s = dev_alloc(h, &h->ogv_mu, ldm)) != GP_OK) return s;
     }
     h->m_cap = ldm;
@@ -545,7 +549,7 @@ void gp_destroy(gp_t h)
                     h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
-                    h->dag_upd, h->dag_fin, h->OGP, h->OGS, h->og_mu, h->OGL, h->ogl_mu, h->OGT, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->ogv_mu,
+                    h->dag_upd, h->dag_fin, h->OGP, h->OGS, h->og_mu, h->OGL, h->ogl_mu, h->OGT, h->OGTS, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->OGVS, h->ogv_mu,
                     h->OGC, h->ogc_mu, h->ogc_bits, h->ZXS, h->zx_mu, h->zx_nrm, h->ZSS, h->zs_mu, h->zs_nrm};
     for (void* p : ptrs)
         if (p) cudaFree(p);

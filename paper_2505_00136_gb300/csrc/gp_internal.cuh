@@ -104,12 +104,13 @@ struct gp_handle {
     // GP_FP64_OZAKI gradient: column slices of one row block of L^{-1} (7 x Np x b), of all
     // of L^{-1} (7 x Np x Np), their column scales and the column maxima
     __nv_bfloat16 *OGT, *OGX, *OGL;   // OGL: row slices of one diagonal-tile inverse (7 x b x b)
+    __nv_bfloat16* OGTS;              // columns of GP_OG_SP row blocks of L^{-1} (7 x Np x SP b)
     double* ogl_mu;
     double *ogt_mu, *ogx_mu;
     unsigned long long* ogx_bits;
     // GP_FP64_OZAKI prediction: test columns of one row block of V (7 x m_cap x b), all of V
     // (7 x m_cap x Np, allocated with the full covariance), their scales and column maxima
-    __nv_bfloat16 *OGV, *OGC;
+    __nv_bfloat16 *OGV, *OGC, *OGVS;   // OGVS: columns of GP_OG_SP row blocks of V (7 x m_cap x SP b)
     double *ogv_mu, *ogc_mu;
     unsigned long long* ogc_bits;
     int64_t ogc_cap;
@@ -168,9 +169,11 @@ bool factor_fp64(gp_t h);                                      // tiled Cholesky
 bool og_chol_update_cols(gp_t h, int64_t k, int64_t e);         // GP_FP64_OZAKI: columns k+1..e-1 by column k
 bool og_chol_update_sp(gp_t h, int64_t K0, int64_t e);          // GP_FP64_OZAKI: trailing update by a super-panel
 constexpr int GP_OG_SP = 4;                                     // GP_FP64_OZAKI super-panel width (tile columns)
-bool og_trtri_accum(gp_t h, int64_t t);                        // GP_FP64_OZAKI inverse: S_ij += L_it X_tj
+bool og_trtri_accum(gp_t h, int64_t t, int64_t e);             // GP_FP64_OZAKI inverse: S_ij += L_it X_tj, i < e
+bool og_trtri_accum_sp(gp_t h, int64_t T0, int64_t e);          // ... by row blocks T0..e-1 for i >= e
 bool og_lauum(gp_t h);                                         // GP_FP64_OZAKI K^{-1} = X^T X
-bool og_vsolve_update(gp_t h, int64_t j, int64_t ldm);          // GP_FP64_OZAKI V solve: B_i -= L_ij V_j
+bool og_vsolve_update(gp_t h, int64_t j, int64_t e, int64_t ldm);   // GP_FP64_OZAKI V solve: B_i -= L_ij V_j, i < e
+bool og_vsolve_update_sp(gp_t h, int64_t J0, int64_t e, int64_t ldm);   // ... by columns J0..e-1 for i >= e
 bool og_vsolve_diag(gp_t h, int64_t j, int64_t ldm);            // GP_FP64_OZAKI V solve: V_j = Linv_jj B_j
 bool og_panel(gp_t h, int64_t k);                              // GP_FP64_OZAKI panel: L_ik = A_ik Linv_kk^T
 bool og_trtri_scale(gp_t h, int64_t t);                        // GP_FP64_OZAKI inverse: X_tj = -Linv_tt S_tj

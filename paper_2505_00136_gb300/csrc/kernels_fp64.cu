@@ -1043,22 +1043,22 @@ bool predict_solve(gp_t h, int64_t m, int64_t ldm)
     const int64_t T = h->T, b = h->b;
     const int P = (int)(b / TB);
     const int64_t nq = h->Np / TB;
+    if (h->opt.prec == GP_FP64_OZAKI) {   // blocks of GP_OG_SP tile columns, as the factorisation
+        for (int64_t J0 = 0; J0 < T; J0 += GP_OG_SP) {
+            const int64_t e = J0 + GP_OG_SP < T ? J0 + GP_OG_SP : T;
+            for (int64_t j = J0; j < e; ++j)
+                if (!og_vsolve_diag(h, j, ldm) || !og_vsolve_update(h, j, e, ldm)) return false;
+            if (!og_vsolve_update_sp(h, J0, e, ldm)) return false;
+        }
+        return true;
+    }
     for (int64_t j = 0; j < T; ++j) {
-        if (h->opt.prec == GP_FP64_OZAKI) {
-            if (!og_vsolve_diag(h, j, ldm)) return false;
-        } else {
-            GPK_LAUNCH(h, GP_PH_VSOLVE, k_diagV, dim3((unsigned)P, (unsigned)(ldm / TB)), NT, DG_SMEM_BYTES,
-                       (const double*)h->Linv, (const double*)h->B, h->V, (const double*)h->beta, h->part,
-                       b, j, ldm, nq);
-        }
-        if (j + 1 < T) {
-            if (h->opt.prec == GP_FP64_OZAKI) {   // exact digit products on the tensor cores
-                if (!og_vsolve_update(h, j, ldm)) return false;
-            } else {
-                GPK_LAUNCH(h, GP_PH_VSOLVE, k_updV, dim3((unsigned)((T - j - 1) * P), (unsigned)(ldm / TB)),
-                           NT, DG_SMEM_BYTES, (const double*)h->L, h->B, (const double*)h->V, b, j, ldm);
-            }
-        }
+        GPK_LAUNCH(h, GP_PH_VSOLVE, k_diagV, dim3((unsigned)P, (unsigned)(ldm / TB)), NT, DG_SMEM_BYTES,
+                   (const double*)h->Linv, (const double*)h->B, h->V, (const double*)h->beta, h->part,
+                   b, j, ldm, nq);
+        if (j + 1 < T)
+            GPK_LAUNCH(h, GP_PH_VSOLVE, k_updV, dim3((unsigned)((T - j - 1) * P), (unsigned)(ldm / TB)),
+                       NT, DG_SMEM_BYTES, (const double*)h->L, h->B, (const double*)h->V, b, j, ldm);
     }
     return true;
 }
@@ -1094,28 +1094,25 @@ bool inverse_tiles(gp_t h)
 {
     const int64_t T = h->T, b = h->b;
     const int P = (int)(b / TB);
-    const bool emu = h->opt.prec == GP_FP64_OZAKI;   // accumulations as exact digit products
     GPK_LAUNCH(h, GP_PH_TRTRI, k_copy_diag, grid_for(T * b * b), NT, 0, (const double*)h->Linv,
                h->Xinv, b, T);
-    for (int64_t t = 0; t < T; ++t) {
-        if (t > 0) {
-            if (emu) {
-                if (!og_trtri_scale(h, t)) return false;
-            } else {
-                GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_scale, dim3((unsigned)P, (unsigned)t), NT, DG_SMEM_BYTES,
-                           (const double*)h->Linv, h->Xinv, b, t);
-            }
+    if (h->opt.prec == GP_FP64_OZAKI) {   // exact digit products, blocks of GP_OG_SP row blocks of X
+        for (int64_t T0 = 0; T0 < T; T0 += GP_OG_SP) {
+            const int64_t e = T0 + GP_OG_SP < T ? T0 + GP_OG_SP : T;
+            for (int64_t t = T0; t < e; ++t)
+                if ((t > 0 && !og_trtri_scale(h, t)) || !og_trtri_accum(h, t, e)) return false;
+            if (!og_trtri_accum_sp(h, T0, e)) return false;
         }
-        if (t + 1 < T) {
-            if (emu) {
-                if (!og_trtri_accum(h, t)) return false;
-            } else {
-                GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_accum, dim3((unsigned)((T - t - 1) * (t + 1)), (unsigned)(P * P)),
-                           NT, DG_SMEM_BYTES, (const double*)h->L, h->Xinv, b, t);
-            }
-        }
+        return og_lauum(h);
     }
-    if (emu) return og_lauum(h);
+    for (int64_t t = 0; t < T; ++t) {
+        if (t > 0)
+            GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_scale, dim3((unsigned)P, (unsigned)t), NT, DG_SMEM_BYTES,
+                       (const double*)h->Linv, h->Xinv, b, t);
+        if (t + 1 < T)
+            GPK_LAUNCH(h, GP_PH_TRTRI, k_trtri_accum, dim3((unsigned)((T - t - 1) * (t + 1)), (unsigned)(P * P)),
+                       NT, DG_SMEM_BYTES, (const double*)h->L, h->Xinv, b, t);
+    }
     GPK_LAUNCH(h, GP_PH_LAUUM, k_lauum, dim3((unsigned)(T * (T + 1) / 2), (unsigned)(P * P)), NT,
                DG_SMEM_BYTES, (const double*)h->Xinv, h->Kinv, b, T);
     return true;

@@ -341,21 +341,25 @@ __global__ void k_rowslices(Src src, int64_t rows, int64_t n, __nv_bfloat16* OS,
     if (lane == 0) mu[r] = m;
 }
 
-// Columns of the tiles (t, 0 .. t) of X = L^{-1} as B-operand rows: row
-// n = j b + c holds column c of tile (t, j) over the tile's b rows (k), scaled
-// by mu[n] = power of two >= its max |.|; entries above the diagonal of the
-// diagonal tile (t, t) are taken as zero.  One CTA per 32 columns.
-__global__ __launch_bounds__(256) void k_colslices_tile(const double* X, int64_t b, int64_t t, __nv_bfloat16* OS,
-                                                        int64_t ps, double* mu)
+// Columns of the row tiles t0 .. t0 + nt - 1 of the lower-triangular
+// X = L^{-1} as B-operand rows: row n = j b + c holds column c of the tiles
+// (t, j) over their nt b rows (k = (t - t0) b + r), scaled by mu[n] = power of
+// two >= its max |.|; entries above the diagonal (t < j, or t = j and r < c)
+// are zero.  One CTA per 32 columns.
+__global__ __launch_bounds__(256) void k_colslices_tile(const double* X, int64_t b, int64_t t0, int64_t nt,
+                                                        __nv_bfloat16* OS, int64_t ps, double* mu)
 {
     __shared__ double red[8][32];
     __shared__ double smu[32];
-    const int64_t n0 = (int64_t)blockIdx.x * 32, j = n0 / b, c0 = n0 % b;
-    const double* tile = X + tri_index(t, j) * b * b;
+    const int64_t n0 = (int64_t)blockIdx.x * 32, j = n0 / b, c0 = n0 % b, K = nt * b;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    auto at = [&](int64_t k, int64_t c) -> double {   // X at row t0 b + k, column j b + c
+        const int64_t t = t0 + k / b, r = k % b;
+        if (t < j || (t == j && r < c)) return 0.0;
+        return X[tri_index(t, j) * b * b + r * b + c];
+    };
     double mx = 0.0;
-    for (int64_t r = w; r < b; r += 8)
-        if (!(j == t && r < c0 + lane)) mx = fmax(mx, fabs(tile[r * b + c0 + lane]));
+    for (int64_t k = w; k < K; k += 8) mx = fmax(mx, fabs(at(k, c0 + lane)));
     red[w][lane] = mx;
     __syncthreads();
     if (w == 0) {
@@ -364,13 +368,12 @@ __global__ __launch_bounds__(256) void k_colslices_tile(const double* X, int64_t
         mu[n0 + lane] = smu[lane];
     }
     __syncthreads();
-    for (int64_t r = threadIdx.x; r < b; r += 256)
+    for (int64_t k = threadIdx.x; k < K; k += 256)
         for (int c = 0; c < 32; ++c) {
-            const double v = (j == t && r < c0 + c) ? 0.0 : tile[r * b + c0 + c];
             __nv_bfloat16 d[OG_S];
-            oz_digits<OG_S>(rint_scaled(v, GP_OZ_BITS * OG_S - pow2_exp(smu[c])), d);
+            oz_digits<OG_S>(rint_scaled(at(k, c0 + c), GP_OZ_BITS * OG_S - pow2_exp(smu[c])), d);
 #pragma unroll
-            for (int s = 0; s < OG_S; ++s) OS[s * ps + (n0 + c) * b + r] = d[s];
+            for (int s = 0; s < OG_S; ++s) OS[s * ps + (n0 + c) * K + k] = d[s];
         }
 }
 
@@ -605,25 +608,25 @@ struct OgTrtri {
     double* Xinv;
     const double *muA, *muB;
     int64_t b;
-    int t, P;
+    int i0, r0t, njt, T0, width, P;   // rows of tiles i0 .., columns j < njt, store when j >= T0
     int a_ps, b_ps;
     __device__ bool unit(int u, OgUnit& o) const
     {
         const int per = P * P, q = u / per;
-        const int ii = q / (t + 1), j = q % (t + 1);
+        const int ii = q / njt, j = q % njt;
         const int rb = (u % per) / P, cb = (u % per) % P;
-        const int64_t i = t + 1 + ii;
-        o.a_row = (int)(ii * b + rb * 128);
+        const int64_t i = i0 + ii;
+        o.a_row = (int)((i - r0t) * b + rb * 128);
         o.b_row = (int)(j * b + cb * 128);
         o.k0 = 0;
-        o.k1 = (int)b;
+        o.k1 = width;
         o.dst = Xinv + tri_index(i, j) * b * b + (int64_t)rb * 128 * b + cb * 128;
         o.ld = b;
         o.muA = muA + o.a_row;
         o.muB = muB + o.b_row;
         o.rows = o.cols = 128;
         o.sign = 1.0;
-        o.overwrite = (j == t);
+        o.overwrite = (j >= T0);   // the first contribution to S_ij
         return true;
     }
 };
@@ -665,17 +668,17 @@ struct OgVsolve {
     double* B;
     const double *muA, *muB;
     int64_t b, ldm;
-    int j, P, nmb;
+    int i0, r0t, width, P, nmb;   // rows of the tiles i0 .., slice row 0 = tile r0t, k range width
     int a_ps, b_ps;
     __device__ bool unit(int u, OgUnit& o) const
     {
         const int mb = u % nmb, rest = u / nmb;
-        const int rb = rest % P, ii = rest / P;
-        const int64_t i = j + 1 + ii;
-        o.a_row = (int)(ii * b + rb * 128);
+        const int rb = rest % P;
+        const int64_t i = i0 + rest / P;
+        o.a_row = (int)((i - r0t) * b + rb * 128);
         o.b_row = mb * 128;
         o.k0 = 0;
-        o.k1 = (int)b;
+        o.k1 = width;
         o.dst = B + (i * b + (int64_t)rb * 128) * ldm + (int64_t)mb * 128;
         o.ld = ldm;
         o.muA = muA + o.a_row;
@@ -880,18 +883,19 @@ bool og_chol_update_sp(gp_t h, int64_t K0, int64_t e)
     return og_launch(h, GP_PH_UPDATE, mP, mP, op, tt * (tt + 1) / 2 * op.P * op.P);
 }
 
-// Step t of the triangular inverse on the tensor cores (after the native
-// scaling X_tj = -Linv_tt S_tj of the row block): slices the panel of column t
-// and the row block (t, 0 .. t) of X, then S_ij (+)= L_it X_tj for i > t.
-bool og_trtri_accum(gp_t h, int64_t t)
+// Step t of the triangular inverse on the tensor cores inside a block of
+// rows ending at e (after the scaling X_tj = -Linv_tt S_tj of row block t):
+// S_ij (+)= L_it X_tj for t < i < e, j <= t (the first contribution, j = t,
+// stores), A = panel slices of column t, B = columns of the row block t of X.
+bool og_trtri_accum(gp_t h, int64_t t, int64_t e)
 {
-    const int64_t T = h->T, b = h->b, tt = T - t - 1;
-    if (tt <= 0) return true;
-    const int64_t rows = tt * b, cols = (t + 1) * b;
+    const int64_t b = h->b, ni = e - t - 1;
+    if (ni <= 0) return true;
+    const int64_t rows = ni * b, cols = (t + 1) * b;
     GPK_LAUNCH(h, GP_PH_TRTRI, k_rowslices<PanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
                PanelRows{h->L, b, t}, rows, b, h->OGP, rows * b, h->og_mu);
     GPK_LAUNCH(h, GP_PH_TRTRI, k_colslices_tile, (unsigned)(cols / 32), 256, 0, (const double*)h->Xinv, b, t,
-               h->OGT, cols * b, h->ogt_mu);
+               (int64_t)1, h->OGT, cols * b, h->ogt_mu);
     CUtensorMap mA, mB;
     if (!og_map(&mA, h->OGP, rows, b) || !og_map(&mB, h->OGT, cols, b)) return false;
     OgTrtri op;
@@ -899,11 +903,43 @@ bool og_trtri_accum(gp_t h, int64_t t)
     op.muA = h->og_mu;
     op.muB = h->ogt_mu;
     op.b = b;
-    op.t = (int)t;
+    op.i0 = op.r0t = (int)(t + 1);
+    op.njt = (int)(t + 1);
+    op.T0 = (int)t;
+    op.width = (int)b;
     op.P = (int)(b / 128);
     op.a_ps = (int)rows;
     op.b_ps = (int)cols;
-    return og_launch(h, GP_PH_TRTRI, mA, mB, op, tt * (t + 1) * op.P * op.P);
+    return og_launch(h, GP_PH_TRTRI, mA, mB, op, ni * (t + 1) * op.P * op.P);
+}
+
+// The inverse's accumulation by a whole block of rows T0 .. e-1 of X:
+// S_ij (+)= sum_t L_it X_tj for i >= e, j < e (stores for j >= T0, where
+// these are the first contributions), one k range of (e - T0) b.
+bool og_trtri_accum_sp(gp_t h, int64_t T0, int64_t e)
+{
+    const int64_t T = h->T, b = h->b, tt = T - e;
+    if (tt <= 0) return true;
+    const int64_t rows = tt * b, cols = e * b, width = (e - T0) * b;
+    GPK_LAUNCH(h, GP_PH_TRTRI, k_rowslices_v<SuperPanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
+               SuperPanelRows{h->L, b, T0, e}, rows, width, h->OGS, rows * width, h->og_mu);
+    GPK_LAUNCH(h, GP_PH_TRTRI, k_colslices_tile, (unsigned)(cols / 32), 256, 0, (const double*)h->Xinv, b, T0,
+               e - T0, h->OGTS, cols * width, h->ogt_mu);
+    CUtensorMap mA, mB;
+    if (!og_map(&mA, h->OGS, rows, width) || !og_map(&mB, h->OGTS, cols, width)) return false;
+    OgTrtri op;
+    op.Xinv = h->Xinv;
+    op.muA = h->og_mu;
+    op.muB = h->ogt_mu;
+    op.b = b;
+    op.i0 = op.r0t = (int)e;
+    op.njt = (int)e;
+    op.T0 = (int)T0;
+    op.width = (int)width;
+    op.P = (int)(b / 128);
+    op.a_ps = (int)rows;
+    op.b_ps = (int)cols;
+    return og_launch(h, GP_PH_TRTRI, mA, mB, op, tt * e * op.P * op.P);
 }
 
 // K^{-1} = X^T X (lower tiles) on the tensor cores from X = L^{-1}.
@@ -927,13 +963,13 @@ bool og_lauum(gp_t h)
     return og_launch(h, GP_PH_LAUUM, mX, mX, op, T * (T + 1) / 2 * op.P * op.P);
 }
 
-// Step j of the V solve on the tensor cores (after the native V_j =
-// Linv_jj B_j): B_i -= L_ij V_j for every tile i > j.
-bool og_vsolve_update(gp_t h, int64_t j, int64_t ldm)
+// Step j of the V solve on the tensor cores, inside a block of columns
+// ending at e: B_i -= L_ij V_j for j < i < e.
+bool og_vsolve_update(gp_t h, int64_t j, int64_t e, int64_t ldm)
 {
-    const int64_t T = h->T, b = h->b, tt = T - j - 1;
-    if (tt <= 0) return true;
-    const int64_t rows = tt * b;
+    const int64_t b = h->b, ni = e - j - 1;
+    if (ni <= 0) return true;
+    const int64_t rows = ni * b;
     GPK_LAUNCH(h, GP_PH_VSOLVE, k_rowslices<PanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
                PanelRows{h->L, b, j}, rows, b, h->OGP, rows * b, h->og_mu);
     GPK_LAUNCH(h, GP_PH_VSOLVE, k_colslices_dense, dim3((unsigned)(ldm / 32), 1), 256, 0,
@@ -947,7 +983,37 @@ bool og_vsolve_update(gp_t h, int64_t j, int64_t ldm)
     op.muB = h->ogv_mu;
     op.b = b;
     op.ldm = ldm;
-    op.j = (int)j;
+    op.i0 = op.r0t = (int)(j + 1);
+    op.width = (int)b;
+    op.P = (int)(b / 128);
+    op.nmb = (int)(ldm / 128);
+    op.a_ps = (int)rows;
+    op.b_ps = (int)ldm;
+    return og_launch(h, GP_PH_VSOLVE, mA, mB, op, ni * op.P * op.nmb);
+}
+
+// The V solve's update by a whole block of columns J0 .. e-1:
+// B_i -= sum_j L_ij V_j for every tile i >= e, one k range of (e - J0) b.
+bool og_vsolve_update_sp(gp_t h, int64_t J0, int64_t e, int64_t ldm)
+{
+    const int64_t T = h->T, b = h->b, tt = T - e;
+    if (tt <= 0) return true;
+    const int64_t rows = tt * b, width = (e - J0) * b;
+    GPK_LAUNCH(h, GP_PH_VSOLVE, k_rowslices_v<SuperPanelRows>, (unsigned)((rows + 7) / 8), 256, 0,
+               SuperPanelRows{h->L, b, J0, e}, rows, width, h->OGS, rows * width, h->og_mu);
+    GPK_LAUNCH(h, GP_PH_VSOLVE, k_colslices_dense, dim3((unsigned)(ldm / 32), 1), 256, 0,
+               (const double*)(h->V + J0 * b * ldm), ldm, width, (const unsigned long long*)nullptr, h->OGVS,
+               ldm * width, width, h->ogv_mu);
+    CUtensorMap mA, mB;
+    if (!og_map(&mA, h->OGS, rows, width) || !og_map(&mB, h->OGVS, ldm, width)) return false;
+    OgVsolve op;
+    op.B = h->B;
+    op.muA = h->og_mu;
+    op.muB = h->ogv_mu;
+    op.b = b;
+    op.ldm = ldm;
+    op.i0 = op.r0t = (int)e;
+    op.width = (int)width;
     op.P = (int)(b / 128);
     op.nmb = (int)(ldm / 128);
     op.a_ps = (int)rows;
@@ -1017,7 +1083,7 @@ bool og_trtri_scale(gp_t h, int64_t t)
     if (t <= 0) return true;
     og_linv_slices(h, t, GP_PH_TRTRI);
     GPK_LAUNCH(h, GP_PH_TRTRI, k_colslices_tile, (unsigned)(cols / 32), 256, 0, (const double*)h->Xinv, b, t,
-               h->OGT, cols * b, h->ogt_mu);
+               (int64_t)1, h->OGT, cols * b, h->ogt_mu);
     CUtensorMap mA, mB;
     if (!og_map(&mA, h->OGL, b, b) || !og_map(&mB, h->OGT, cols, b)) return false;
     OgStore op;
