@@ -266,6 +266,17 @@ gp_status gp_learned_init(const double* X, const double* y, int64_t n, int64_t d
  * usable.  GP_ERR_ARG unless 0 <= j <= i < n_tiles (or i < 0). */
 gp_status gp_dag_stall_tile(gp_t h, int64_t i, int64_t j);
 
+/* Testing aid for the bounded grid-barrier waits of GP_MIXED's persistent
+ * FP32 triangular solves (one cooperative launch per solve): with enable != 0,
+ * every such solve runs with its last CTA never arriving at the first
+ * barrier and with each barrier wait bounded by wait_us microseconds (at
+ * the GPU's maximum SM clock; longer at lower clocks), so the other CTAs'
+ * waits expire, the kernel leaves and the call that factors returns
+ * GP_ERR_TIMEOUT with the device still usable.  enable = 0 restores the
+ * default bound (about 2 s) and normal solves.  The next call refactors.
+ * GP_ERR_ARG if enable != 0 and wait_us is outside [1, 2e6]. */
+gp_status gp_solve_stall(gp_t h, int enable, int64_t wait_us);
+
 /* Tile geometry and last-call diagnostics. */
 typedef struct {
     int64_t n, d, tile, n_tiles, n_padded;

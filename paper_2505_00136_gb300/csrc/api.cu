@@ -588,6 +588,8 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
     h->n = n;
     h->d = d;
     h->dag_stall = -1;
+    h->solve_stall = false;
+    h->solve_wait_cycles = 4000000000ll;   // about 2 s at the maximum SM clock
     int64_t per = (n + opt.n_tiles - 1) / opt.n_tiles;
     h->b = round_up(per, opt.prec != GP_FP64 ? 2 * TB : TB);   // tensor-core paths: 128-row blocks
     h->T = (n + h->b - 1) / h->b;
@@ -624,6 +626,8 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         }
         TRY(dev_alloc(h, &h->OGL, (int64_t)gpk::GP_OG_SLICES * h->b * h->b));
         TRY(dev_alloc(h, &h->ogl_mu, h->b));
+        TRY(dev_alloc(h, &h->solve_flags, 2));   // grid barrier of the diagonal-tile factor
+        TRY(cuda_status(h, cudaMemset(h->solve_flags, 0, 2 * sizeof(int))));
     }
     if (opt.prec == GP_MIXED) {
         const int64_t bb = h->b * h->b;
@@ -926,6 +930,16 @@ gp_status gp_dag_stall_tile(gp_t h, int64_t i, int64_t j)
 {
     if (!h || (i >= 0 && (j < 0 || j > i || i >= h->T))) return GP_ERR_ARG;
     h->dag_stall = i < 0 ? -1 : tri_index(i, j);
+    h->factored = false;
+    return GP_OK;
+}
+
+gp_status gp_solve_stall(gp_t h, int enable, int64_t wait_us)
+{
+    if (!h || (enable && (wait_us < 1 || wait_us > 2000000))) return GP_ERR_ARG;
+    h->solve_stall = enable != 0;
+    // clock64 counts SM cycles: 2100 per microsecond bounds the wait from above at any clock up to 2.1 GHz
+    h->solve_wait_cycles = enable ? (long long)wait_us * 2100 : 4000000000ll;
     h->factored = false;
     return GP_OK;
 }

@@ -120,7 +120,7 @@ struct gp_handle {
     __nv_bfloat16* ZSS;       // digit slices of the test rows, 6 x m_cap x dp
     double *zs_mu, *zs_nrm;   // their row scales and |zhat|^2 (m_cap)
     bool tc_pending;          // a tensor-core kernel ran since its timeout word was last read
-    int* solve_flags;         // grid barrier of the persistent FP32 solve: arrival count, generation
+    int* solve_flags;         // grid barrier of the persistent FP32 solve and of the grid POTRF: count, generation
     __nv_bfloat16* ZP;        // T(T+1)/2 tiles x 3 planes of (L^{-1})^T tiles (gradient)
     float* U32;               // T(T+1)/2 tiles: TRTRI accumulators (gradient)
     float* Kinv32;            // T(T+1)/2 tiles: K^{-1} lower (gradient)
@@ -132,6 +132,8 @@ struct gp_handle {
     int* dag_upd;             // T(T+1)/2 update counters
     int* dag_fin;             // T(T+1)/2 final flags
     int64_t dag_stall;        // test aid: tile whose counter is poisoned (-1: none)
+    bool solve_stall;         // test aid: the last CTA of each persistent FP32 solve never arrives
+    long long solve_wait_cycles;   // bound on one grid-barrier wait of the persistent FP32 solve
 
     int64_t bytes;            // device bytes held
     int64_t last_info;
@@ -193,6 +195,9 @@ void set_info_none(gp_t h);
 // FP64 POTRF + inverse of one b x b diagonal tile A (in place) into X; adds
 // sum log L_ii to *logdet_slot; a failing pivot records row0 + its row.
 void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot);
+// The same on the whole GPU (one cooperative launch, bounded grid barriers on
+// h->solve_flags); b a multiple of 32.  False if it cannot be launched.
+bool potrf_diag_grid(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot);
 void factor_dag(gp_t h, bool reset_err);                       // persistent tile-DAG factor (FP64)
 
 // kernels_mixed.cu

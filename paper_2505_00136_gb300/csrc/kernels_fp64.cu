@@ -963,7 +963,8 @@ void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, do
 }
 
 // GP_FP64_OZAKI: right-looking in super-panels of GP_OG_SP tile columns (as
-// the mixed path): each column of a super-panel is factored, solved and
+// the mixed path), each diagonal tile factored and inverted by the whole GPU
+// (kernels_potrf_grid.cu): each column of a super-panel is factored, solved and
 // applied to the super-panel's later columns; one update with a k range of
 // the whole super-panel then reaches the trailing triangle, so each trailing
 // tile is read and written once per super-panel instead of once per column.
@@ -973,8 +974,9 @@ static bool factor_fp64_ozaki(gp_t h)
     for (int64_t K0 = 0; K0 < T; K0 += GP_OG_SP) {
         const int64_t e = K0 + GP_OG_SP < T ? K0 + GP_OG_SP : T;
         for (int64_t k = K0; k < e; ++k) {
-            potrf_diag_launch(h, h->L + tri_index(k, k) * b * b, h->Linv + k * b * b, b, k * b,
-                              h->logdet_part + k);
+            if (!potrf_diag_grid(h, h->L + tri_index(k, k) * b * b, h->Linv + k * b * b, b, k * b,
+                                 h->logdet_part + k))
+                return false;
             if (k + 1 < T && (!og_panel(h, k) || !og_chol_update_cols(h, k, e))) return false;
         }
         if (e < T && !og_chol_update_sp(h, K0, e)) return false;

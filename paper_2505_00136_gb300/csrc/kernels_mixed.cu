@@ -380,13 +380,13 @@ __global__ void k_split_panel(const float* A32, __nv_bfloat16* PA, int64_t b, in
 // chunk's own copy of s (b / SV_CH copies, summed in phase (A)), so every
 // element has one writer per step and the result is deterministic.
 // Phases are separated by a grid barrier (arrival counter and generation
-// word, bounded wait); a timeout sets *err and the kernel leaves, the caller
-// reports it.
+// word, a wait bounded by wait_limit clock cycles); a timeout sets *err and
+// the kernel leaves, the caller reports it.
 constexpr int SV_CH = 64;     // rows per chunk of a tile in phase (B)
 constexpr int SV_SEG = 256;   // columns per pass: lanes hold 4 lane + 128 u, u = 0, 1
 
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err,
-                                             int* okb)
+                                             int* okb, long long limit)
 {
     __threadfence();
     __syncthreads();
@@ -403,7 +403,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
                 unsigned v;
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(gen) : "memory");
                 if (v != g) break;
-                if (clock64() - t0 > 4000000000ll) {
+                if (clock64() - t0 > limit) {
                     atomicExch(err, 1);
                     *okb = 0;
                     break;
@@ -542,12 +542,14 @@ __device__ __forceinline__ void chunk_cols_dot(const float* Lc, const float* x, 
 // s = sbuf: Np floats (lower) or (b / SV_CH) copies of Np floats (upper).
 __global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* Linv, int64_t b, int64_t T,
                                                   const float* in, float* out, float* sbuf, int upper, unsigned* bar,
-                                                  int* err)
+                                                  int* err, long long wait_limit, int stall_last)
 {
     static_assert(NTH == 256 && NTH / 32 * 8 == SV_CH && NTH >= SV_SEG, "chunk of 8 warps x 8 rows");
     __shared__ int okb;
     __shared__ __align__(16) float red[8 * SV_SEG];
     if (threadIdx.x == 0) okb = 1;
+    // test aid: the last CTA never arrives, so every other CTA's first barrier wait runs out
+    if (stall_last && blockIdx.x == gridDim.x - 1) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nw = (int64_t)gridDim.x * (NTH / 32);
     const int64_t gw = (int64_t)blockIdx.x * (NTH / 32) + warp;
@@ -555,7 +557,7 @@ __global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* 
     const int np = upper ? (int)cpt : 1;
     for (int64_t e = (int64_t)blockIdx.x * NTH + threadIdx.x; e < np * Np; e += (int64_t)gridDim.x * NTH)
         sbuf[e] = 0.f;
-    if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
+    if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb, wait_limit)) return;
     for (int64_t q = 0; q < T; ++q) {
         const int64_t t = upper ? T - 1 - q : q;
         // (A) out_t = Linv_tt (in_t - s_t), or the transpose
@@ -571,7 +573,7 @@ __global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* 
                 if (lane == 0) *(float4*)(out + t * b + c4) = v;
             }
         }
-        if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb, wait_limit)) return;
         // (B) partial sums of the blocks still to solve, chunk by chunk
         const float* xt = out + t * b;
         if (!upper) {
@@ -588,7 +590,7 @@ __global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* 
                                sbuf + kc * Np + j * b, b, red);
             }
         }
-        if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb)) return;
+        if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb, wait_limit)) return;
     }
 }
 
@@ -1028,8 +1030,10 @@ static void solve32(gp_t h, const float* in32, float* out32, bool upper)
     float* sbuf = h->w32;
     unsigned* bar = (unsigned*)h->solve_flags;
     int* err = tc_error_dev();
+    long long limit = h->solve_wait_cycles;
+    int stall = h->solve_stall ? 1 : 0;
     void* args[] = {(void*)&Lt, (void*)&Li, (void*)&bb, (void*)&TT, (void*)&in32, (void*)&out32, (void*)&sbuf,
-                    (void*)&up, (void*)&bar, (void*)&err};
+                    (void*)&up, (void*)&bar, (void*)&err, (void*)&limit, (void*)&stall};
     cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), h->st);   // fresh barrier words, whatever a failed solve left
     const bool p_ = h->prof_on && prof_begin(h, GP_PH_SOLVE);
     // a failed launch leaves its error for the caller's check of the last launch error

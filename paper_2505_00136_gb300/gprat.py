@@ -82,6 +82,7 @@ _SIGS = {
     "gp_get_factor": (ctypes.c_int, [_H, _vp]),
     "gp_get_alpha": (ctypes.c_int, [_H, _vp]),
     "gp_dag_stall_tile": (ctypes.c_int, [_H, _i64, _i64]),
+    "gp_solve_stall": (ctypes.c_int, [_H, ctypes.c_int, _i64]),
     "gp_info": (ctypes.c_int, [_H, ctypes.POINTER(gp_info_t)]),
     "gp_profile": (ctypes.c_int, [_H, ctypes.c_int]),
     "gp_profile_read": (ctypes.c_int, [_H, _vp, _vp, ctypes.c_int]),
@@ -331,6 +332,11 @@ class GP:
     def dag_stall_tile(self, i, j=0):
         """Testing aid: poison tile (i, j)'s update counter (i < 0 clears)."""
         _check(_lib.gp_dag_stall_tile(self.h, int(i), int(j)), self.h, "gp_dag_stall_tile")
+
+    def solve_stall(self, enable, wait_us=0):
+        """Testing aid: the mixed path's persistent solves stall at their first
+        grid barrier, whose waits are bounded by wait_us (enable=False clears)."""
+        _check(_lib.gp_solve_stall(self.h, 1 if enable else 0, int(wait_us)), self.h, "gp_solve_stall")
 
     def info(self):
         inf = gp_info_t()

@@ -73,6 +73,8 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     opt.n_tiles = -1                        # 0 selects gp_auto_tiles; negative is invalid
     assert g.gp_create(px, py, 4, 2, ctypes.byref(hp), ctypes.byref(opt), ctypes.byref(h)) == g.GP_ERR_ARG
     assert g.gp_factor(None) == g.GP_ERR_ARG
+    assert g.gp_solve_stall(None, 1, 1000) == g.GP_ERR_ARG
+    assert g.gp_dag_stall_tile(None, 0, 0) == g.GP_ERR_ARG
     assert g.gp_status_str(g.GP_ERR_NOT_PD) == b"matrix not positive definite"
 
 

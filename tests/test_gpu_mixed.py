@@ -10,6 +10,8 @@ below follow from FP32 unit roundoff (6e-8) times the growth measured at
 these sizes, with a margin of 10 or more.  Reported errors are printed for the
 record (pytest -s).
 """
+import time
+
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -208,3 +210,24 @@ def test_uncorrected_variance_is_fp32_level(g, orc):
     print("variance uncorrected / corrected", e_u, e_c)
     assert 1e-9 < e_u < 1e-3
     assert e_c < VAR_TOL and rel(va_c2, va_c) < 1e-14
+
+
+def test_solve_barrier_wait_expires_and_device_stays_usable(g):
+    """A bounded wait of the persistent FP32 solve runs out: the last CTA never
+    arrives at the first grid barrier (host-set test aid, 20 ms bound), the
+    factorising call returns GP_ERR_TIMEOUT, and the same handle and context
+    then give the unstalled result bit for bit."""
+    X, y, Xs, _ = dg.msd_dataset(1024, 64, 8, seed=91)
+    hyp = (1.0, 1.0, 0.1)
+    with g.GP(X, y, hyp, n_tiles=4, precision="mixed") as ref:
+        mu_r, va_r = ref.predict_var(Xs)
+    with g.GP(X, y, hyp, n_tiles=4, precision="mixed") as gp:
+        gp.solve_stall(True, 20000)
+        t0 = time.perf_counter()
+        with pytest.raises(g.GPError) as e:
+            gp.predict_var(Xs)
+        assert e.value.status == g.GP_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 20.0
+        gp.solve_stall(False)
+        mu, va = gp.predict_var(Xs)
+    assert np.array_equal(mu, mu_r) and np.array_equal(va, va_r)
