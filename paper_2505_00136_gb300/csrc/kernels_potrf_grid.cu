@@ -183,7 +183,10 @@ __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
     __shared__ double Iv[PG_NB * PG_LD];
     __shared__ double logacc;
     __shared__ int okb, fail;
-    if (failed(a.info)) return;
+    // No early exit on an earlier failure here: CTA 0 may record a failing
+    // pivot before a late CTA starts, and a CTA that left before the first
+    // barrier would stall the others.  Every CTA reads *info after the first
+    // barrier instead, where it is the same for all of them.
     const int tid = threadIdx.x, r = tid >> 5, c = tid & 31;
     if (tid == 0) {
         okb = 1;
