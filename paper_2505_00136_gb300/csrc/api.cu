@@ -355,19 +355,33 @@ gp_status factor_mixed_refined(gp_t h)
     if ((s = read_info(h)) != GP_OK) return s;
     gpk::refine_start(h, h->y, h->alpha);
     if ((s = check_launch(h)) != GP_OK) return s;
+    // Each pass measures the FP64 residual of the current iterate first and
+    // corrects only while that residual still falls: a pass whose residual
+    // fell by less than half ends the loop without another correction, and
+    // one that rose brings back the previous iterate.
     double prev = INFINITY, nrm[2];
     int it = 0;
-    while (it < h->opt.refine_max_iter) {
-        gpk::refine_step(h, h->y, h->alpha, h->res, h->norms);
-        ++it;
+    for (;;) {
+        gpk::refine_residual(h, h->y, h->alpha, h->res, h->norms);
         if ((s = check_launch(h)) != GP_OK) return s;
         if ((s = cuda_status(h, cudaMemcpyAsync(nrm, h->norms, sizeof(nrm), cudaMemcpyDeviceToHost, h->st))) != GP_OK)
             return s;
         if ((s = sync(h)) != GP_OK) return s;
-        const double rel = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
+        double rel = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
+        if (rel > prev) {
+            if ((s = cuda_status(h, cudaMemcpyAsync(h->alpha, h->xprev, h->Np * sizeof(double),
+                                                    cudaMemcpyDeviceToDevice, h->st))) != GP_OK)
+                return s;
+            rel = prev;
+        }
         h->refine_residual = rel;
-        if (!(rel > h->opt.refine_tol) || rel > 0.5 * prev) break;
+        if (!(rel > h->opt.refine_tol) || rel > 0.5 * prev || it >= h->opt.refine_max_iter) break;
         prev = rel;
+        if ((s = cuda_status(h, cudaMemcpyAsync(h->xprev, h->alpha, h->Np * sizeof(double),
+                                                cudaMemcpyDeviceToDevice, h->st))) != GP_OK)
+            return s;
+        gpk::refine_correct(h, h->res, h->alpha);
+        ++it;
     }
     h->refine_iters = it;
     if ((s = tc_status(h)) != GP_OK) return s;   // bounded waits of the persistent solves
@@ -546,7 +560,7 @@ void gp_destroy(gp_t h)
     void* ptrs[] = {h->X, h->y, h->hyp, h->adam, h->L, h->Linv, h->beta, h->alpha, h->work,
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
-                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->norms, h->R32, h->RP,
+                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->xprev, h->pg_ws, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
                     h->dag_upd, h->dag_fin, h->OGP, h->OGS, h->og_mu, h->OGL, h->ogl_mu, h->OGT, h->OGTS, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->OGVS, h->ogv_mu,
@@ -642,6 +656,8 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(dev_alloc(h, &h->solve_flags, 2));
         TRY(cuda_status(h, cudaMemset(h->solve_flags, 0, 2 * sizeof(int))));
         TRY(dev_alloc(h, &h->res, h->Np));
+        TRY(dev_alloc(h, &h->xprev, h->Np));
+        TRY(dev_alloc(h, &h->pg_ws, 2 * bb));
         TRY(dev_alloc(h, &h->norms, 2));
         TRY(dev_alloc(h, &h->kappa, 1));
         h->tc_dist = gpk::use_tc_dist(h);
@@ -682,7 +698,7 @@ gp_status gp_predict(gp_t h, const double* Xs, int64_t m, double* mean, double* 
     if (s != GP_OK) return s;
     bool any_host = false;
     if (h->opt.prec == GP_MIXED) {
-        if (!gpk::predict_mixed(h, m, ldm, var != nullptr || cov != nullptr)) return GP_ERR_CUDA;
+        if (!gpk::predict_mixed(h, m, ldm, var != nullptr, cov != nullptr)) return GP_ERR_CUDA;
     } else if (!var && !cov) {  // Eq. 3 alone: one pass K_{Z*,Z} alpha, no solve
         gpk::predict_mean_only(h, m, ldm);
     } else {

@@ -80,6 +80,8 @@ struct gp_handle {
     __nv_bfloat16* PA;        // (T-1) tiles x 3 planes: panel operand scratch
     float *r32, *t32, *w32;   // FP32 vectors of the refinement solves (w32: b / 64 copies of Np)
     double* res;              // Np FP64 residual
+    double* xprev;            // Np: the refinement's previous iterate
+    double* pg_ws;            // 2 b^2: FP64 work space of the diagonal-tile factor
     double* norms;            // 2 FP64 norms
     float* R32;               // m_cap x Np: K_{Z*,Z}, overwritten by the W solve
     __nv_bfloat16 *RP, *WP;   // planes: RP 3 x m_cap x b (scratch), WP 3 x m_cap x Np (all of W)
@@ -198,15 +200,21 @@ void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, do
 // The same on the whole GPU (one cooperative launch, bounded grid barriers on
 // h->solve_flags); b a multiple of 32.  False if it cannot be launched.
 bool potrf_diag_grid(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot);
+// The same for an FP32 tile (GP_MIXED), factored in FP64 in work (2 b^2
+// doubles): A32 (lower, in place) = L, X32 = L^{-1}, XP = its three BF16 planes.
+bool potrf_diag_grid32(gp_t h, float* A32, float* X32, __nv_bfloat16* XP, double* work, int64_t b, int64_t row0,
+                       double* logdet_slot);
 void factor_dag(gp_t h, bool reset_err);                       // persistent tile-DAG factor (FP64)
 
 // kernels_mixed.cu
 bool factor_mixed(gp_t h);                                     // mixed factor of h->A32
 void refine_start(gp_t h, const double* rhs, double* x);       // x = L~^{-T} L~^{-1} rhs
-void refine_step(gp_t h, const double* rhs, double* x, double* r, double* norms);  // r = rhs - K x; x += correction
+void refine_residual(gp_t h, const double* rhs, const double* x, double* r,
+                     double* norms);                             // r = rhs - K x (FP64), ||r||^2, ||rhs||^2
+void refine_correct(gp_t h, const double* r, double* x);        // x += L~^{-T} L~^{-1} r (FP32 solves)
 void residual64(gp_t h, const double* x, const double* y, double* r);              // r = y - K x (FP64)
 void nlml_mixed(gp_t h);                                       // scal[0] from y^T alpha and log|K|
-bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var);
+bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var, bool want_cov);
 void copy_factor_dense_mixed(gp_t h, double* out);
 bool full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov);  // cov (prefilled prior) -= W W^T
 bool inverse_mixed(gp_t h);                                    // Kinv32 = (L~ L~^T)^{-1}
@@ -218,8 +226,11 @@ int* tc_error_dev();                                            // device addres
 // kernels_tgemm.cu: split-BF16 block products on tcgen05 (false: tensor map not encodable)
 bool tg_panel(gp_t h, int64_t k);
 bool tg_update(gp_t h, int k0, int nsrc, int j0, int w);   // A_ij -= sum_k L_ik L_jk^T on a column band
-bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j);
-bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni);   // R_i -= sum W_j L_ij^T
+// The four multi-RHS sweep products take planes = 3 (six plane products, FP32
+// accuracy) or 2 (the three of order <= 2^-8, about 2^-16 relative).
+bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j, int planes);
+bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni,
+              int planes);   // R_i -= sum W_j L_ij^T
 bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov);
 bool tg_trtri_fin(gp_t h, int64_t t);
 bool tg_trtri_acc(gp_t h, int t0, int t1, int i0, int ni, int nj);   // U_ij (+)= sum_t Z_tj L_it^T
@@ -231,8 +242,8 @@ void zslices(gp_t h, const double* Z, const double* center, int64_t rows, int64_
 bool dist_train_tc(gp_t h);                                     // K tiles into L (FP64) and A32
 bool dist_cross_tc(gp_t h, int64_t m, int64_t ldm);             // R32, R64, mean partials
 bool dist_prior_tc(gp_t h, int64_t m, int64_t ldm, double* out);   // K_{Z*,Z*} (m x m)
-bool tg_bdiag(gp_t h, int64_t ldm, int64_t i);                  // Y_i = S_i Linv_ii (NN form)
-bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj);   // S_j -= sum Y_i L_ij (NN form)
+bool tg_bdiag(gp_t h, int64_t ldm, int64_t i, int planes);      // Y_i = S_i Linv_ii (NN form)
+bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj, int planes);   // S_j -= sum Y_i L_ij (NN form)
 constexpr int GP_OZ_SLICES = 6;                                // digit slices of K (kernels_mixed.cu)
 constexpr int GP_OZ_YSLICES = 2;                               // digit slices of x~0: x0 rounded to 14 bits per row
 constexpr int GP_OZ_BITS = 7;                                   // bits per signed digit: |d| <= 2^7, exact in BF16

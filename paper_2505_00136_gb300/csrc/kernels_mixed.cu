@@ -977,10 +977,28 @@ static void ensure_attrs_mixed()
     done_dev = dev;
 }
 
+// Operand planes of the three multi-RHS sweeps of a prediction.  W =
+// K_{Z*,Z} L~^{-T} feeds x0 and the full covariance and keeps all three
+// planes (FP32 accuracy).  The backward sweep x0^T = W L~^{-1} and the forward
+// sweep of r0 take the three plane products of order <= 2^-8 (about 2^-16
+// relative): x0 is rounded to 14 bits afterwards and the exact correction
+// holds for any x0, and ||L~^{-1} r0||^2 is a small second-order term.
+// Measured at N = 32768, M = 8192 against the emulated FP64 path: variance
+// error 4.2e-11 with three planes everywhere, 3.4e-11 with these choices;
+// two planes on W as well give 1.2e-9 (worst element 5e-8).
+constexpr int SWEEP_PLANES_W = 3;
+constexpr int SWEEP_PLANES_B = 2;
+constexpr int SWEEP_PLANES_R = 2;
+
 // The factorisation and the multi-RHS sweeps update their trailing FP32
 // matrix once per block of SWEEP_BLOCK tile columns (one k-segment per
 // column), so it is read and written T / SWEEP_BLOCK times, not T.
 constexpr int SWEEP_BLOCK = 4;
+
+// Diagonal tiles: FP32 factor and inverse on one SM (k_potrf32, 0.32 ms per
+// tile of 256) or the FP64 factor spread over the GPU (potrf_diag_grid32,
+// measured 0.71 ms per tile).
+constexpr bool MIXED_DIAG_FP64 = false;
 
 // Right-looking, in super-panels of SWEEP_BLOCK tile columns: each column k
 // of a super-panel is factored (diagonal tile, panel) and applied only to the
@@ -994,8 +1012,15 @@ bool factor_mixed(gp_t h)
     for (int K0 = 0; K0 < T; K0 += SWEEP_BLOCK) {
         const int e = K0 + SWEEP_BLOCK < T ? K0 + SWEEP_BLOCK : T;
         for (int k = K0; k < e; ++k) {
-            GPK_LAUNCH(h, GP_PH_POTRF, k_potrf32, 1, NTH, POTRF32_SMEM, h->A32 + tri_index(k, k) * bb,
-                       h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b, (int64_t)k * b, h->logdet_part + k, h->info);
+            if (MIXED_DIAG_FP64) {
+                if (!potrf_diag_grid32(h, h->A32 + tri_index(k, k) * bb, h->Linv32 + k * bb,
+                                       h->LinvP + k * 3 * bb, h->pg_ws, b, (int64_t)k * b, h->logdet_part + k))
+                    return false;
+            } else {
+                GPK_LAUNCH(h, GP_PH_POTRF, k_potrf32, 1, NTH, POTRF32_SMEM, h->A32 + tri_index(k, k) * bb,
+                           h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b, (int64_t)k * b, h->logdet_part + k,
+                           h->info);
+            }
             if (k + 1 < T) {
                 const unsigned tt = (unsigned)(T - k - 1);
                 GPK_LAUNCH(h, GP_PH_TRSM, k_split_panel, dim3((unsigned)grid_for(bb) / 4 + 1, tt), NTH, 0,
@@ -1065,11 +1090,15 @@ void refine_start(gp_t h, const double* rhs, double* x)
     correct(h, x);
 }
 
-void refine_step(gp_t h, const double* rhs, double* x, double* r, double* norms)
+void refine_residual(gp_t h, const double* rhs, const double* x, double* r, double* norms)
 {
     residual64(h, x, rhs, r);
     GPK_LAUNCH(h, GP_PH_REFINE, k_norms2, 1, NTH, 0, (const double*)r, rhs, h->Np, norms);
-    GPK_LAUNCH(h, GP_PH_REFINE, k_d2f, grid_for(h->Np), NTH, 0, (const double*)r, h->r32, h->Np);
+}
+
+void refine_correct(gp_t h, const double* r, double* x)
+{
+    GPK_LAUNCH(h, GP_PH_REFINE, k_d2f, grid_for(h->Np), NTH, 0, r, h->r32, h->Np);
     correct(h, x);
 }
 
@@ -1082,7 +1111,7 @@ void nlml_mixed(gp_t h)
 // Forward multi-RHS solve W = R L~^{-T} in place over R (ldm x Np, FP32): W
 // planes into WP, FP32 W over R, FP64 row sums of W^2 into vpart.
 
-static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase)
+static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase, int planes)
 {
     const int T = (int)h->T;
     const int64_t b = h->b, Np = h->Np;
@@ -1091,15 +1120,15 @@ static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase)
         for (int j = J; j < e; ++j) {
             GPK_LAUNCH(h, phase, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)R, Np, (int64_t)j, b, ldm,
                        h->RP);
-            if (!tg_diag_w(h, phase, R, ldm, vpart, j)) return false;
-            if (j + 1 < e && !tg_upd_w(h, phase, R, ldm, j, 1, j + 1, e - j - 1)) return false;
+            if (!tg_diag_w(h, phase, R, ldm, vpart, j, planes)) return false;
+            if (j + 1 < e && !tg_upd_w(h, phase, R, ldm, j, 1, j + 1, e - j - 1, planes)) return false;
         }
-        if (e < T && !tg_upd_w(h, phase, R, ldm, J, e - J, e, T - e)) return false;
+        if (e < T && !tg_upd_w(h, phase, R, ldm, J, e - J, e, T - e, planes)) return false;
     }
     return true;
 }
 
-bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
+bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var, bool want_cov)
 {
     ensure_attrs_mixed();
     const int64_t Np = h->Np;
@@ -1112,7 +1141,9 @@ bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var)
                    (const double*)h->Xs, m, (const double*)h->X, h->n, h->d, (const double*)h->alpha,
                    (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm, h->R64);
     }
-    if (want_var && !forward_w(h, h->R32, ldm, h->vpart, GP_PH_VSOLVE)) return false;
+    if ((want_var || want_cov) &&
+        !forward_w(h, h->R32, ldm, h->vpart, GP_PH_VSOLVE, SWEEP_PLANES_W))
+        return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_mixed_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->mpart,
                nmp, (const double*)h->vpart, want_var ? nvp : (int64_t)0, ldm, m, (const GpHyperDev*)h->hyp,
                h->opt.noisy_test_var, h->outm, want_var ? h->outv : (double*)nullptr);
@@ -1132,10 +1163,10 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
         for (int i = I; i >= lo; --i) {
             GPK_LAUNCH(h, GP_PH_BSOLVE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np,
                        (int64_t)i, b, ldm, h->RP);
-            if (!tg_bdiag(h, ldm, i)) return false;
-            if (i > lo && !tg_bupd(h, ldm, i, 1, lo, i - lo)) return false;
+            if (!tg_bdiag(h, ldm, i, SWEEP_PLANES_B)) return false;
+            if (i > lo && !tg_bupd(h, ldm, i, 1, lo, i - lo, SWEEP_PLANES_B)) return false;
         }
-        if (lo > 0 && !tg_bupd(h, ldm, lo, I - lo + 1, 0, lo)) return false;
+        if (lo > 0 && !tg_bupd(h, ldm, lo, I - lo + 1, 0, lo, SWEEP_PLANES_B)) return false;
     }
     GPK_LAUNCH(h, GP_PH_SLICES, k_yslices, (unsigned)ldm, NTH, 0, h->R32, Np, h->YS, ldm * Np, h->mu);
     if (!h->ks_valid) {
@@ -1144,7 +1175,7 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
         h->ks_valid = true;
     }
     if (!ozaki_tc(h, m, ldm)) return false;
-    if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_RSOLVE)) return false;
+    if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_RSOLVE, SWEEP_PLANES_R)) return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, Np / 64,
                (const double*)h->vpart2, Np / 64, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
                h->outv);

@@ -1,5 +1,5 @@
 // FP64 Cholesky factor and inverse of one diagonal tile, spread over the
-// whole GPU (GP_FP64_OZAKI).
+// whole GPU (GP_FP64_OZAKI, and GP_MIXED on its FP32 tiles).
 //
 // On this part one SM retires about 1.7 FP64 FMAs per clock, so the b x b
 // diagonal tile's factor and inverse (b^3 / 3 FMAs, 5.6e6 at b = 256) take
@@ -27,8 +27,11 @@
 // triangle zero), *logdet_slot = sum of log L_jj (summed in block order).
 #include <math.h>
 
+#include <utility>
+
 #include "gp_internal.cuh"
 #include "se_common.cuh"
+#include "split_bf16.cuh"
 
 namespace gpk {
 namespace {
@@ -48,6 +51,12 @@ struct PgArgs {
     unsigned* bar;              // arrival count, generation (zeroed before the launch)
     int* err;
     long long limit;            // bound on one barrier wait, in SM clock cycles
+    // FP32 tile (GP_MIXED): A and X are then FP64 work space; the tile A32
+    // (lower triangle read) is copied into A first, and on return holds L;
+    // X32 = L^{-1}, XP = the three BF16 planes of X32 (plane q at XP + q b^2).
+    float* A32;
+    float* X32;
+    __nv_bfloat16* XP;
 };
 
 __device__ bool pg_barrier(const PgArgs& a, int* okb)
@@ -113,59 +122,96 @@ __device__ __forceinline__ void pg_term(double& acc, const double* Ab, int r0, c
     acc += s0 + s1;
 }
 
-// (a): factor and invert block (p, p) in shared memory (CTA 0).  Returns false
-// on a non-positive pivot (recorded in *info).
+// Step J of the 32 x 32 factor held in one warp's registers (lane l holds
+// row l): pivot, column J scaled by 1 / L_JJ, rank-1 update of the later
+// columns.  Entries above the diagonal are scratch.  bad = first pivot that
+// is not positive; dinv = 1 / L_ll on lane l.
+template <int J>
+__device__ __forceinline__ void chol32_step(double (&row)[32], int l, int& bad, double& dinv)
+{
+    const double d = __shfl_sync(0xffffffffu, row[J], J);
+    if (!(d > 0.0) && bad < 0) bad = J;
+    const double dj = sqrt(d), inv = 1.0 / dj;
+    if (l == J) dinv = inv;
+    row[J] = (l == J) ? dj : row[J] * inv;
+#pragma unroll
+    for (int c = J + 1; c < 32; ++c) row[c] = fma(-row[J], __shfl_sync(0xffffffffu, row[J], c), row[c]);
+}
+
+template <int... J>
+__device__ __forceinline__ void chol32_steps(double (&row)[32], int l, int& bad, double& dinv,
+                                             std::integer_sequence<int, J...>)
+{
+    (chol32_step<J>(row, l, bad, dinv), ...);
+}
+
+// Row R of the forward substitution L x = e_c (L in S, row stride PG_LD;
+// dv[R] = 1 / L_RR): rows above c come out exactly zero.
+template <int R>
+__device__ __forceinline__ void trinv32_row(const double* S, const double* dv, int c, double (&x)[32])
+{
+    double s4[4] = {(R == c) ? 1.0 : 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int t = 0; t < R; ++t) s4[t & 3] = fma(-S[R * PG_LD + t], x[t], s4[t & 3]);
+    x[R] = ((s4[0] + s4[1]) + (s4[2] + s4[3])) * dv[R];
+}
+
+template <int... R>
+__device__ __forceinline__ void trinv32_rows(const double* S, const double* dv, int c, double (&x)[32],
+                                             std::integer_sequence<int, R...>)
+{
+    (trinv32_row<R>(S, dv, c, x), ...);
+}
+
+// (a): factor and invert block (p, p) (CTA 0).  Warp 0 factors the block in
+// registers and then, lane c for column c, inverts it by forward
+// substitution; the other warps only stage the block in and out.  Returns
+// false on a pivot that is not positive (recorded in *info).
 __device__ bool pg_diag(const PgArgs& a, int p, double* S, double* Iv, double* logacc, int* fail)
 {
     const int tid = threadIdx.x;
     double* App = blk(a.A, a.b, p, p);
+    double* dv = Iv + PG_NB * PG_LD;   // 32 reciprocals of the pivots
     for (int e = tid; e < PG_NB * PG_NB; e += PG_TH) {
         const int r = e >> 5, c = e & 31;
         S[r * PG_LD + c] = (c <= r) ? __ldcg(App + (int64_t)r * a.b + c) : 0.0;
-        Iv[r * PG_LD + c] = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
-    // right-looking: pivot, column scaling, rank-1 update of the trailing lower triangle
-    for (int j = 0; j < PG_NB; ++j) {
-        if (tid == 0) {
-            const double piv = S[j * PG_LD + j];
-            if (piv > 0.0) {
-                S[j * PG_LD + j] = sqrt(piv);
-            } else {
-                *fail = 1;
-                atomicMin(a.info, (unsigned long long)(a.row0 + (int64_t)p * PG_NB + j));
-            }
-        }
-        __syncthreads();
-        if (*fail) return false;
-        const double djj = S[j * PG_LD + j];
-        if (tid > j && tid < PG_NB) S[tid * PG_LD + j] /= djj;
-        __syncthreads();
-        const int n = PG_NB - 1 - j;   // trailing order
-        for (int e = tid; e < n * n; e += PG_TH) {
-            const int r = j + 1 + e / n, c = j + 1 + e % n;
-            if (c <= r) S[r * PG_LD + c] = fma(-S[r * PG_LD + j], S[c * PG_LD + j], S[r * PG_LD + c]);
-        }
-        __syncthreads();
-    }
     if (tid < 32) {
-        double lg = log(S[tid * PG_LD + tid]);
+        const int l = tid;
+        double row[32], dinv = 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
-        if (tid == 0) *logacc += lg;
-    }
-    // inverse by column-oriented forward substitution: for t = 0 .. 31, row t of
-    // X is final after dividing by L_tt; then X(r, c) -= L(r, t) X(t, c) for r > t
-    for (int t = 0; t < PG_NB; ++t) {
-        if (tid <= t) Iv[t * PG_LD + tid] /= S[t * PG_LD + t];
-        __syncthreads();
-        const int n = PG_NB - 1 - t;
-        for (int e = tid; e < n * (t + 1); e += PG_TH) {
-            const int r = t + 1 + e / (t + 1), c = e % (t + 1);
-            Iv[r * PG_LD + c] = fma(-S[r * PG_LD + t], Iv[t * PG_LD + c], Iv[r * PG_LD + c]);
+        for (int c = 0; c < 32; ++c) row[c] = S[l * PG_LD + c];
+        int bad = -1;
+        chol32_steps(row, l, bad, dinv, std::make_integer_sequence<int, 32>{});
+        if (bad >= 0) {   // the same pivot on every lane
+            if (l == 0) {
+                *fail = 1;
+                atomicMin(a.info, (unsigned long long)(a.row0 + (int64_t)p * PG_NB + bad));
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) S[l * PG_LD + c] = (c <= l) ? row[c] : 0.0;
+            dv[l] = dinv;
+            double dl = 1.0;
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c == l) dl = row[c];
+            double lg = log(dl);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
+            if (l == 0) *logacc += lg;
         }
-        __syncthreads();
+        __syncwarp();
+        if (!*fail) {
+            double x[32];
+            trinv32_rows(S, dv, l, x, std::make_integer_sequence<int, 32>{});
+#pragma unroll
+            for (int r = 0; r < 32; ++r) Iv[r * PG_LD + l] = x[r];
+        }
     }
+    __syncthreads();
+    if (*fail) return false;
     double* Xpp = blk(a.X, a.b, p, p);
     for (int e = tid; e < PG_NB * PG_NB; e += PG_TH) {
         const int r = e >> 5, c = e & 31;
@@ -175,12 +221,13 @@ __device__ bool pg_diag(const PgArgs& a, int p, double* S, double* Iv, double* l
     return true;
 }
 
+template <bool F32>
 __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
 {
     __shared__ double As[PG_ROWS * PG_LD];
     __shared__ double Bs[PG_NB * PG_LD];
     __shared__ double S[PG_NB * PG_LD];
-    __shared__ double Iv[PG_NB * PG_LD];
+    __shared__ double Iv[PG_NB * PG_LD + PG_NB];
     __shared__ double logacc;
     __shared__ int okb, fail;
     // No early exit on an earlier failure here: CTA 0 may record a failing
@@ -197,6 +244,11 @@ __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
     const int P = (int)(a.b / PG_NB);
     const int64_t b = a.b;
     const int units_per_blk = PG_NB / PG_ROWS;
+    if (F32) {   // the FP32 tile into the FP64 work space
+        for (int64_t e = (int64_t)blockIdx.x * PG_TH + tid; e < b * b; e += (int64_t)gridDim.x * PG_TH)
+            a.A[e] = (double)__ldcg(a.A32 + e);
+        if (!pg_barrier(a, &okb)) return;
+    }
 
     for (int p = 0; p < P; ++p) {
         if (blockIdx.x == 0) pg_diag(a, p, S, Iv, &logacc, &fail);
@@ -283,10 +335,19 @@ __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
         }
         if (!pg_barrier(a, &okb)) return;
     }
-    // strict upper triangles of L and X (the latter held the products T)
+    // strict upper triangles of L and X are zero (X's held the products T)
     for (int64_t e = (int64_t)blockIdx.x * PG_TH + tid; e < b * b; e += (int64_t)gridDim.x * PG_TH) {
         const int64_t rr = e / b, cc = e % b;
-        if (cc > rr) {
+        if (F32) {
+            const float lv = cc > rr ? 0.f : (float)a.A[e], xv = cc > rr ? 0.f : (float)a.X[e];
+            a.A32[e] = lv;
+            a.X32[e] = xv;
+            __nv_bfloat16 hi, mid, lo;
+            split3(xv, hi, mid, lo);
+            a.XP[e] = hi;
+            a.XP[b * b + e] = mid;
+            a.XP[2 * b * b + e] = lo;
+        } else if (cc > rr) {
             a.A[e] = 0.0;
             a.X[e] = 0.0;
         }
@@ -296,8 +357,10 @@ __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
 
 }  // namespace
 
-// One cooperative launch per diagonal tile; b must be a multiple of 32.
-bool potrf_diag_grid(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot)
+namespace {
+
+template <bool F32>
+bool potrf_grid_launch(gp_t h, PgArgs& a)
 {
     static int grid_dev = -1, grid_blocks = 0;
     int dev = 0;
@@ -305,31 +368,55 @@ bool potrf_diag_grid(gp_t h, double* A, double* X, int64_t b, int64_t row0, doub
     if (grid_dev != dev) {   // every CTA resident at once: the blocks wait on one another
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_potrf_grid, PG_TH, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_potrf_grid<F32>, PG_TH, 0);
         grid_blocks = per >= 1 ? sms : 0;   // one CTA per SM: the FP64 pipe, not occupancy, sets the pace
         grid_dev = dev;
     }
-    if (grid_blocks < 1 || b % PG_NB) return false;
-    PgArgs a;
-    a.A = A;
-    a.X = X;
-    a.b = b;
-    a.row0 = row0;
-    a.logdet_slot = logdet_slot;
+    if (grid_blocks < 1 || a.b % PG_NB || a.b < PG_NB) return false;
     a.info = h->info;
     a.bar = (unsigned*)h->solve_flags;
     a.err = tc_error_dev();
-    a.limit = 4000000000ll;
+    a.limit = 4000000000ll;   // about 2 s at the maximum SM clock
     if (!a.err || !a.bar) return false;
     void* args[] = {(void*)&a};
     cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), h->st);   // fresh barrier words
     const bool p_ = h->prof_on && prof_begin(h, GP_PH_POTRF);
     // a failed launch leaves its error for the caller's check of the last launch error
-    cudaLaunchCooperativeKernel((const void*)k_potrf_grid, dim3((unsigned)grid_blocks), dim3(PG_TH), args, 0, h->st);
+    cudaLaunchCooperativeKernel((const void*)k_potrf_grid<F32>, dim3((unsigned)grid_blocks), dim3(PG_TH), args, 0,
+                                h->st);
     h->launches++;
     if (p_) prof_end(h);
     h->tc_pending = true;
     return true;
+}
+
+}  // namespace
+
+// One cooperative launch per diagonal tile; b must be a multiple of 32.
+bool potrf_diag_grid(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot)
+{
+    PgArgs a{};
+    a.A = A;
+    a.X = X;
+    a.b = b;
+    a.row0 = row0;
+    a.logdet_slot = logdet_slot;
+    return potrf_grid_launch<false>(h, a);
+}
+
+bool potrf_diag_grid32(gp_t h, float* A32, float* X32, __nv_bfloat16* XP, double* work, int64_t b, int64_t row0,
+                       double* logdet_slot)
+{
+    PgArgs a{};
+    a.A = work;
+    a.X = work + b * b;
+    a.b = b;
+    a.row0 = row0;
+    a.logdet_slot = logdet_slot;
+    a.A32 = A32;
+    a.X32 = X32;
+    a.XP = XP;
+    return potrf_grid_launch<true>(h, a);
 }
 
 }  // namespace gpk

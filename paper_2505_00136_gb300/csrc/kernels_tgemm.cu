@@ -41,11 +41,15 @@ constexpr int TG_EPI_WARPS = 8;
 constexpr int TG_KS = 32;                          // k per stage
 constexpr int TG_APLANE = 128 * TG_KS * 2;         // bytes of one 128-row A plane tile
 
-template <int N>
+// P = operand planes used (3: the six plane products a + b <= 2, FP32
+// accuracy; 2: the three with a + b <= 1, about 2^-16 relative; 1: the
+// leading planes only, about 2^-8): a stage holds P planes of A and of B.
+template <int N, int P = 3>
 struct TgCfg {
+    static_assert(P >= 1 && P <= 3, "one to three planes");
     static constexpr int BPLANE = N * TG_KS * 2;                 // bytes of one N-row B plane tile
-    static constexpr int STAGE = 3 * TG_APLANE + 3 * BPLANE;     // 48 KB (N = 128) or 72 KB (N = 256)
-    static constexpr int STAGES = N == 256 ? 3 : 4;
+    static constexpr int STAGE = P * TG_APLANE + P * BPLANE;     // P = 3: 48 KB (N = 128) or 72 KB (N = 256)
+    static constexpr int STAGES = (216 * 1024 / STAGE) < 12 ? (216 * 1024 / STAGE) : 12;
     static constexpr int BAR_OFF = STAGES * STAGE;
     static constexpr int SMEM = 1024 + BAR_OFF + 256;
     static constexpr uint32_t IDESC = tc::idesc_bf16(128, N);
@@ -74,7 +78,7 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                                                          const __grid_constant__ CUtensorMap mapB, const Op op,
                                                          int* err)
 {
-    using C = TgCfg<Op::kN>;
+    using C = TgCfg<Op::kN, Op::kP>;
     extern __shared__ unsigned char dyn[];
     if (op.skip_all()) return;
     unsigned char* base = dyn + ((1024 - (tc::su32(dyn) & 1023)) & 1023);
@@ -127,13 +131,14 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                         }
                         const uint32_t dst = sbase + st * C::STAGE;
                         tc::mbar_expect_tx(full(st), C::STAGE);
-                        // one box per operand: the three planes are the box's last dimension
+                        // one box per operand: the P planes are the box's last dimension
                         tc::tma_load_3d_hint(dst, &mapA, sg.a_x + k, sg.a_row, 0, full(st), pol);
                         if (Op::kBMN)
-                            tc::tma_load_4d_hint(dst + 3 * TG_APLANE, &mapB, 0, sg.b_row + k, sg.b_x / 64, 0,
+                            tc::tma_load_4d_hint(dst + Op::kP * TG_APLANE, &mapB, 0, sg.b_row + k, sg.b_x / 64, 0,
                                                  full(st), pol);
                         else
-                            tc::tma_load_3d_hint(dst + 3 * TG_APLANE, &mapB, sg.b_x + k, sg.b_row, 0, full(st), pol);
+                            tc::tma_load_3d_hint(dst + Op::kP * TG_APLANE, &mapB, sg.b_x + k, sg.b_row, 0, full(st),
+                                                 pol);
                     }
                 }
             }
@@ -169,8 +174,8 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
                         // bytes (K-major) or 2048 bytes (MN-major B)
                         const uint32_t s0 = sbase + st * C::STAGE;
                         const uint64_t da = tc::desc_sw64(s0);
-                        const uint64_t db = Op::kBMN ? tc::desc_mn32_sw128(s0 + 3 * TG_APLANE)
-                                                     : tc::desc_sw64(s0 + 3 * TG_APLANE);
+                        const uint64_t db = Op::kBMN ? tc::desc_mn32_sw128(s0 + Op::kP * TG_APLANE)
+                                                     : tc::desc_sw64(s0 + Op::kP * TG_APLANE);
                         constexpr uint64_t apl = (uint64_t)(TG_APLANE >> 4);
                         constexpr uint64_t bpl = (uint64_t)(C::BPLANE >> 4);
                         constexpr uint64_t bstep = Op::kBMN ? (2048 >> 4) : 2;
@@ -181,9 +186,9 @@ __global__ __launch_bounds__(TG_THREADS, 1) void k_tgemm(const __grid_constant__
 #pragma unroll
                         for (int kk = 0; kk < TG_KS / 16; ++kk)
 #pragma unroll
-                            for (int qa = 0; qa < 3; ++qa)
+                            for (int qa = 0; qa < Op::kP; ++qa)
 #pragma unroll
-                                for (int qb = 0; qa + qb < 3; ++qb) {
+                                for (int qb = 0; qa + qb < Op::kP; ++qb) {
                                     if (kk == 0 && qa == 0 && qb == 0) continue;
                                     tc::mma_bf16_acc(d, da + qa * apl + 2 * kk, db + qb * bpl + bstep * kk, idesc);
                                 }
@@ -319,6 +324,7 @@ template <int N>
 struct OpPanel {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
+    static constexpr int kP = 3;
     float* A32;
     __nv_bfloat16* LP;
     int b, k, tt, Q, Qn;
@@ -362,6 +368,7 @@ template <int N>
 struct OpUpdate {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
+    static constexpr int kP = 3;
     float* A32;
     int b, k0, nsrc, j0, w, T, Q, Qn;
     const unsigned long long* info;
@@ -414,10 +421,11 @@ struct OpUpdate {
 // Forward multi-RHS solve, diagonal step: W_j = R_j Linv_jj^T; planes of W_j
 // into WP, FP32 W_j over R_j, FP64 row sums of W_j^2 into vpart (one slot per
 // 64 columns).
-template <int N>
+template <int N, int P = 3>
 struct OpDiagW {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
+    static constexpr int kP = P;
     __nv_bfloat16* WP;
     float* Wout;
     double* vpart;
@@ -460,10 +468,11 @@ struct OpDiagW {
 // Forward multi-RHS solve, update: R_i -= sum_{j in [j0, j0 + nsrc)} W_j L_ij^T
 // for the target tiles i in [i0, i0 + ni), one k-segment per source column
 // (the block step of the sweep: R_i is read and written once per block).
-template <int N>
+template <int N, int P = 3>
 struct OpUpdW {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
+    static constexpr int kP = P;
     float* R32;
     int64_t ldr;
     int b, j0, nsrc, i0, ni, Qn, nmb;
@@ -502,6 +511,7 @@ struct OpUpdW {
 struct OpSyrkCov {
     static constexpr bool kBMN = false;
     static constexpr int kN = 128;
+    static constexpr int kP = 3;
     double* cov;
     int64_t m;
     int kdim, nb;
@@ -545,6 +555,7 @@ template <int N>
 struct OpTrtriFin {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
+    static constexpr int kP = 3;
     __nv_bfloat16* ZP;
     int b, t, Q, Qn;
     __device__ bool skip_all() const { return false; }
@@ -581,6 +592,7 @@ template <int N>
 struct OpTrtriAcc {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
+    static constexpr int kP = 3;
     float* U32;
     int b, t0, t1, i0, ni, nj, Q, Qn;
     __device__ bool skip_all() const { return false; }
@@ -626,6 +638,7 @@ template <int N>
 struct OpLauum {
     static constexpr bool kBMN = false;
     static constexpr int kN = N;
+    static constexpr int kP = 3;
     float* Kinv32;
     int b, T, Q, Qn;
     __device__ bool skip_all() const { return false; }
@@ -676,10 +689,11 @@ struct OpLauum {
 // k-range of a column unit starts at its first column.  FP32 Y_i over S_i
 // (column block i of R32) and its planes into column block i of planes
 // (three planes of ldm x ldr: the W plane buffer).
-template <int N>
+template <int N, int P = 3>
 struct OpBDiag {
     static constexpr bool kBMN = true;
     static constexpr int kN = N;
+    static constexpr int kP = P;
     float* R32;
     __nv_bfloat16* planes;
     int64_t ldr, ldm;
@@ -715,10 +729,11 @@ struct OpBDiag {
 // Backward solve, update: S_j -= sum_{i in [i0, i0 + nsrc)} Y_i L_ij for the
 // target tiles j in [j0, j0 + nj), all below i0 (NN form, L_ij[t][c]), one
 // k-segment per source column.
-template <int N>
+template <int N, int P = 3>
 struct OpBUpd {
     static constexpr bool kBMN = true;
     static constexpr int kN = N;
+    static constexpr int kP = P;
     float* R32;
     int64_t ldr;
     int b, i0, nsrc, j0, nj, Qn, nmb;
@@ -775,26 +790,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn_tg()
 // 32 k, box_rows / 64 column groups, 3 planes}, 128-byte swizzle, which lands
 // as [plane][group][k][n].  The row extent stops two planes short of the
 // array's end, so the plane offset of any in-range coordinate stays inside
-// the allocation.
+// the allocation.  planes < 3 loads only the leading planes of each box.
 bool map_tiles(CUtensorMap* map, const void* p, int64_t rows, int64_t cols, int64_t plane_rows, int box_rows,
-               bool mn = false)
+               bool mn = false, int planes = 3)
 {
     auto enc = encode_fn_tg();
     const int64_t ext = rows - 2 * plane_rows;
-    if (!enc || ((uintptr_t)p & 15) || (cols * 2) % 16 || ext <= 0 || rows >= (1ll << 31) || (mn && cols % 64))
+    if (!enc || ((uintptr_t)p & 15) || (cols * 2) % 16 || ext <= 0 || rows >= (1ll << 31) || (mn && cols % 64) ||
+        planes < 1 || planes > 3)
         return false;
     cuuint32_t es[4] = {1, 1, 1, 1};
     if (!mn) {
         cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)ext, 3};
         cuuint64_t strides[2] = {(cuuint64_t)cols * 2, (cuuint64_t)(plane_rows * cols * 2)};
-        cuuint32_t box[3] = {(cuuint32_t)TG_KS, (cuuint32_t)box_rows, 3u};
+        cuuint32_t box[3] = {(cuuint32_t)TG_KS, (cuuint32_t)box_rows, (cuuint32_t)planes};
         return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(p), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
     cuuint64_t dims[4] = {64, (cuuint64_t)ext, (cuuint64_t)(cols / 64), 3};
     cuuint64_t strides[3] = {(cuuint64_t)cols * 2, 128, (cuuint64_t)(plane_rows * cols * 2)};
-    cuuint32_t box[4] = {64u, (cuuint32_t)TG_KS, (cuuint32_t)(box_rows / 64), 3u};
+    cuuint32_t box[4] = {64u, (cuuint32_t)TG_KS, (cuuint32_t)(box_rows / 64), (cuuint32_t)planes};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(p), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -809,7 +825,8 @@ bool launch(gp_t h, int phase, const CUtensorMap& mA, const CUtensorMap& mB, con
     int dev = 0;
     cudaGetDevice(&dev);
     if (done_dev != dev) {
-        cudaFuncSetAttribute(k_tgemm<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgCfg<Op::kN>::SMEM);
+        cudaFuncSetAttribute(k_tgemm<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TgCfg<Op::kN, Op::kP>::SMEM);
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         done_dev = dev;
     }
@@ -817,7 +834,8 @@ bool launch(gp_t h, int phase, const CUtensorMap& mA, const CUtensorMap& mB, con
     int* err = tc_error_dev();
     if (!err) return false;
     const int grid = units < g_num_sms ? units : g_num_sms;
-    GPK_LAUNCH(h, phase, k_tgemm<Op>, (unsigned)grid, TG_THREADS, TgCfg<Op::kN>::SMEM, mA, mB, op, err);
+    constexpr int smem = TgCfg<Op::kN, Op::kP>::SMEM;
+    GPK_LAUNCH(h, phase, k_tgemm<Op>, (unsigned)grid, TG_THREADS, smem, mA, mB, op, err);
     h->tc_pending = true;
     return true;
 }
@@ -850,25 +868,27 @@ bool update_n(gp_t h, int k0, int nsrc, int j0, int w)
     return launch(h, GP_PH_UPDATE, mA, mB, op, (w * (w - 1) / 2 + w * (T - j0 - w + 1)) * (b / 128) * (b / N));
 }
 
-template <int N>
+template <int N, int P>
 bool diag_w_n(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j)
 {
     const int b = (int)h->b, T = (int)h->T;
     CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->RP, 3 * ldm, b, ldm, 128) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N))
+    if (!map_tiles(&mA, h->RP, 3 * ldm, b, ldm, 128, false, P) ||
+        !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N, false, P))
         return false;
-    OpDiagW<N> op{h->WP, R, vpart, h->Np, ldm, b, (int)j, b / N, (int)(ldm / 128)};
+    OpDiagW<N, P> op{h->WP, R, vpart, h->Np, ldm, b, (int)j, b / N, (int)(ldm / 128)};
     return launch(h, phase, mA, mB, op, (b / N) * (int)(ldm / 128));
 }
 
-template <int N>
+template <int N, int P>
 bool upd_w_n(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni)
 {
     const int b = (int)h->b;
     CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np, ldm, 128) || !map_tiles(&mB, h->LP, lp_rows(h), b, b, N))
+    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np, ldm, 128, false, P) ||
+        !map_tiles(&mB, h->LP, lp_rows(h), b, b, N, false, P))
         return false;
-    OpUpdW<N> op{R, h->Np, b, j0, nsrc, i0, ni, b / N, (int)(ldm / 128)};
+    OpUpdW<N, P> op{R, h->Np, b, j0, nsrc, i0, ni, b / N, (int)(ldm / 128)};
     return launch(h, phase, mA, mB, op, ni * (b / N) * (int)(ldm / 128));
 }
 
@@ -904,25 +924,27 @@ bool lauum_n(gp_t h)
     return launch(h, GP_PH_LAUUM, mA, mB, op, T * (T + 1) / 2 * (b / 128) * (b / N));
 }
 
-template <int N>
+template <int N, int P>
 bool bdiag_n(gp_t h, int64_t ldm, int64_t i)
 {
     const int b = (int)h->b, T = (int)h->T;
     CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->RP, 3 * ldm, b, ldm, 128) || !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N, true))
+    if (!map_tiles(&mA, h->RP, 3 * ldm, b, ldm, 128, false, P) ||
+        !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N, true, P))
         return false;
-    OpBDiag<N> op{h->R32, h->WP, h->Np, ldm, b, (int)i, b / N, (int)(ldm / 128)};
+    OpBDiag<N, P> op{h->R32, h->WP, h->Np, ldm, b, (int)i, b / N, (int)(ldm / 128)};
     return launch(h, GP_PH_BSOLVE, mA, mB, op, (b / N) * (int)(ldm / 128));
 }
 
-template <int N>
+template <int N, int P>
 bool bupd_n(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj)
 {
     const int b = (int)h->b;
     CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np, ldm, 128) || !map_tiles(&mB, h->LP, lp_rows(h), b, b, N, true))
+    if (!map_tiles(&mA, h->WP, 3 * ldm, h->Np, ldm, 128, false, P) ||
+        !map_tiles(&mB, h->LP, lp_rows(h), b, b, N, true, P))
         return false;
-    OpBUpd<N> op{h->R32, h->Np, b, i0, nsrc, j0, nj, b / N, (int)(ldm / 128)};
+    OpBUpd<N, P> op{h->R32, h->Np, b, i0, nsrc, j0, nj, b / N, (int)(ldm / 128)};
     return launch(h, GP_PH_BSOLVE, mA, mB, op, nj * (b / N) * (int)(ldm / 128));
 }
 
@@ -934,15 +956,27 @@ bool tg_update(gp_t h, int k0, int nsrc, int j0, int w)
     return wide(h) ? update_n<256>(h, k0, nsrc, j0, w) : update_n<128>(h, k0, nsrc, j0, w);
 }
 
-bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j)
+// Sweep products with P operand planes: the 128- or 256-wide instantiation.
+template <int P>
+bool diag_w_p(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j)
 {
-    return wide(h) ? diag_w_n<256>(h, phase, R, ldm, vpart, j) : diag_w_n<128>(h, phase, R, ldm, vpart, j);
+    return wide(h) ? diag_w_n<256, P>(h, phase, R, ldm, vpart, j) : diag_w_n<128, P>(h, phase, R, ldm, vpart, j);
 }
-
-bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni)
+template <int P>
+bool upd_w_p(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni)
 {
-    return wide(h) ? upd_w_n<256>(h, phase, R, ldm, j0, nsrc, i0, ni)
-                   : upd_w_n<128>(h, phase, R, ldm, j0, nsrc, i0, ni);
+    return wide(h) ? upd_w_n<256, P>(h, phase, R, ldm, j0, nsrc, i0, ni)
+                   : upd_w_n<128, P>(h, phase, R, ldm, j0, nsrc, i0, ni);
+}
+template <int P>
+bool bdiag_p(gp_t h, int64_t ldm, int64_t i)
+{
+    return wide(h) ? bdiag_n<256, P>(h, ldm, i) : bdiag_n<128, P>(h, ldm, i);
+}
+template <int P>
+bool bupd_p(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj)
+{
+    return wide(h) ? bupd_n<256, P>(h, ldm, i0, nsrc, j0, nj) : bupd_n<128, P>(h, ldm, i0, nsrc, j0, nj);
 }
 
 bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov)
@@ -960,10 +994,22 @@ bool tg_trtri_acc(gp_t h, int t0, int t1, int i0, int ni, int nj)
     return wide(h) ? trtri_acc_n<256>(h, t0, t1, i0, ni, nj) : trtri_acc_n<128>(h, t0, t1, i0, ni, nj);
 }
 bool tg_lauum(gp_t h) { return wide(h) ? lauum_n<256>(h) : lauum_n<128>(h); }
-bool tg_bdiag(gp_t h, int64_t ldm, int64_t i) { return wide(h) ? bdiag_n<256>(h, ldm, i) : bdiag_n<128>(h, ldm, i); }
-bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj)
+bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j, int planes)
 {
-    return wide(h) ? bupd_n<256>(h, ldm, i0, nsrc, j0, nj) : bupd_n<128>(h, ldm, i0, nsrc, j0, nj);
+    return planes == 2 ? diag_w_p<2>(h, phase, R, ldm, vpart, j) : diag_w_p<3>(h, phase, R, ldm, vpart, j);
+}
+bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni, int planes)
+{
+    return planes == 2 ? upd_w_p<2>(h, phase, R, ldm, j0, nsrc, i0, ni)
+                       : upd_w_p<3>(h, phase, R, ldm, j0, nsrc, i0, ni);
+}
+bool tg_bdiag(gp_t h, int64_t ldm, int64_t i, int planes)
+{
+    return planes == 2 ? bdiag_p<2>(h, ldm, i) : bdiag_p<3>(h, ldm, i);
+}
+bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj, int planes)
+{
+    return planes == 2 ? bupd_p<2>(h, ldm, i0, nsrc, j0, nj) : bupd_p<3>(h, ldm, i0, nsrc, j0, nj);
 }
 
 }  // namespace gpk
