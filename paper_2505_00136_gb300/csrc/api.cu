@@ -560,7 +560,7 @@ void gp_destroy(gp_t h)
     void* ptrs[] = {h->X, h->y, h->hyp, h->adam, h->L, h->Linv, h->beta, h->alpha, h->work,
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
-                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->xprev, h->pg_ws, h->norms, h->R32, h->RP,
+                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->xprev, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
                     h->dag_upd, h->dag_fin, h->OGP, h->OGS, h->og_mu, h->OGL, h->ogl_mu, h->OGT, h->OGTS, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->OGVS, h->ogv_mu,
@@ -657,7 +657,6 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(cuda_status(h, cudaMemset(h->solve_flags, 0, 2 * sizeof(int))));
         TRY(dev_alloc(h, &h->res, h->Np));
         TRY(dev_alloc(h, &h->xprev, h->Np));
-        TRY(dev_alloc(h, &h->pg_ws, 2 * bb));
         TRY(dev_alloc(h, &h->norms, 2));
         TRY(dev_alloc(h, &h->kappa, 1));
         h->tc_dist = gpk::use_tc_dist(h);

@@ -81,7 +81,6 @@ struct gp_handle {
     float *r32, *t32, *w32;   // FP32 vectors of the refinement solves (w32: b / 64 copies of Np)
     double* res;              // Np FP64 residual
     double* xprev;            // Np: the refinement's previous iterate
-    double* pg_ws;            // 2 b^2: FP64 work space of the diagonal-tile factor
     double* norms;            // 2 FP64 norms
     float* R32;               // m_cap x Np: K_{Z*,Z}, overwritten by the W solve
     __nv_bfloat16 *RP, *WP;   // planes: RP 3 x m_cap x b (scratch), WP 3 x m_cap x Np (all of W)
@@ -200,10 +199,11 @@ void potrf_diag_launch(gp_t h, double* A, double* X, int64_t b, int64_t row0, do
 // The same on the whole GPU (one cooperative launch, bounded grid barriers on
 // h->solve_flags); b a multiple of 32.  False if it cannot be launched.
 bool potrf_diag_grid(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot);
-// The same for an FP32 tile (GP_MIXED), factored in FP64 in work (2 b^2
-// doubles): A32 (lower, in place) = L, X32 = L^{-1}, XP = its three BF16 planes.
-bool potrf_diag_grid32(gp_t h, float* A32, float* X32, __nv_bfloat16* XP, double* work, int64_t b, int64_t row0,
-                       double* logdet_slot);
+// FP32 factor and inverse of an FP32 tile on one cluster of eight CTAs
+// (kernels_potrf_cl.cu): A32 (lower, in place) = L, X32 = L^{-1}, XP = its
+// three BF16 planes, sum log L_jj (FP64) into *logdet_slot; b a multiple of 32.
+bool potrf_diag_cl32(gp_t h, float* A32, float* X32, __nv_bfloat16* XP, int64_t b, int64_t row0,
+                     double* logdet_slot);
 void factor_dag(gp_t h, bool reset_err);                       // persistent tile-DAG factor (FP64)
 
 // kernels_mixed.cu

@@ -5,9 +5,9 @@
 //    the gradient) and in FP32 (working copy).
 //  - Tiled right-looking Cholesky (Fig. 1) on the FP32 copy, in super-panels
 //    of SWEEP_BLOCK tile columns: each diagonal tile is factored and inverted
-//    in FP32 by one CTA (k_potrf32), the panel TRSM (L_ik = A_ik Linv_kk^T)
-//    and the trailing SYRK/GEMM run as bf16x6 products with FP32 accumulation
-//    on the tensor cores (kernels_tgemm.cu).  Every finished off-diagonal
+//    in FP32 by one cluster of eight CTAs (kernels_potrf_cl.cu), the panel
+//    TRSM (L_ik = A_ik Linv_kk^T) and the trailing SYRK/GEMM run as bf16x6
+//    products with FP32 accumulation on the tensor cores (kernels_tgemm.cu).  Every finished off-diagonal
 //    tile of L is also kept as three BF16 planes, the operand format of later
 //    products.
 //  - log|K| = 2 sum log L_jj, the logarithms taken and summed in FP64.
@@ -34,321 +34,6 @@
 namespace gpk {
 
 constexpr int NTH = 256;
-
-// ---------------------------------------------------------------- FP32 diagonal-tile factor
-// 64 x 64 FP32 block product for the diagonal tile: acc(r, c) += sum over k in
-// [kb, ke) of A(r, k) B(c, k), element (row, k) of a view at p[row*sr + k*sk].
-// 256 threads as 16 x 16, thread (tr, tc) owns rows 4 tr + i, columns 4 tc + j,
-// so one k step reads its operands with two 16-byte shared-memory loads.
-struct SView {
-    const float* p;
-    int64_t sr, sk;
-};
-
-constexpr int SG_KC = 32;                     // k per shared-memory chunk
-constexpr int SG_LD = 68;                     // padded row of a k-major chunk (16-byte aligned)
-constexpr int SG_FLOATS = 2 * SG_KC * SG_LD;  // A and B chunks, k-major, padded
-
-constexpr int SG_PER = 64 * SG_KC / NTH;   // elements of one chunk per thread
-
-__device__ __forceinline__ void sg_index(const SView& v, int e, int& r, int& kk)
-{
-    if (v.sk == 1) { r = e / SG_KC; kk = e % SG_KC; }
-    else           { kk = e / 64;   r = e % 64; }
-}
-
-__device__ __forceinline__ void sg_load(const SView& v, int64_t k0, int64_t ke, float (&t)[SG_PER])
-{
-#pragma unroll
-    for (int i = 0; i < SG_PER; ++i) {
-        int r, kk;
-        sg_index(v, threadIdx.x + i * NTH, r, kk);
-        t[i] = (k0 + kk < ke) ? __ldcg(v.p + (int64_t)r * v.sr + (k0 + kk) * v.sk) : 0.f;
-    }
-}
-
-__device__ __forceinline__ void sg_store(const SView& v, const float (&t)[SG_PER], float* dst)
-{
-#pragma unroll
-    for (int i = 0; i < SG_PER; ++i) {
-        int r, kk;
-        sg_index(v, threadIdx.x + i * NTH, r, kk);
-        dst[kk * SG_LD + r] = t[i];
-    }
-}
-
-__device__ void sgemm64(float (&acc)[4][4], const SView& A, const SView& B, int64_t kb, int64_t ke, float* sm)
-{
-    float* As = sm;
-    float* Bs = sm + SG_KC * SG_LD;
-    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-    float ta[SG_PER], tb[SG_PER];   // the next chunk's loads, in flight during this chunk's products
-    __syncthreads();                // the operands may be the block's own writes just before the call
-    if (kb < ke) {
-        sg_load(A, kb, ke, ta);
-        sg_load(B, kb, ke, tb);
-    }
-    for (int64_t k0 = kb; k0 < ke; k0 += SG_KC) {
-        __syncthreads();
-        sg_store(A, ta, As);
-        sg_store(B, tb, Bs);
-        __syncthreads();
-        if (k0 + SG_KC < ke) {
-            sg_load(A, k0 + SG_KC, ke, ta);
-            sg_load(B, k0 + SG_KC, ke, tb);
-        }
-#pragma unroll 8
-        for (int kk = 0; kk < SG_KC; ++kk) {
-            const float4 a4 = *reinterpret_cast<const float4*>(As + kk * SG_LD + 4 * tr);
-            const float4 b4 = *reinterpret_cast<const float4*>(Bs + kk * SG_LD + 4 * tc);
-            const float a[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
-        }
-    }
-    __syncthreads();
-}
-
-// f(row, first column, the thread's four consecutive results of that row)
-template <class F>
-__device__ __forceinline__ void sacc_rows(const float (&acc)[4][4], F&& f)
-{
-    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) f(4 * tr + i, 4 * tc, make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
-}
-
-__device__ __forceinline__ void sub4_cg(float* q, const float4& v)   // *q -= v, q 16-byte aligned
-{
-    float4 o = __ldcg(reinterpret_cast<const float4*>(q));
-    o.x -= v.x;
-    o.y -= v.y;
-    o.z -= v.z;
-    o.w -= v.w;
-    *reinterpret_cast<float4*>(q) = o;
-}
-
-__device__ __forceinline__ void sacc_zero(float (&acc)[4][4])
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-}
-
-// Step j of the register-resident 64 x 64 factor (one warp, lane l holds
-// row l in ra and row l + 32 in rb): pivot, scale column j, rank-1 update of
-// the later columns.  bad = first non-positive pivot.
-template <int J>
-__device__ __forceinline__ void chol64_step(float (&ra)[32], float (&rb)[64], int l, int& bad)
-{
-    const float d = __shfl_sync(0xffffffffu, J < 32 ? ra[J & 31] : rb[J], J & 31);
-    if (!(d > 0.f) && bad < 0) bad = J;
-    const float dj = sqrtf(d), dinv = 1.f / dj;
-    if (J < 32) ra[J & 31] = (l == J) ? dj : ra[J & 31] * dinv;
-    rb[J] = (l + 32 == J) ? dj : rb[J] * dinv;
-#pragma unroll
-    for (int c = J + 1; c < 64; ++c) {
-        const float lc = __shfl_sync(0xffffffffu, c < 32 ? ra[J & 31] : rb[J], c & 31);
-        if (c < 32) ra[c & 31] = fmaf(-ra[J & 31], lc, ra[c & 31]);
-        rb[c] = fmaf(-rb[J], lc, rb[c]);
-    }
-}
-
-template <int... J>
-__device__ __forceinline__ void chol64_steps(float (&ra)[32], float (&rb)[64], int l, int& bad,
-                                             std::integer_sequence<int, J...>)
-{
-    (chol64_step<J>(ra, rb, l, bad), ...);
-}
-
-// Row r of the forward substitution L x = e_c (L in S, row stride 65).
-template <int R>
-__device__ __forceinline__ void trinv64_row(const float* S, int c, float (&x)[64])
-{
-    float s4[4] = {(R == c) ? 1.f : 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int t = 0; t < R; ++t) s4[t & 3] = fmaf(-S[R * 65 + t], x[t], s4[t & 3]);
-    x[R] = ((s4[0] + s4[1]) + (s4[2] + s4[3])) / S[R * 65 + R];
-}
-
-template <int... R>
-__device__ __forceinline__ void trinv64_rows(const float* S, int c, float (&x)[64], std::integer_sequence<int, R...>)
-{
-    (trinv64_row<R>(S, c, x), ...);
-}
-
-constexpr int POTRF32_SMEM = (2 * 64 * 65 + SG_FLOATS) * 4;
-
-// Cholesky factor and inverse of one b x b diagonal tile in FP32 (one CTA):
-// A (lower tile, in place) = L_kk with a zero upper triangle, X = L_kk^{-1},
-// XP = the three BF16 planes of X, *logdet_slot = sum of log L_jj in FP64.
-// 64-blocks inside the tile, left-looking: A_pp -= A_p,<p A_p,<p^T, unblocked
-// factor and inverse of the 64-block, panel A_rp = (A_rp - A_r,<p A_p,<p^T)
-// L_pp^{-T}; then X_rq = -X_rr sum_{t=q}^{r-1} L_rt X_tq.  A non-positive
-// pivot records its global row in *info.
-__global__ __launch_bounds__(NTH) void k_potrf32(float* A, float* X, __nv_bfloat16* XP, int64_t b, int64_t row0,
-                                                 double* logdet_slot, unsigned long long* info)
-{
-    extern __shared__ __align__(16) float fsm[];
-    float* S = fsm;
-    float* Iv = S + 64 * 65;
-    float* gsm = Iv + 64 * 65;
-    __shared__ double logacc;
-    __shared__ int fail;
-    if (failed(info)) return;
-    const int tid = threadIdx.x;
-    const int P = (int)(b / 64);
-    if (tid == 0) { logacc = 0.0; fail = 0; }
-    for (int p = 0; p < P; ++p) {
-        float* App = A + (int64_t)p * 64 * b + p * 64;
-        if (p > 0) {
-            float acc[4][4];
-            sacc_zero(acc);
-            const SView va{A + (int64_t)p * 64 * b, b, 1};
-            sgemm64(acc, va, va, 0, (int64_t)p * 64, gsm);
-            sacc_rows(acc, [&](int r, int c, const float4& v) { sub4_cg(App + (int64_t)r * b + c, v); });
-        }
-        __syncthreads();
-        {   // the 64-block's lower triangle into S, all loads in flight first
-            float t[64 * 64 / NTH];
-#pragma unroll
-            for (int i = 0; i < 64 * 64 / NTH; ++i) {
-                const int e = tid + i * NTH, r = e >> 6, c = e & 63;
-                t[i] = (c <= r) ? __ldcg(App + (int64_t)r * b + c) : 0.f;
-            }
-#pragma unroll
-            for (int i = 0; i < 64 * 64 / NTH; ++i) {
-                const int e = tid + i * NTH;
-                S[(e >> 6) * 65 + (e & 63)] = t[i];
-            }
-        }
-        __syncthreads();
-        // Unblocked right-looking factor of the 64-block in the registers of
-        // warp 0: lane l holds row l (columns 0..31) and row l + 32; the
-        // multipliers L(c, j) of column j are broadcast by shuffles.  Entries
-        // above the diagonal are scratch and written back as zero.
-        if (tid < 32) {
-            const int l = tid;
-            float ra[32], rb[64];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) ra[c] = S[l * 65 + c];
-#pragma unroll
-            for (int c = 0; c < 64; ++c) rb[c] = S[(l + 32) * 65 + c];
-            int bad = -1;
-            chol64_steps(ra, rb, l, bad, std::make_integer_sequence<int, 64>{});
-            if (bad >= 0) {   // the same pivot on every lane
-                if (l == 0) {
-                    fail = 1;
-                    atomicMin(info, (unsigned long long)(row0 + p * 64 + bad));
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < 32; ++c) S[l * 65 + c] = (c <= l) ? ra[c] : 0.f;
-#pragma unroll
-                for (int c = 0; c < 64; ++c) S[(l + 32) * 65 + c] = (c <= l + 32) ? rb[c] : 0.f;
-            }
-        }
-        __syncthreads();
-        if (fail) return;
-        if (tid < 32) {
-            double lg = log((double)S[tid * 65 + tid]) + log((double)S[(tid + 32) * 65 + tid + 32]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
-            if (tid == 0) logacc += lg;
-        }
-        // Inverse of the 64-block factor: thread c solves L x = e_c by forward
-        // substitution in registers (x(r) = 0 for r < c falls out exactly).
-        if (tid < 64) {
-            const int c = tid;
-            float x[64];
-            trinv64_rows(S, c, x, std::make_integer_sequence<int, 64>{});
-#pragma unroll
-            for (int r = 0; r < 64; ++r) Iv[r * 65 + c] = x[r];
-        }
-        __syncthreads();
-        float* Xpp = X + (int64_t)p * 64 * b + p * 64;
-        for (int e = tid; e < 64 * 64; e += NTH) {
-            const int r = e >> 6, c = e & 63;
-            App[(int64_t)r * b + c] = S[r * 65 + c];
-            Xpp[(int64_t)r * b + c] = Iv[r * 65 + c];
-        }
-        __syncthreads();
-        for (int r = p + 1; r < P; ++r) {
-            float* Arp = A + (int64_t)r * 64 * b + p * 64;
-            if (p > 0) {
-                float acc[4][4];
-                sacc_zero(acc);
-                sgemm64(acc, SView{A + (int64_t)r * 64 * b, b, 1}, SView{A + (int64_t)p * 64 * b, b, 1}, 0,
-                        (int64_t)p * 64, gsm);
-                sacc_rows(acc, [&](int rr, int c, const float4& v) { sub4_cg(Arp + (int64_t)rr * b + c, v); });
-            }
-            float acc[4][4];
-            sacc_zero(acc);
-            sgemm64(acc, SView{Arp, b, 1}, SView{Xpp, b, 1}, 0, 64, gsm);
-            sacc_rows(acc, [&](int rr, int c, const float4& v) {
-                *reinterpret_cast<float4*>(Arp + (int64_t)rr * b + c) = v;
-            });
-        }
-    }
-    __syncthreads();
-    // strictly upper 64-blocks of L and X are zero (the diagonal blocks were written whole)
-    for (int q = 0; q < P; ++q)
-        for (int pc = q + 1; pc < P; ++pc)
-            for (int e = tid; e < 64 * 64; e += NTH) {
-                const int64_t o = (int64_t)(q * 64 + (e >> 6)) * b + pc * 64 + (e & 63);
-                A[o] = 0.f;
-                X[o] = 0.f;
-            }
-    for (int r = 1; r < P; ++r) {
-        for (int q = 0; q < r; ++q) {
-            float* Xrq = X + (int64_t)r * 64 * b + q * 64;
-            float acc[4][4];
-            sacc_zero(acc);
-            sgemm64(acc, SView{A + (int64_t)r * 64 * b, b, 1}, SView{X + q * 64, 1, b}, (int64_t)q * 64,
-                    (int64_t)r * 64, gsm);
-            sacc_rows(acc, [&](int rr, int c, const float4& v) {
-                *reinterpret_cast<float4*>(Xrq + (int64_t)rr * b + c) = v;
-            });
-            sacc_zero(acc);
-            sgemm64(acc, SView{X + (int64_t)r * 64 * b + r * 64, b, 1}, SView{Xrq, 1, b}, 0, 64, gsm);
-            sacc_rows(acc, [&](int rr, int c, const float4& v) {
-                *reinterpret_cast<float4*>(Xrq + (int64_t)rr * b + c) = make_float4(-v.x, -v.y, -v.z, -v.w);
-            });
-        }
-    }
-    __syncthreads();
-    const int64_t bb = b * b, q4 = bb / 4;
-    for (int64_t e0 = tid; e0 < q4; e0 += 8 * NTH) {   // planes of X, eight float4 loads in flight
-        float4 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t e = e0 + i * NTH;
-            v[i] = e < q4 ? __ldcg(reinterpret_cast<const float4*>(X) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t e = e0 + i * NTH;
-            if (e >= q4) continue;
-            const float f[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-            __nv_bfloat16 h[3][4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) split3(f[u], h[0][u], h[1][u], h[2][u]);
-#pragma unroll
-            for (int pl = 0; pl < 3; ++pl) {
-                __nv_bfloat162 lo2 = __halves2bfloat162(h[pl][0], h[pl][1]);
-                __nv_bfloat162 hi2 = __halves2bfloat162(h[pl][2], h[pl][3]);
-                uint2 w;
-                w.x = *reinterpret_cast<unsigned*>(&lo2);
-                w.y = *reinterpret_cast<unsigned*>(&hi2);
-                reinterpret_cast<uint2*>(XP + pl * bb)[e] = w;
-            }
-        }
-    }
-    if (tid == 0) *logdet_slot = logacc;
-}
 
 // Planes of the panel tiles A32_(i,k), i = k+1..T-1, into PA (one slot per tile).
 __global__ void k_split_panel(const float* A32, __nv_bfloat16* PA, int64_t b, int64_t k)
@@ -967,16 +652,6 @@ static int grid_for(int64_t work, int per = NTH)
     return (int)g;
 }
 
-static void ensure_attrs_mixed()
-{
-    static int done_dev = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (done_dev == dev) return;
-    cudaFuncSetAttribute(k_potrf32, cudaFuncAttributeMaxDynamicSharedMemorySize, POTRF32_SMEM);
-    done_dev = dev;
-}
-
 // Operand planes of the three multi-RHS sweeps of a prediction.  W =
 // K_{Z*,Z} L~^{-T} feeds x0 and the full covariance and keeps all three
 // planes (FP32 accuracy).  The backward sweep x0^T = W L~^{-1} and the forward
@@ -995,32 +670,21 @@ constexpr int SWEEP_PLANES_R = 2;
 // column), so it is read and written T / SWEEP_BLOCK times, not T.
 constexpr int SWEEP_BLOCK = 4;
 
-// Diagonal tiles: FP32 factor and inverse on one SM (k_potrf32, 0.32 ms per
-// tile of 256) or the FP64 factor spread over the GPU (potrf_diag_grid32,
-// measured 0.71 ms per tile).
-constexpr bool MIXED_DIAG_FP64 = false;
-
 // Right-looking, in super-panels of SWEEP_BLOCK tile columns: each column k
 // of a super-panel is factored (diagonal tile, panel) and applied only to the
 // super-panel's later columns; then one update with a k-segment per column
 // applies the whole super-panel to the trailing triangle.
 bool factor_mixed(gp_t h)
 {
-    ensure_attrs_mixed();
     const int T = (int)h->T;
     const int64_t b = h->b, bb = b * b;
     for (int K0 = 0; K0 < T; K0 += SWEEP_BLOCK) {
         const int e = K0 + SWEEP_BLOCK < T ? K0 + SWEEP_BLOCK : T;
         for (int k = K0; k < e; ++k) {
-            if (MIXED_DIAG_FP64) {
-                if (!potrf_diag_grid32(h, h->A32 + tri_index(k, k) * bb, h->Linv32 + k * bb,
-                                       h->LinvP + k * 3 * bb, h->pg_ws, b, (int64_t)k * b, h->logdet_part + k))
-                    return false;
-            } else {
-                GPK_LAUNCH(h, GP_PH_POTRF, k_potrf32, 1, NTH, POTRF32_SMEM, h->A32 + tri_index(k, k) * bb,
-                           h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b, (int64_t)k * b, h->logdet_part + k,
-                           h->info);
-            }
+            // diagonal tile: FP32 factor and inverse on one cluster of eight CTAs
+            if (!potrf_diag_cl32(h, h->A32 + tri_index(k, k) * bb, h->Linv32 + k * bb, h->LinvP + k * 3 * bb, b,
+                                 (int64_t)k * b, h->logdet_part + k))
+                return false;
             if (k + 1 < T) {
                 const unsigned tt = (unsigned)(T - k - 1);
                 GPK_LAUNCH(h, GP_PH_TRSM, k_split_panel, dim3((unsigned)grid_for(bb) / 4 + 1, tt), NTH, 0,
@@ -1130,7 +794,6 @@ static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase, i
 
 bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var, bool want_cov)
 {
-    ensure_attrs_mixed();
     const int64_t Np = h->Np;
     const int64_t nmp = Np / 64, nvp = Np / 64;   // variance partials: one slot per 64 columns
     if (h->tc_dist) {   // squared distances on the tensor cores, origin at the first training row
@@ -1154,7 +817,6 @@ bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var, bool want_cov)
 // holds W, R64 holds K_{Z*,Z}).  Overwrites the W planes (run after full_cov_mixed).
 bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 {
-    ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, Np = h->Np;
     // x0^T = W L~^{-1}: backward sweep over tile columns, in place over R32, in
     // blocks of SWEEP_BLOCK columns; Y planes go to the W plane buffer
@@ -1184,7 +846,6 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 
 bool full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)
 {
-    ensure_attrs_mixed();
     if (h->tc_dist) {   // test digits again, origin at the first test row (test-test distances only)
         zslices(h, h->Xs, h->Xs, ldm, m, h->ZSS, h->zs_mu, h->zs_nrm, GP_PH_COV);
         if (!dist_prior_tc(h, m, ldm, cov)) return false;
@@ -1196,7 +857,6 @@ bool full_cov_mixed(gp_t h, int64_t m, int64_t ldm, double* cov)
 
 bool inverse_mixed(gp_t h)
 {
-    ensure_attrs_mixed();
     const int64_t T = h->T, b = h->b, bb = b * b;
     GPK_LAUNCH(h, GP_PH_TRTRI, k_zdiag, dim3((unsigned)grid_for(bb) / 4 + 1, (unsigned)T), NTH, 0,
                (const float*)h->Linv32, h->ZP, b);

@@ -1,5 +1,5 @@
 // FP64 Cholesky factor and inverse of one diagonal tile, spread over the
-// whole GPU (GP_FP64_OZAKI, and GP_MIXED on its FP32 tiles).
+// whole GPU (GP_FP64_OZAKI).
 //
 // On this part one SM retires about 1.7 FP64 FMAs per clock, so the b x b
 // diagonal tile's factor and inverse (b^3 / 3 FMAs, 5.6e6 at b = 256) take
@@ -31,7 +31,6 @@
 
 #include "gp_internal.cuh"
 #include "se_common.cuh"
-#include "split_bf16.cuh"
 
 namespace gpk {
 namespace {
@@ -51,12 +50,6 @@ struct PgArgs {
     unsigned* bar;              // arrival count, generation (zeroed before the launch)
     int* err;
     long long limit;            // bound on one barrier wait, in SM clock cycles
-    // FP32 tile (GP_MIXED): A and X are then FP64 work space; the tile A32
-    // (lower triangle read) is copied into A first, and on return holds L;
-    // X32 = L^{-1}, XP = the three BF16 planes of X32 (plane q at XP + q b^2).
-    float* A32;
-    float* X32;
-    __nv_bfloat16* XP;
 };
 
 __device__ bool pg_barrier(const PgArgs& a, int* okb)
@@ -221,7 +214,6 @@ __device__ bool pg_diag(const PgArgs& a, int p, double* S, double* Iv, double* l
     return true;
 }
 
-template <bool F32>
 __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
 {
     __shared__ double As[PG_ROWS * PG_LD];
@@ -244,11 +236,6 @@ __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
     const int P = (int)(a.b / PG_NB);
     const int64_t b = a.b;
     const int units_per_blk = PG_NB / PG_ROWS;
-    if (F32) {   // the FP32 tile into the FP64 work space
-        for (int64_t e = (int64_t)blockIdx.x * PG_TH + tid; e < b * b; e += (int64_t)gridDim.x * PG_TH)
-            a.A[e] = (double)__ldcg(a.A32 + e);
-        if (!pg_barrier(a, &okb)) return;
-    }
 
     for (int p = 0; p < P; ++p) {
         if (blockIdx.x == 0) pg_diag(a, p, S, Iv, &logacc, &fail);
@@ -338,16 +325,7 @@ __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
     // strict upper triangles of L and X are zero (X's held the products T)
     for (int64_t e = (int64_t)blockIdx.x * PG_TH + tid; e < b * b; e += (int64_t)gridDim.x * PG_TH) {
         const int64_t rr = e / b, cc = e % b;
-        if (F32) {
-            const float lv = cc > rr ? 0.f : (float)a.A[e], xv = cc > rr ? 0.f : (float)a.X[e];
-            a.A32[e] = lv;
-            a.X32[e] = xv;
-            __nv_bfloat16 hi, mid, lo;
-            split3(xv, hi, mid, lo);
-            a.XP[e] = hi;
-            a.XP[b * b + e] = mid;
-            a.XP[2 * b * b + e] = lo;
-        } else if (cc > rr) {
+        if (cc > rr) {
             a.A[e] = 0.0;
             a.X[e] = 0.0;
         }
@@ -357,10 +335,8 @@ __global__ __launch_bounds__(PG_TH) void k_potrf_grid(const PgArgs a)
 
 }  // namespace
 
-namespace {
-
-template <bool F32>
-bool potrf_grid_launch(gp_t h, PgArgs& a)
+// One cooperative launch per diagonal tile; b must be a multiple of 32.
+bool potrf_diag_grid(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot)
 {
     static int grid_dev = -1, grid_blocks = 0;
     int dev = 0;
@@ -368,11 +344,17 @@ bool potrf_grid_launch(gp_t h, PgArgs& a)
     if (grid_dev != dev) {   // every CTA resident at once: the blocks wait on one another
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_potrf_grid<F32>, PG_TH, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_potrf_grid, PG_TH, 0);
         grid_blocks = per >= 1 ? sms : 0;   // one CTA per SM: the FP64 pipe, not occupancy, sets the pace
         grid_dev = dev;
     }
-    if (grid_blocks < 1 || a.b % PG_NB || a.b < PG_NB) return false;
+    if (grid_blocks < 1 || b % PG_NB || b < PG_NB) return false;
+    PgArgs a{};
+    a.A = A;
+    a.X = X;
+    a.b = b;
+    a.row0 = row0;
+    a.logdet_slot = logdet_slot;
     a.info = h->info;
     a.bar = (unsigned*)h->solve_flags;
     a.err = tc_error_dev();
@@ -382,41 +364,11 @@ bool potrf_grid_launch(gp_t h, PgArgs& a)
     cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), h->st);   // fresh barrier words
     const bool p_ = h->prof_on && prof_begin(h, GP_PH_POTRF);
     // a failed launch leaves its error for the caller's check of the last launch error
-    cudaLaunchCooperativeKernel((const void*)k_potrf_grid<F32>, dim3((unsigned)grid_blocks), dim3(PG_TH), args, 0,
-                                h->st);
+    cudaLaunchCooperativeKernel((const void*)k_potrf_grid, dim3((unsigned)grid_blocks), dim3(PG_TH), args, 0, h->st);
     h->launches++;
     if (p_) prof_end(h);
     h->tc_pending = true;
     return true;
-}
-
-}  // namespace
-
-// One cooperative launch per diagonal tile; b must be a multiple of 32.
-bool potrf_diag_grid(gp_t h, double* A, double* X, int64_t b, int64_t row0, double* logdet_slot)
-{
-    PgArgs a{};
-    a.A = A;
-    a.X = X;
-    a.b = b;
-    a.row0 = row0;
-    a.logdet_slot = logdet_slot;
-    return potrf_grid_launch<false>(h, a);
-}
-
-bool potrf_diag_grid32(gp_t h, float* A32, float* X32, __nv_bfloat16* XP, double* work, int64_t b, int64_t row0,
-                       double* logdet_slot)
-{
-    PgArgs a{};
-    a.A = work;
-    a.X = work + b * b;
-    a.b = b;
-    a.row0 = row0;
-    a.logdet_slot = logdet_slot;
-    a.A32 = A32;
-    a.X32 = X32;
-    a.XP = XP;
-    return potrf_grid_launch<true>(h, a);
 }
 
 }  // namespace gpk
