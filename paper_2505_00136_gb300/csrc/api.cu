@@ -560,7 +560,7 @@ void gp_destroy(gp_t h)
     void* ptrs[] = {h->X, h->y, h->hyp, h->adam, h->L, h->Linv, h->beta, h->alpha, h->work,
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
-                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->xprev, h->norms, h->R32, h->RP,
+                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->xprev, h->Xsb, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
                     h->dag_upd, h->dag_fin, h->OGP, h->OGS, h->og_mu, h->OGL, h->ogl_mu, h->OGT, h->OGTS, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->OGVS, h->ogv_mu,
@@ -652,7 +652,9 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(dev_alloc(h, &h->PA, 3 * (h->T > 1 ? h->T - 1 : 1) * bb));
         TRY(dev_alloc(h, &h->r32, h->Np));
         TRY(dev_alloc(h, &h->t32, h->Np));
-        TRY(dev_alloc(h, &h->w32, h->Np * (h->b >= 64 ? h->b / 64 : 1)));   // partial sums of the solves
+        TRY(dev_alloc(h, &h->w32, h->Np * gpk::GP_SOLVE_SB));   // partial sums of the solves (one copy per tile of a super-block)
+        TRY(dev_alloc(h, &h->Xsb, (h->T + gpk::GP_SOLVE_SB - 1) / gpk::GP_SOLVE_SB * (gpk::GP_SOLVE_SB * h->b) *
+                                      (gpk::GP_SOLVE_SB * h->b)));
         TRY(dev_alloc(h, &h->solve_flags, 2));
         TRY(cuda_status(h, cudaMemset(h->solve_flags, 0, 2 * sizeof(int))));
         TRY(dev_alloc(h, &h->res, h->Np));

@@ -81,6 +81,7 @@ struct gp_handle {
     float *r32, *t32, *w32;   // FP32 vectors of the refinement solves (w32: b / 64 copies of Np)
     double* res;              // Np FP64 residual
     double* xprev;            // Np: the refinement's previous iterate
+    float* Xsb;               // inverses of the super-blocks of GP_SOLVE_SB diagonal tiles, (GP_SOLVE_SB b)^2 each
     double* norms;            // 2 FP64 norms
     float* R32;               // m_cap x Np: K_{Z*,Z}, overwritten by the W solve
     __nv_bfloat16 *RP, *WP;   // planes: RP 3 x m_cap x b (scratch), WP 3 x m_cap x Np (all of W)
@@ -244,6 +245,7 @@ bool dist_cross_tc(gp_t h, int64_t m, int64_t ldm);             // R32, R64, mea
 bool dist_prior_tc(gp_t h, int64_t m, int64_t ldm, double* out);   // K_{Z*,Z*} (m x m)
 bool tg_bdiag(gp_t h, int64_t ldm, int64_t i, int planes);      // Y_i = S_i Linv_ii (NN form)
 bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj, int planes);   // S_j -= sum Y_i L_ij (NN form)
+constexpr int GP_SOLVE_SB = 4;                                 // tiles per super-block of the FP32 solves
 constexpr int GP_OZ_SLICES = 6;                                // digit slices of K (kernels_mixed.cu)
 constexpr int GP_OZ_YSLICES = 2;                               // digit slices of x~0: x0 rounded to 14 bits per row
 constexpr int GP_OZ_BITS = 7;                                   // bits per signed digit: |d| <= 2^7, exact in BF16

@@ -52,22 +52,138 @@ __global__ void k_split_panel(const float* A32, __nv_bfloat16* PA, int64_t b, in
     }
 }
 
+// ---------------------------------------------------------------- FP32 triangular solves
+// The refinement's solves run in super-blocks of SB_TILES diagonal tiles
+// (edge B = SB_TILES b): the T-step recurrence over tiles becomes a
+// ceil(T / SB_TILES)-step recurrence over super-blocks, each step one
+// product with the super-block's inverse X_I = L~_II^{-1} and one sweep of
+// the factor's rows below (or columns left of) it.  X_I is built once per
+// factorisation from the tile inverses by recursive doubling, exactly as the
+// tile inverses are built from 32-blocks: groups of w tiles merge pairwise,
+// X_CA = -X_CC (L_CA X_AA), with the product T = L_CA X_AA kept in the
+// (otherwise unused) upper tiles of X_I.  Each X_I is dense row-major with
+// row stride B; only its lower tiles are read by the solves.
+constexpr int SB_TILES = GP_SOLVE_SB;
+
+// acc += A (64 x K, row stride lda) * B (K x 64, row stride ldb), FP32; 256
+// threads, thread (tr, tc) owns rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3.
+// K a multiple of 32; both operands 16-byte aligned rows.
+constexpr int SBG_LD = 68;   // padded k-major chunk row (16-byte aligned)
+__device__ void sb_gemm64(float (&acc)[4][4], const float* A, int64_t lda, const float* B, int64_t ldb, int64_t K,
+                          float* As, float* Bs)
+{
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    for (int64_t k0 = 0; k0 < K; k0 += 32) {
+        float4 a[2], bv[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int e = tid + q * NTH;               // 512 float4 of each chunk
+            const int ar = e >> 3, ak = (e & 7) * 4;   // A: 64 rows x 8 float4
+            a[q] = __ldcg((const float4*)(A + (int64_t)ar * lda + k0 + ak));
+            const int bk = e >> 4, bc = (e & 15) * 4;  // B: 32 rows x 16 float4
+            bv[q] = __ldcg((const float4*)(B + (k0 + bk) * ldb + bc));
+        }
+        __syncthreads();   // the previous chunk is no longer read
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int e = tid + q * NTH;
+            const int ar = e >> 3, ak = (e & 7) * 4;
+            As[(ak + 0) * SBG_LD + ar] = a[q].x;
+            As[(ak + 1) * SBG_LD + ar] = a[q].y;
+            As[(ak + 2) * SBG_LD + ar] = a[q].z;
+            As[(ak + 3) * SBG_LD + ar] = a[q].w;
+            const int bk = e >> 4, bc = (e & 15) * 4;
+            *(float4*)(Bs + bk * SBG_LD + bc) = bv[q];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            const float4 a4 = *(const float4*)(As + kk * SBG_LD + 4 * tr);
+            const float4 b4 = *(const float4*)(Bs + kk * SBG_LD + 4 * tc);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bw[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bw[y], acc[x][y]);
+        }
+    }
+}
+
+// Diagonal tiles of every X_I: the tile inverses.
+__global__ void k_sbinv_diag(const float* Linv32, float* Xsb, int64_t b, int64_t T)
+{
+    const int64_t t = blockIdx.y, I = t / SB_TILES, r = t % SB_TILES, SBb = SB_TILES * b;
+    const float* src = Linv32 + t * b * b;
+    float* dst = Xsb + I * SBb * SBb + r * b * SBb + r * b;
+    for (int64_t e = (int64_t)blockIdx.x * NTH + threadIdx.x; e < b * b; e += (int64_t)gridDim.x * NTH)
+        dst[(e / b) * SBb + e % b] = __ldcg(src + e);
+}
+
+// One phase of the recursive doubling at group width w for every
+// super-block: grid (b / 64)^2 sub-tiles x pairs (i in C, j in A) x
+// super-blocks.  Phase 1: T(i, j) = sum_{k=j}^{a0+w-1} L(i, k) X(k, j) into
+// tile (j, i); phase 2: X(i, j) = -sum_{k=c0}^{i} X(i, k) T(k, j).
+__global__ __launch_bounds__(NTH) void k_sbinv_level(const float* A32, float* Xsb, int64_t b, int64_t T, int w,
+                                                     int phase)
+{
+    __shared__ __align__(16) float As[32 * SBG_LD];
+    __shared__ __align__(16) float Bs[32 * SBG_LD];
+    const int64_t I = blockIdx.z, t0 = I * SB_TILES, SBb = SB_TILES * b;
+    const int st = (int)(T - t0 < SB_TILES ? T - t0 : SB_TILES);
+    // the blockIdx.y-th (i, j) pair of the super-block at width w
+    int u = blockIdx.y, a0 = 0, c0 = 0, i = -1, j = -1;
+    for (int g = 0;; ++g) {
+        a0 = 2 * w * g;
+        if (a0 + w >= st) break;
+        c0 = a0 + w;
+        const int c1 = min(a0 + 2 * w, st), cnt = (c1 - c0) * w;
+        if (u < cnt) {
+            i = c0 + u / w;
+            j = a0 + u % w;
+            break;
+        }
+        u -= cnt;
+    }
+    if (i < 0) return;   // fewer pairs in this (ragged) super-block: the whole CTA leaves
+    const int nsub = (int)(b / 64), sr = blockIdx.x / nsub, sc = blockIdx.x % nsub;
+    float* X = Xsb + I * SBb * SBb;
+    auto xt = [&](int r, int c) { return X + (int64_t)r * b * SBb + (int64_t)c * b; };
+    float acc[4][4] = {};
+    if (phase == 1) {
+        for (int k = j; k < a0 + w; ++k)
+            sb_gemm64(acc, A32 + tri_index(t0 + i, t0 + k) * b * b + (int64_t)sr * 64 * b, b,
+                      xt(k, j) + sc * 64, SBb, b, As, Bs);
+    } else {
+        for (int k = c0; k <= i; ++k)
+            sb_gemm64(acc, xt(i, k) + (int64_t)sr * 64 * SBb, SBb, xt(j, k) + sc * 64, SBb, b, As, Bs);
+    }
+    float* out = (phase == 1 ? xt(j, i) : xt(i, j)) + (int64_t)sr * 64 * SBb + sc * 64;
+    const float sg = phase == 1 ? 1.f : -1.f;
+    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+        *(float4*)(out + (int64_t)(4 * tr + x) * SBb + 4 * tc) =
+            make_float4(sg * acc[x][0], sg * acc[x][1], sg * acc[x][2], sg * acc[x][3]);
+}
+
 // One cooperative launch per solve, every CTA on every step: out = L~^{-1} in
-// (upper = 0) or out = L~^{-T} in (upper = 1), FP32 throughout.  Lower, for
-// t = 0 .. T-1: (A) out_t = Linv_tt (in_t - s_t), the rows of the b x b
-// product spread over all warps; (B) s_i += L_it out_t for every i > t.
-// Upper, for t = T-1 .. 0: (A) out_t = Linv_tt^T (in_t - s_t) by four-column
-// groups; (B) s_j += L_tj^T out_t for every j < t.  Phase (B) runs over
-// chunks of SV_CH rows of a tile, one chunk per CTA at a time, eight rows per
-// warp with all of a warp's loads in flight before any product.  Lower: each
-// row's dot product belongs to one warp, s has one copy.  Upper: a chunk's
-// column sums are reduced over its warps in shared memory and added to the
-// chunk's own copy of s (b / SV_CH copies, summed in phase (A)), so every
-// element has one writer per step and the result is deterministic.
-// Phases are separated by a grid barrier (arrival counter and generation
-// word, a wait bounded by wait_limit clock cycles); a timeout sets *err and
-// the kernel leaves, the caller reports it.
-constexpr int SV_CH = 64;     // rows per chunk of a tile in phase (B)
+// (upper = 0) or out = L~^{-T} in (upper = 1), FP32 throughout, over
+// super-blocks I of st <= SB_TILES tiles (edge B = st b, first tile t0).
+// Lower, I = 0 .. TS-1: (A) x_I = X_I (in_I - s_I); (B) s_i += L_iI x_I for
+// every row below the super-block.  Upper, I = TS-1 .. 0: (A) x_I = X_I^T
+// (in_I - s_I); (B) s_j += L_Ij^T x_I for every tile column j < t0.  A grid
+// barrier separates (A) and (B), and (B) from the next (A).  (A): every CTA
+// stages v_I = in_I - s_I in shared memory; the rows (lower) or four-column
+// groups (upper) of the product are spread over all warps of the grid.
+// (B), lower: chunks of SV_CH rows below the super-block, one per CTA at a
+// time, eight rows per warp, each row's dot product over the super-block's
+// columns held by one warp (one copy of s).  (B), upper: a unit is one tile
+// (t0 + r, j); its column sums over the tile's rows are reduced over the
+// CTA's warps and added to copy r of s (SB_TILES copies, summed in (A)), so
+// every element has one writer per step and the result is deterministic.
+// Grid barrier: arrival counter and generation word, each wait bounded by
+// wait_limit clock cycles; a timeout sets *err and the kernel leaves.
+constexpr int SV_CH = 64;     // rows per chunk in phase (B)
 constexpr int SV_SEG = 256;   // columns per pass: lanes hold 4 lane + 128 u, u = 0, 1
 
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err,
@@ -100,179 +216,164 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
     return *okb != 0;
 }
 
-// Dot product of a row (b floats, 16-byte aligned) with x - z (z may be
-// null) over one warp.
-__device__ __forceinline__ float warp_row_dot(const float* row, const float* x, const float* z, int64_t b, int lane)
-{
-    float sum = 0.f;
-    for (int64_t c = 4 * lane; c < b; c += 128) {
-        const float4 v = __ldcs((const float4*)(row + c));
-        float4 w = __ldcg((const float4*)(x + c));
-        if (z) {
-            const float4 u = __ldcg((const float4*)(z + c));
-            w.x -= u.x;
-            w.y -= u.y;
-            w.z -= u.z;
-            w.w -= u.w;
-        }
-        sum += v.x * w.x + v.y * w.y + v.z * w.z + v.w * w.w;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    return sum;
-}
-
-__device__ __forceinline__ float4 ld4_or0(const float* base, int64_t c, int64_t b, bool stream)
-{
-    if (c >= b) return make_float4(0.f, 0.f, 0.f, 0.f);
-    return stream ? __ldcs((const float4*)(base + c)) : __ldcg((const float4*)(base + c));
-}
-
 __device__ __forceinline__ float dot4(const float4& a, const float4& x)
 {
     return fmaf(a.x, x.x, fmaf(a.y, x.y, fmaf(a.z, x.z, a.w * x.w)));
 }
 
-// Four columns c4 .. c4+3 of M^T w, w_r = x_r - sum_{k < np} z[k * zs + r]
-// (M b x b row-major) over one warp: lanes take rows lane, lane + 32, ...
-__device__ __forceinline__ float4 warp_col4_dot(const float* M, const float* x, const float* z, int64_t zs, int np,
-                                                int64_t b, int64_t c4, int lane)
-{
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-    for (int64_t r = lane; r < b; r += 32) {
-        const float4 v = __ldcs((const float4*)(M + r * b + c4));
-        float xr = __ldcg(x + r);
-        for (int k = 0; k < np; ++k) xr -= __ldcg(z + k * zs + r);
-        s.x = fmaf(v.x, xr, s.x);
-        s.y = fmaf(v.y, xr, s.y);
-        s.z = fmaf(v.z, xr, s.z);
-        s.w = fmaf(v.w, xr, s.w);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-        s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
-        s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
-    }
-    return s;
-}
-
-// Phase (B), lower: s_i(r0 + k) += L_it(r0 + k, :) . x for the warp's rows k < 8.
-__device__ __forceinline__ void chunk_rows_dot(const float* Lb, const float* x, float* s, int64_t b, int lane)
-{
-    float acc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-    for (int64_t seg = 0; seg < b; seg += SV_SEG) {
-        float4 xv[2], v[8][2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) xv[u] = ld4_or0(x, seg + 4 * lane + 128 * u, b, false);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int u = 0; u < 2; ++u) v[k][u] = ld4_or0(Lb + k * b, seg + 4 * lane + 128 * u, b, true);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += dot4(v[k][0], xv[0]) + dot4(v[k][1], xv[1]);
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if (lane == k) s[k] = __ldcg(s + k) + acc[k];
-}
-
-// Phase (B), upper: s(c) += sum over the chunk's SV_CH rows r of L(r, c) x(r),
-// Lc = the chunk's first row; red = 8 x SV_SEG floats of shared memory.
-__device__ __forceinline__ void chunk_cols_dot(const float* Lc, const float* x, float* s, int64_t b, float* red)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float* Lb = Lc + (int64_t)warp * 8 * b;
-    float xr[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) xr[k] = __ldcg(x + warp * 8 + k);
-    for (int64_t seg = 0; seg < b; seg += SV_SEG) {
-        float4 v[8][2];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int u = 0; u < 2; ++u) v[k][u] = ld4_or0(Lb + k * b, seg + 4 * lane + 128 * u, b, true);
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                a.x = fmaf(v[k][u].x, xr[k], a.x);
-                a.y = fmaf(v[k][u].y, xr[k], a.y);
-                a.z = fmaf(v[k][u].z, xr[k], a.z);
-                a.w = fmaf(v[k][u].w, xr[k], a.w);
-            }
-            *(float4*)(red + warp * SV_SEG + 4 * lane + 128 * u) = a;
-        }
-        __syncthreads();
-        const int64_t c = seg + threadIdx.x;
-        if (threadIdx.x < SV_SEG && c < b) {
-            float sum = 0.f;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) sum += red[w * SV_SEG + threadIdx.x];
-            s[c] = __ldcg(s + c) + sum;
-        }
-        __syncthreads();
-    }
-}
-
-// s = sbuf: Np floats (lower) or (b / SV_CH) copies of Np floats (upper).
-__global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* Linv, int64_t b, int64_t T,
+// Dynamic shared memory: 2 SB_TILES b floats (v_I, x_I).
+__global__ __launch_bounds__(NTH) void k_solve32p(const float* Lt, const float* Xsb, int64_t b, int64_t T,
                                                   const float* in, float* out, float* sbuf, int upper, unsigned* bar,
                                                   int* err, long long wait_limit, int stall_last)
 {
     static_assert(NTH == 256 && NTH / 32 * 8 == SV_CH && NTH >= SV_SEG, "chunk of 8 warps x 8 rows");
+    extern __shared__ __align__(16) float sv_dyn[];
     __shared__ int okb;
     __shared__ __align__(16) float red[8 * SV_SEG];
+    const int64_t SBb = SB_TILES * b;
+    float* vs = sv_dyn;
+    float* xs = sv_dyn + SBb;
     if (threadIdx.x == 0) okb = 1;
     // test aid: the last CTA never arrives, so every other CTA's first barrier wait runs out
     if (stall_last && blockIdx.x == gridDim.x - 1) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nw = (int64_t)gridDim.x * (NTH / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (NTH / 32) + warp;
-    const int64_t Np = T * b, cpt = b / SV_CH;
-    const int np = upper ? (int)cpt : 1;
+    const int64_t gw = (int64_t)blockIdx.x * (NTH / 32) + warp, nw = (int64_t)gridDim.x * (NTH / 32);
+    const int64_t Np = T * b, TS = (T + SB_TILES - 1) / SB_TILES;
+    const int np = upper ? SB_TILES : 1;
     for (int64_t e = (int64_t)blockIdx.x * NTH + threadIdx.x; e < np * Np; e += (int64_t)gridDim.x * NTH)
         sbuf[e] = 0.f;
     if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb, wait_limit)) return;
-    for (int64_t q = 0; q < T; ++q) {
-        const int64_t t = upper ? T - 1 - q : q;
-        // (A) out_t = Linv_tt (in_t - s_t), or the transpose
-        const float* X = Linv + t * b * b;
+    for (int64_t q = 0; q < TS; ++q) {
+        const int64_t I = upper ? TS - 1 - q : q, t0 = I * SB_TILES;
+        const int st = (int)(T - t0 < SB_TILES ? T - t0 : SB_TILES);
+        const int64_t B = st * b, R0 = t0 * b;
+        const float* X = Xsb + I * SBb * SBb;
+        // (A) v_I in shared memory, then x_I = X_I v_I (rows over the grid's warps) or X_I^T v_I
+        for (int64_t e = threadIdx.x; e < B; e += NTH) {
+            float v = __ldcg(in + R0 + e);
+            for (int k = 0; k < np; ++k) v -= __ldcg(sbuf + k * Np + R0 + e);
+            vs[e] = v;
+        }
+        __syncthreads();
         if (!upper) {
-            for (int64_t r = gw; r < b; r += nw) {
-                const float v = warp_row_dot(X + r * b, in + t * b, sbuf + t * b, b, lane);
-                if (lane == 0) out[t * b + r] = v;
+            for (int64_t r = gw; r < B; r += nw) {   // row r: lower tiles only, columns < (r / b + 1) b
+                const int64_t ce = (r / b + 1) * b;
+                float sum = 0.f;
+                for (int64_t c = 4 * lane; c < ce; c += 128)
+                    sum += dot4(__ldcg((const float4*)(X + r * SBb + c)), *(const float4*)(vs + c));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (lane == 0) out[R0 + r] = sum;
             }
         } else {
-            for (int64_t c4 = 4 * gw; c4 < b; c4 += 4 * nw) {
-                const float4 v = warp_col4_dot(X, in + t * b, sbuf + t * b, Np, np, b, c4, lane);
-                if (lane == 0) *(float4*)(out + t * b + c4) = v;
+            for (int64_t c4 = 4 * gw; c4 < B; c4 += 4 * nw) {   // columns c4 .. c4+3: rows >= (c4 / b) b
+                float4 sm = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int64_t r = (c4 / b) * b + lane; r < B; r += 32) {
+                    const float4 m = __ldcg((const float4*)(X + r * SBb + c4));
+                    const float vr = vs[r];
+                    sm.x = fmaf(m.x, vr, sm.x);
+                    sm.y = fmaf(m.y, vr, sm.y);
+                    sm.z = fmaf(m.z, vr, sm.z);
+                    sm.w = fmaf(m.w, vr, sm.w);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sm.x += __shfl_xor_sync(0xffffffffu, sm.x, o);
+                    sm.y += __shfl_xor_sync(0xffffffffu, sm.y, o);
+                    sm.z += __shfl_xor_sync(0xffffffffu, sm.z, o);
+                    sm.w += __shfl_xor_sync(0xffffffffu, sm.w, o);
+                }
+                if (lane == 0) *(float4*)(out + R0 + c4) = sm;
             }
         }
         if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb, wait_limit)) return;
-        // (B) partial sums of the blocks still to solve, chunk by chunk
-        const float* xt = out + t * b;
+        // (B) partial sums of the rows (columns) still to solve
+        for (int64_t e = threadIdx.x; e < B; e += NTH) xs[e] = __ldcg(out + R0 + e);
+        __syncthreads();
         if (!upper) {
-            const int64_t nch = (T - t - 1) * cpt;
+            const int64_t nch = (Np - R0 - B) / SV_CH;   // chunks of SV_CH rows below the super-block
             for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-                const int64_t i = t + 1 + ch / cpt, r0 = (ch % cpt) * SV_CH + warp * 8;
-                chunk_rows_dot(Lt + tri_index(i, t) * b * b + r0 * b, xt, sbuf + i * b + r0, b, lane);
+                const int64_t row = R0 + B + ch * SV_CH + warp * 8, i = row / b, ro = row % b;
+                float acc[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+                for (int rt = 0; rt < st; ++rt) {
+                    const float* Lb = Lt + tri_index(i, t0 + rt) * b * b + ro * b;
+                    for (int64_t seg = 0; seg < b; seg += SV_SEG) {
+                        float4 xv[2], v[8][2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int64_t c = seg + 4 * lane + 128 * u;
+                            xv[u] = c < b ? *(const float4*)(xs + rt * b + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+#pragma unroll
+                            for (int u = 0; u < 2; ++u) {
+                                const int64_t c = seg + 4 * lane + 128 * u;
+                                v[k][u] = c < b ? __ldcs((const float4*)(Lb + k * b + c))
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                            }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) acc[k] += dot4(v[k][0], xv[0]) + dot4(v[k][1], xv[1]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+                if (lane < 8) {
+                    float a = acc[0];
+#pragma unroll
+                    for (int k = 1; k < 8; ++k)
+                        if (lane == k) a = acc[k];
+                    sbuf[row + lane] = __ldcg(sbuf + row + lane) + a;
+                }
             }
         } else {
-            const int64_t nch = t * cpt;
-            for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-                const int64_t j = ch / cpt, kc = ch % cpt;
-                chunk_cols_dot(Lt + tri_index(t, j) * b * b + kc * SV_CH * b, xt + kc * SV_CH,
-                               sbuf + kc * Np + j * b, b, red);
+            const int64_t nu = t0 * st;   // units (j, rt): tile (t0 + rt, j), j < t0
+            for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
+                const int64_t j = u / st;
+                const int rt = (int)(u % st);
+                const float* Lc = Lt + tri_index(t0 + rt, j) * b * b;
+                float* sc = sbuf + rt * Np + j * b;
+                for (int64_t seg = 0; seg < b; seg += SV_SEG) {
+                    float4 a[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+                    for (int64_t r0 = warp * 8; r0 < b; r0 += SV_CH) {   // the warp's rows of each chunk
+                        float4 v[8][2];
+                        float xr[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            xr[k] = xs[rt * b + r0 + k];
+#pragma unroll
+                            for (int u2 = 0; u2 < 2; ++u2) {
+                                const int64_t c = seg + 4 * lane + 128 * u2;
+                                v[k][u2] = c < b ? __ldcs((const float4*)(Lc + (r0 + k) * b + c))
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                            }
+                        }
+#pragma unroll
+                        for (int u2 = 0; u2 < 2; ++u2)
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                a[u2].x = fmaf(v[k][u2].x, xr[k], a[u2].x);
+                                a[u2].y = fmaf(v[k][u2].y, xr[k], a[u2].y);
+                                a[u2].z = fmaf(v[k][u2].z, xr[k], a[u2].z);
+                                a[u2].w = fmaf(v[k][u2].w, xr[k], a[u2].w);
+                            }
+                    }
+#pragma unroll
+                    for (int u2 = 0; u2 < 2; ++u2) *(float4*)(red + warp * SV_SEG + 4 * lane + 128 * u2) = a[u2];
+                    __syncthreads();
+                    const int64_t c = seg + threadIdx.x;
+                    if (threadIdx.x < SV_SEG && c < b) {
+                        float sum = 0.f;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) sum += red[w * SV_SEG + threadIdx.x];
+                        sc[c] = __ldcg(sc + c) + sum;
+                    }
+                    __syncthreads();
+                }
             }
         }
         if (!grid_barrier(bar, bar + 1, gridDim.x, err, &okb, wait_limit)) return;
@@ -674,6 +775,8 @@ constexpr int SWEEP_BLOCK = 4;
 // of a super-panel is factored (diagonal tile, panel) and applied only to the
 // super-panel's later columns; then one update with a k-segment per column
 // applies the whole super-panel to the trailing triangle.
+static void build_sbinv(gp_t h);
+
 bool factor_mixed(gp_t h)
 {
     const int T = (int)h->T;
@@ -695,38 +798,60 @@ bool factor_mixed(gp_t h)
         }
         if (e < T && !tg_update(h, K0, e - K0, e, T - e)) return false;
     }
+    build_sbinv(h);
     return true;
 }
 
+
+// Super-block inverses X_I of the mixed factor (end of factor_mixed): the
+// tile inverses on the diagonal, then the recursive doubling, two launches
+// (T, then X) per group width.
+static void build_sbinv(gp_t h)
+{
+    const int64_t b = h->b, T = h->T, TS = (T + SB_TILES - 1) / SB_TILES, nsub = b / 64;
+    GPK_LAUNCH(h, GP_PH_POTRF, k_sbinv_diag, dim3((unsigned)grid_for(b * b) / 8 + 1, (unsigned)T), NTH, 0,
+               (const float*)h->Linv32, h->Xsb, b, T);
+    for (int w = 1; w < SB_TILES; w *= 2) {
+        int np = 0;   // (i, j) pairs of a full super-block at width w
+        for (int a0 = 0; a0 + w < SB_TILES; a0 += 2 * w)
+            np += ((a0 + 2 * w < SB_TILES ? a0 + 2 * w : SB_TILES) - a0 - w) * w;
+        for (int phase = 1; phase <= 2; ++phase)
+            GPK_LAUNCH(h, GP_PH_POTRF, k_sbinv_level, dim3((unsigned)(nsub * nsub), (unsigned)np, (unsigned)TS), NTH,
+                       0, (const float*)h->A32, h->Xsb, b, T, w, phase);
+    }
+}
 
 // out32 = L~^{-1} in32 (lower) or L~^{-T} in32 (upper), FP32 throughout.
 static void solve32(gp_t h, const float* in32, float* out32, bool upper)
 {
     static int grid_dev = -1, grid_blocks = 0;
+    static int64_t grid_b = -1;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (grid_dev != dev) {   // every CTA resident at once: the blocks wait on one another
+    const size_t dyn = 2 * (size_t)SB_TILES * h->b * sizeof(float);
+    if (grid_dev != dev || grid_b != h->b) {   // every CTA resident at once: the blocks wait on one another
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve32p, NTH, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve32p, NTH, dyn);
         grid_blocks = sms * (per < 2 ? per : 2);
         grid_dev = dev;
+        grid_b = h->b;
     }
     int64_t bb = h->b, TT = h->T;
     int up = upper ? 1 : 0;
     const float* Lt = h->A32;
-    const float* Li = h->Linv32;
+    const float* Xs = h->Xsb;
     float* sbuf = h->w32;
     unsigned* bar = (unsigned*)h->solve_flags;
     int* err = tc_error_dev();
     long long limit = h->solve_wait_cycles;
     int stall = h->solve_stall ? 1 : 0;
-    void* args[] = {(void*)&Lt, (void*)&Li, (void*)&bb, (void*)&TT, (void*)&in32, (void*)&out32, (void*)&sbuf,
+    void* args[] = {(void*)&Lt, (void*)&Xs, (void*)&bb, (void*)&TT, (void*)&in32, (void*)&out32, (void*)&sbuf,
                     (void*)&up, (void*)&bar, (void*)&err, (void*)&limit, (void*)&stall};
     cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), h->st);   // fresh barrier words, whatever a failed solve left
     const bool p_ = h->prof_on && prof_begin(h, GP_PH_SOLVE);
-    // a failed launch leaves its error for the caller's check of the last launch error
-    cudaLaunchCooperativeKernel((const void*)k_solve32p, dim3((unsigned)grid_blocks), dim3(NTH), args, 0, h->st);
+    // a failed launch (including a grid of zero) leaves its error for the caller's check of the last launch error
+    cudaLaunchCooperativeKernel((const void*)k_solve32p, dim3((unsigned)grid_blocks), dim3(NTH), args, dyn, h->st);
     h->launches++;
     if (p_) prof_end(h);
     h->tc_pending = true;

@@ -15,7 +15,11 @@
 //      (b) every warp of the cluster takes 8-row strips of the panel
 //          L_rp = A_rp X_pp^T, r > p;
 //      (c) every warp takes 8-row strips of the trailing update
-//          A_ij -= L_ip L_jp^T, p < j <= i;
+//          A_ij -= L_ip L_jp^T, p < j <= i, with one step of lookahead: four
+//          warps of CTA 0 update block (p+1, p+1) first and one of them then
+//          factors it (step (a) of p+1) while the other warps finish (c), so
+//          each block column costs two cluster barriers and the diagonal
+//          factor is off the critical path;
 //  - then X = L^{-1} by recursive doubling: groups of w blocks merge
 //    pairwise, w = 1, 2, 4, ...; for a pair with first half A and second half
 //    C, X_CA = -X_CC (L_CA X_AA), the product L_CA X_AA kept in the strict
@@ -41,7 +45,7 @@ namespace gpk {
 namespace {
 
 constexpr int CL_CTAS = 8;                 // CTAs of the cluster
-constexpr int CL_TH = 256;                 // threads per CTA
+constexpr int CL_TH = 512;                 // threads per CTA
 constexpr int CL_WARPS = CL_CTAS * CL_TH / 32;
 constexpr int CL_NB = 32;                  // block edge
 constexpr int CL_R = 8;                    // rows of a warp unit
@@ -92,7 +96,7 @@ __device__ __forceinline__ void chol32f_step(float (&row)[32], int l, int& bad, 
 {
     const float d = __shfl_sync(0xffffffffu, row[J], J);
     if (!(d > 0.f) && bad < 0) bad = J;
-    const float dj = sqrtf(d), inv = 1.f / dj;
+    const float inv = rsqrtf(d), dj = d * inv;   // the factor is FP32-level: approximate 1/sqrt suffices
     if (l == J) dinv = inv;
     row[J] = (l == J) ? dj : row[J] * inv;
 #pragma unroll
@@ -202,21 +206,36 @@ __device__ __forceinline__ bool pair_unit(int u, int w, int P, int& a0, int& c0,
     }
 }
 
-__global__ __launch_bounds__(CL_TH) void k_potrf_cl(const ClArgs a)
+// One 8-row strip of the trailing update of step p: A_ij -= L_ip L_jp^T for
+// the u-th unit of the lower block triangle below block (p, p).
+__device__ __forceinline__ void cl_update_unit(const ClArgs& a, int p, int u, int lane)
+{
+    const int64_t b = a.b;
+    int64_t ii, jj;
+    tri_decode(u / CL_UPB, ii, jj);
+    const int bi = p + 1 + (int)ii, bj = p + 1 + (int)jj, r0 = (u % CL_UPB) * CL_R;
+    float acc[CL_R] = {};
+    strip_term(acc, cblk(a.A, b, bi, p), r0, cblk(a.A, b, bj, p), true, b, lane);
+    float* q = cblk(a.A, b, bi, bj) + (int64_t)r0 * b + lane;
+#pragma unroll
+    for (int r = 0; r < CL_R; ++r) q[(int64_t)r * b] = __ldcg(q + (int64_t)r * b) - acc[r];
+}
+
+__global__ __launch_bounds__(CL_TH, 1) void k_potrf_cl(const ClArgs a)
 {
     __shared__ float S[32 * 33];
     __shared__ float dv[32];
     double logacc = 0.0;   // lane 0 of warp 0 of CTA 0
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (CL_TH / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (CL_TH / 32) + warp;
+    const bool lead = blockIdx.x == 0 && warp < CL_UPB;   // the lookahead warps
     const int P = (int)(a.b / CL_NB);
     const int64_t b = a.b;
 
-    for (int p = 0; p < P; ++p) {
-        if (gw == 0) cl_diag(a, p, S, dv, &logacc, lane);
-        cluster_sync();
-        if (failed(a.info)) return;   // every CTA reads the same word after the same barrier
-        if (p + 1 == P) break;
+    if (gw == 0) cl_diag(a, 0, S, dv, &logacc, lane);
+    cluster_sync();
+    if (failed(a.info)) return;   // every CTA reads the same word after the same barrier
+    for (int p = 0; p + 1 < P; ++p) {
         // (b) panel strips L_rp = A_rp X_pp^T, in place (each strip is read by its own warp only)
         const int np = (P - 1 - p) * CL_UPB;
         for (int u = gw; u < np; u += CL_WARPS) {
@@ -228,20 +247,21 @@ __global__ __launch_bounds__(CL_TH) void k_potrf_cl(const ClArgs a)
             for (int r = 0; r < CL_R; ++r) Arp[(int64_t)(r0 + r) * b + lane] = acc[r];
         }
         cluster_sync();
-        // (c) trailing update strips A_ij -= L_ip L_jp^T, p < j <= i
+        // (c) trailing update; units 0 .. CL_UPB-1 are block (p+1, p+1), taken by the
+        // lookahead warps, which then factor it (step (a) of p+1)
         const int n = P - 1 - p;
         const int nu = n * (n + 1) / 2 * CL_UPB;
-        for (int u = gw; u < nu; u += CL_WARPS) {
-            int64_t ii, jj;
-            tri_decode(u / CL_UPB, ii, jj);
-            const int bi = p + 1 + (int)ii, bj = p + 1 + (int)jj, r0 = (u % CL_UPB) * CL_R;
-            float acc[CL_R] = {};
-            strip_term(acc, cblk(a.A, b, bi, p), r0, cblk(a.A, b, bj, p), true, b, lane);
-            float* q = cblk(a.A, b, bi, bj) + (int64_t)r0 * b + lane;
-#pragma unroll
-            for (int r = 0; r < CL_R; ++r) q[(int64_t)r * b] = __ldcg(q + (int64_t)r * b) - acc[r];
+        if (lead) {
+            cl_update_unit(a, p, warp, lane);
+            __threadfence();
+            asm volatile("bar.sync 1, %0;\n" ::"n"(CL_UPB * 32) : "memory");
+            if (warp == 0) cl_diag(a, p + 1, S, dv, &logacc, lane);
+        } else {
+            // the other warps, numbered from 0 (the lookahead warps are gw 0 .. CL_UPB-1)
+            for (int u = gw; u < nu; u += CL_WARPS - CL_UPB) cl_update_unit(a, p, u, lane);
         }
         cluster_sync();
+        if (failed(a.info)) return;
     }
     // inverse by recursive doubling
     for (int w = 1; w < P; w *= 2) {
