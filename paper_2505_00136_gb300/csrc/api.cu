@@ -131,7 +131,7 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
     const int64_t old = h->m_cap;
     dev_free(h, &h->Xs, old * h->d);
     dev_free(h, &h->R32, old * h->Np);
-    dev_free(h, &h->RP, 3 * old * h->b);
+    dev_free(h, &h->RP, 3 * old * gpk::GP_SOLVE_SB * h->b);
     dev_free(h, &h->WP, 3 * old * h->Np);
     dev_free(h, &h->mpart, old * (h->Np / TB));
     dev_free(h, &h->vpart, old * (h->Np / 64));
@@ -158,7 +158,7 @@ gp_status ensure_predict_space_mixed(gp_t h, int64_t m)
         if ((s = dev_alloc(h, &h->qpart, 2 * ldm * (h->Np / 64))) != GP_OK) return s;   // one slot per 64 columns
         if ((s = dev_alloc(h, &h->vpart2, ldm * (h->Np / 64))) != GP_OK) return s;   // one slot per 64 columns
     }
-    if ((s = dev_alloc(h, &h->RP, 3 * ldm * h->b)) != GP_OK) return s;
+    if ((s = dev_alloc(h, &h->RP, 3 * ldm * gpk::GP_SOLVE_SB * h->b)) != GP_OK) return s;   // one super-block
     if ((s = dev_alloc(h, &h->WP, 3 * ldm * h->Np)) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->mpart, ldm * (h->Np / TB))) != GP_OK) return s;
     if ((s = dev_alloc(h, &h->vpart, ldm * (h->Np / 64))) != GP_OK) return s;     // one slot per 64 columns
@@ -560,7 +560,7 @@ void gp_destroy(gp_t h)
     void* ptrs[] = {h->X, h->y, h->hyp, h->adam, h->L, h->Linv, h->beta, h->alpha, h->work,
                     h->logdet_part, h->info, h->scal, h->Xinv, h->Kinv, h->gpart, h->Xs, h->B,
                     h->V, h->part, h->outm, h->outv, h->cov, h->A32, h->LP, h->Linv32, h->LinvP,
-                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->xprev, h->Xsb, h->norms, h->R32, h->RP,
+                    h->PA, h->r32, h->t32, h->w32, h->solve_flags, h->res, h->xprev, h->Xsb, h->XsbP, h->norms, h->R32, h->RP,
                     h->WP, h->mpart, h->vpart, h->ZP, h->U32, h->Kinv32, h->R64, h->Rr32,
                     h->YS, h->KS, h->mu, h->kappa, h->qpart, h->vpart2, h->dag_tasks, h->dag_ctl,
                     h->dag_upd, h->dag_fin, h->OGP, h->OGS, h->og_mu, h->OGL, h->ogl_mu, h->OGT, h->OGTS, h->ogt_mu, h->OGX, h->ogx_mu, h->ogx_bits, h->OGV, h->OGVS, h->ogv_mu,
@@ -653,8 +653,10 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         TRY(dev_alloc(h, &h->r32, h->Np));
         TRY(dev_alloc(h, &h->t32, h->Np));
         TRY(dev_alloc(h, &h->w32, h->Np * gpk::GP_SOLVE_SB));   // partial sums of the solves (one copy per tile of a super-block)
-        TRY(dev_alloc(h, &h->Xsb, (h->T + gpk::GP_SOLVE_SB - 1) / gpk::GP_SOLVE_SB * (gpk::GP_SOLVE_SB * h->b) *
-                                      (gpk::GP_SOLVE_SB * h->b)));
+        const int64_t sbx = (h->T + gpk::GP_SOLVE_SB - 1) / gpk::GP_SOLVE_SB * (gpk::GP_SOLVE_SB * h->b) *
+                            (gpk::GP_SOLVE_SB * h->b);
+        TRY(dev_alloc(h, &h->Xsb, sbx));
+        TRY(dev_alloc(h, &h->XsbP, 3 * sbx));
         TRY(dev_alloc(h, &h->solve_flags, 2));
         TRY(cuda_status(h, cudaMemset(h->solve_flags, 0, 2 * sizeof(int))));
         TRY(dev_alloc(h, &h->res, h->Np));

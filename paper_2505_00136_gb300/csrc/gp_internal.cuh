@@ -82,6 +82,7 @@ struct gp_handle {
     double* res;              // Np FP64 residual
     double* xprev;            // Np: the refinement's previous iterate
     float* Xsb;               // inverses of the super-blocks of GP_SOLVE_SB diagonal tiles, (GP_SOLVE_SB b)^2 each
+    __nv_bfloat16* XsbP;      // their three BF16 planes (upper tiles zero), plane-major
     double* norms;            // 2 FP64 norms
     float* R32;               // m_cap x Np: K_{Z*,Z}, overwritten by the W solve
     __nv_bfloat16 *RP, *WP;   // planes: RP 3 x m_cap x b (scratch), WP 3 x m_cap x Np (all of W)
@@ -230,6 +231,8 @@ bool tg_update(gp_t h, int k0, int nsrc, int j0, int w);   // A_ij -= sum_k L_ik
 // The four multi-RHS sweep products take planes = 3 (six plane products, FP32
 // accuracy) or 2 (the three of order <= 2^-8, about 2^-16 relative).
 bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j, int planes);
+// W_I = R_I X_I^T for super-block I (R_I planes in RP), W planes, FP32 W, row sums of W^2
+bool tg_diag_w_sb(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t I, int planes);
 bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0, int ni,
               int planes);   // R_i -= sum W_j L_ij^T
 bool tg_syrk_cov(gp_t h, int64_t m, int64_t ldm, double* cov);
@@ -243,7 +246,7 @@ void zslices(gp_t h, const double* Z, const double* center, int64_t rows, int64_
 bool dist_train_tc(gp_t h);                                     // K tiles into L (FP64) and A32
 bool dist_cross_tc(gp_t h, int64_t m, int64_t ldm);             // R32, R64, mean partials
 bool dist_prior_tc(gp_t h, int64_t m, int64_t ldm, double* out);   // K_{Z*,Z*} (m x m)
-bool tg_bdiag(gp_t h, int64_t ldm, int64_t i, int planes);      // Y_i = S_i Linv_ii (NN form)
+bool tg_bdiag_sb(gp_t h, int64_t ldm, int64_t I, int planes);   // Y_I = S_I X_I (NN form), super-block I
 bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj, int planes);   // S_j -= sum Y_i L_ij (NN form)
 constexpr int GP_SOLVE_SB = 4;                                 // tiles per super-block of the FP32 solves
 constexpr int GP_OZ_SLICES = 6;                                // digit slices of K (kernels_mixed.cu)

@@ -166,6 +166,26 @@ __global__ __launch_bounds__(NTH) void k_sbinv_level(const float* A32, float* Xs
             make_float4(sg * acc[x][0], sg * acc[x][1], sg * acc[x][2], sg * acc[x][3]);
 }
 
+// The three BF16 planes of every X_I (plane q at XsbP + q TS B^2), the
+// upper tiles (which held the products T of the doubling) and the unused
+// tiles of a short last super-block written as zero: the operand of the
+// multi-RHS sweeps' super-block steps.
+__global__ void k_split_sbx(const float* Xsb, int64_t b, int64_t T, __nv_bfloat16* XsbP)
+{
+    const int64_t SBb = SB_TILES * b, TS = (T + SB_TILES - 1) / SB_TILES, total = TS * SBb * SBb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t I = e / (SBb * SBb), r = (e / SBb) % SBb, c = e % SBb;
+        const int64_t st = T - I * SB_TILES < SB_TILES ? T - I * SB_TILES : SB_TILES;   // tiles of super-block I
+        const float v = (c / b > r / b || r / b >= st) ? 0.f : __ldcg(Xsb + e);
+        __nv_bfloat16 hi, mid, lo;
+        split3(v, hi, mid, lo);
+        XsbP[e] = hi;
+        XsbP[total + e] = mid;
+        XsbP[2 * total + e] = lo;
+    }
+}
+
 // One cooperative launch per solve, every CTA on every step: out = L~^{-1} in
 // (upper = 0) or out = L~^{-T} in (upper = 1), FP32 throughout, over
 // super-blocks I of st <= SB_TILES tiles (edge B = st b, first tile t0).
@@ -514,18 +534,20 @@ __global__ __launch_bounds__(NTH) void k_cross_mixed(const double* Xs, int64_t m
 }
 
 // Planes of the column block R32[:, j*b .. (j+1)*b) into RP ([3][ldm][b]).
-__global__ void k_split_cols(const float* R32, int64_t ldr, int64_t j, int64_t b, int64_t rows,
+// Planes of columns col0 .. col0 + width - 1 of R32 (rows x ldr) into RP
+// (three planes of rows x ldp).
+__global__ void k_split_cols(const float* R32, int64_t ldr, int64_t col0, int64_t width, int64_t ldp, int64_t rows,
                              __nv_bfloat16* RP)
 {
-    const int64_t total = rows * b, ps = rows * b;
+    const int64_t total = rows * width, ps = rows * ldp;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e / b, c = e % b;
+        const int64_t r = e / width, c = e % width;
         __nv_bfloat16 hi, mid, lo;
-        split3(R32[r * ldr + j * b + c], hi, mid, lo);
-        RP[e] = hi;
-        RP[ps + e] = mid;
-        RP[2 * ps + e] = lo;
+        split3(R32[r * ldr + col0 + c], hi, mid, lo);
+        RP[r * ldp + c] = hi;
+        RP[ps + r * ldp + c] = mid;
+        RP[2 * ps + r * ldp + c] = lo;
     }
 }
 
@@ -753,7 +775,7 @@ static int grid_for(int64_t work, int per = NTH)
     return (int)g;
 }
 
-// Operand planes of the three multi-RHS sweeps of a prediction.  W =
+// Operand planes and steps of the three multi-RHS sweeps of a prediction.  W =
 // K_{Z*,Z} L~^{-T} feeds x0 and the full covariance and keeps all three
 // planes (FP32 accuracy).  The backward sweep x0^T = W L~^{-1} and the forward
 // sweep of r0 take the three plane products of order <= 2^-8 (about 2^-16
@@ -761,7 +783,10 @@ static int grid_for(int64_t work, int per = NTH)
 // holds for any x0, and ||L~^{-1} r0||^2 is a small second-order term.
 // Measured at N = 32768, M = 8192 against the emulated FP64 path: variance
 // error 4.2e-11 with three planes everywhere, 3.4e-11 with these choices;
-// two planes on W as well give 1.2e-9 (worst element 5e-8).
+// two planes on W as well give 1.2e-9 (worst element 5e-8).  The backward
+// and r0 sweeps step over super-blocks with their inverses X_I (4.4e-11);
+// W takes the tile-by-tile steps: through X_I, whose off-diagonal tiles are
+// FP32 products, its variance error rose to 9.5e-10 (worst 3e-8).
 constexpr int SWEEP_PLANES_W = 3;
 constexpr int SWEEP_PLANES_B = 2;
 constexpr int SWEEP_PLANES_R = 2;
@@ -819,6 +844,8 @@ static void build_sbinv(gp_t h)
             GPK_LAUNCH(h, GP_PH_POTRF, k_sbinv_level, dim3((unsigned)(nsub * nsub), (unsigned)np, (unsigned)TS), NTH,
                        0, (const float*)h->A32, h->Xsb, b, T, w, phase);
     }
+    GPK_LAUNCH(h, GP_PH_POTRF, k_split_sbx, grid_for(TS * SB_TILES * b * SB_TILES * b), NTH, 0,
+               (const float*)h->Xsb, b, T, h->XsbP);
 }
 
 // out32 = L~^{-1} in32 (lower) or L~^{-T} in32 (upper), FP32 throughout.
@@ -898,21 +925,35 @@ void nlml_mixed(gp_t h)
 }
 
 // Forward multi-RHS solve W = R L~^{-T} in place over R (ldm x Np, FP32): W
-// planes into WP, FP32 W over R, FP64 row sums of W^2 into vpart.
-
-static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase, int planes)
+// planes into WP, FP32 W over R, FP64 row sums of W^2 into vpart.  Tile by
+// tile (sb false): W_j = R_j Linv_jj^T, then the later columns of the same
+// block of SWEEP_BLOCK tiles, then one update of every later tile per block.
+// By super-blocks (sb true): W_I = R_I X_I^T, then R_i -= sum over the
+// super-block's tiles j of W_j L_ij^T for every later tile i.  Either way R
+// is read and written once per block of four tile columns.
+static bool forward_w(gp_t h, float* R, int64_t ldm, double* vpart, int phase, int planes, bool sb)
 {
     const int T = (int)h->T;
-    const int64_t b = h->b, Np = h->Np;
-    for (int J = 0; J < T; J += SWEEP_BLOCK) {
-        const int e = J + SWEEP_BLOCK < T ? J + SWEEP_BLOCK : T;
-        for (int j = J; j < e; ++j) {
-            GPK_LAUNCH(h, phase, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)R, Np, (int64_t)j, b, ldm,
-                       h->RP);
-            if (!tg_diag_w(h, phase, R, ldm, vpart, j, planes)) return false;
-            if (j + 1 < e && !tg_upd_w(h, phase, R, ldm, j, 1, j + 1, e - j - 1, planes)) return false;
+    const int64_t b = h->b, Np = h->Np, SBb = SB_TILES * b;
+    if (!sb) {
+        for (int J = 0; J < T; J += SWEEP_BLOCK) {
+            const int e = J + SWEEP_BLOCK < T ? J + SWEEP_BLOCK : T;
+            for (int j = J; j < e; ++j) {
+                GPK_LAUNCH(h, phase, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)R, Np, (int64_t)j * b, b, b,
+                           ldm, h->RP);
+                if (!tg_diag_w(h, phase, R, ldm, vpart, j, planes)) return false;
+                if (j + 1 < e && !tg_upd_w(h, phase, R, ldm, j, 1, j + 1, e - j - 1, planes)) return false;
+            }
+            if (e < T && !tg_upd_w(h, phase, R, ldm, J, e - J, e, T - e, planes)) return false;
         }
-        if (e < T && !tg_upd_w(h, phase, R, ldm, J, e - J, e, T - e, planes)) return false;
+        return true;
+    }
+    for (int t0 = 0; t0 < T; t0 += SB_TILES) {
+        const int st = T - t0 < SB_TILES ? T - t0 : SB_TILES;
+        GPK_LAUNCH(h, phase, k_split_cols, grid_for(ldm * st * b), NTH, 0, (const float*)R, Np, (int64_t)t0 * b,
+                   (int64_t)st * b, SBb, ldm, h->RP);
+        if (!tg_diag_w_sb(h, phase, R, ldm, vpart, t0 / SB_TILES, planes)) return false;
+        if (t0 + st < T && !tg_upd_w(h, phase, R, ldm, t0, st, t0 + st, T - t0 - st, planes)) return false;
     }
     return true;
 }
@@ -930,7 +971,7 @@ bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var, bool want_cov)
                    (const GpHyperDev*)h->hyp, h->R32, Np, h->mpart, ldm, h->R64);
     }
     if ((want_var || want_cov) &&
-        !forward_w(h, h->R32, ldm, h->vpart, GP_PH_VSOLVE, SWEEP_PLANES_W))
+        !forward_w(h, h->R32, ldm, h->vpart, GP_PH_VSOLVE, SWEEP_PLANES_W, false))
         return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_mixed_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->mpart,
                nmp, (const double*)h->vpart, want_var ? nvp : (int64_t)0, ldm, m, (const GpHyperDev*)h->hyp,
@@ -943,17 +984,16 @@ bool predict_mixed(gp_t h, int64_t m, int64_t ldm, bool want_var, bool want_cov)
 bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
 {
     const int64_t T = h->T, b = h->b, Np = h->Np;
-    // x0^T = W L~^{-1}: backward sweep over tile columns, in place over R32, in
-    // blocks of SWEEP_BLOCK columns; Y planes go to the W plane buffer
-    for (int I = (int)T - 1; I >= 0; I -= SWEEP_BLOCK) {
-        const int lo = I - SWEEP_BLOCK + 1 > 0 ? I - SWEEP_BLOCK + 1 : 0;
-        for (int i = I; i >= lo; --i) {
-            GPK_LAUNCH(h, GP_PH_BSOLVE, k_split_cols, grid_for(ldm * b), NTH, 0, (const float*)h->R32, Np,
-                       (int64_t)i, b, ldm, h->RP);
-            if (!tg_bdiag(h, ldm, i, SWEEP_PLANES_B)) return false;
-            if (i > lo && !tg_bupd(h, ldm, i, 1, lo, i - lo, SWEEP_PLANES_B)) return false;
-        }
-        if (lo > 0 && !tg_bupd(h, ldm, lo, I - lo + 1, 0, lo, SWEEP_PLANES_B)) return false;
+    // x0^T = W L~^{-1}: backward sweep over super-blocks, in place over R32:
+    // Y_I = S_I X_I, then S_j -= sum over the super-block's tiles i of Y_i L_ij
+    // for every earlier tile j; Y planes go to the W plane buffer
+    const int64_t SBb = SB_TILES * b, TS = (T + SB_TILES - 1) / SB_TILES;
+    for (int64_t I = TS - 1; I >= 0; --I) {
+        const int t0 = (int)(I * SB_TILES), st = (int)(T - t0 < SB_TILES ? T - t0 : SB_TILES);
+        GPK_LAUNCH(h, GP_PH_BSOLVE, k_split_cols, grid_for(ldm * st * b), NTH, 0, (const float*)h->R32, Np,
+                   (int64_t)t0 * b, (int64_t)st * b, SBb, ldm, h->RP);
+        if (!tg_bdiag_sb(h, ldm, I, SWEEP_PLANES_B)) return false;
+        if (t0 > 0 && !tg_bupd(h, ldm, t0, st, 0, t0, SWEEP_PLANES_B)) return false;
     }
     GPK_LAUNCH(h, GP_PH_SLICES, k_yslices, (unsigned)ldm, NTH, 0, h->R32, Np, h->YS, ldm * Np, h->mu);
     if (!h->ks_valid) {
@@ -962,7 +1002,7 @@ bool var_correction_mixed(gp_t h, int64_t m, int64_t ldm)
         h->ks_valid = true;
     }
     if (!ozaki_tc(h, m, ldm)) return false;
-    if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_RSOLVE, SWEEP_PLANES_R)) return false;
+    if (!forward_w(h, h->Rr32, ldm, h->vpart2, GP_PH_RSOLVE, SWEEP_PLANES_R, true)) return false;
     GPK_LAUNCH(h, GP_PH_REDUCE, k_var_finish, (unsigned)((m + 255) / 256), 256, 0, (const double*)h->qpart, Np / 64,
                (const double*)h->vpart2, Np / 64, ldm, m, (const GpHyperDev*)h->hyp, h->opt.noisy_test_var,
                h->outv);

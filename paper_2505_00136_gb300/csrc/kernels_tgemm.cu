@@ -418,6 +418,55 @@ struct OpUpdate {
     }
 };
 
+// Forward multi-RHS solve, super-block step: W_I = R_I X_I^T, X_I the
+// inverse of the super-block's diagonal block (R_I planes in RP, row stride
+// B = GP_SOLVE_SB b; X_I planes K-major, rows xrow0 ..); planes of W_I into
+// WP, FP32 W_I over R, FP64 row sums of W_I^2 into vpart (one slot per 64
+// columns).  X_I is lower triangular: column unit cn needs k < (cn + 1) N.
+template <int N, int P = 3>
+struct OpDiagWSB {
+    static constexpr bool kBMN = false;
+    static constexpr int kN = N;
+    static constexpr int kP = P;
+    __nv_bfloat16* WP;
+    float* Wout;
+    double* vpart;
+    int64_t ldw, ldm;
+    int col0, xrow0, Qn, nmb;
+    __device__ bool skip_all() const { return false; }
+    __device__ int units() const { return Qn * nmb; }
+    __device__ bool active(int) const { return true; }
+    __device__ int nseg(int) const { return 1; }
+    __device__ Seg seg(int u, int) const
+    {
+        const int cn = u % Qn, mb = u / Qn;
+        return Seg{mb * 128, 0, xrow0 + cn * N, 0, 0, (cn + 1) * N};
+    }
+    template <class W>
+    __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
+    {
+        const int cn = u % Qn, mb = u / Qn;
+        const int64_t r = (int64_t)mb * 128 + row;
+        const int64_t o = r * ldw + col0 + cn * N;
+        if (!wait()) return false;
+#pragma unroll 1
+        for (int h64 = 0; h64 < N / 2; h64 += 64) {
+            double sq = 0.0;
+#pragma unroll 1
+            for (int h = 0; h < 64; h += 32) {
+                float v[32];
+                tc::tmem_ld32(t + c0 + h64 + h, v);
+                planes32(WP + o + c0 + h64 + h, ldm * ldw, v);
+                row_store(Wout + o + c0 + h64 + h, v, 0);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) sq += (double)v[q] * v[q];
+            }
+            vpart[(((int64_t)col0 + cn * N + c0 + h64) / 64) * ldm + r] = sq;
+        }
+        return true;
+    }
+};
+
 // Forward multi-RHS solve, diagonal step: W_j = R_j Linv_jj^T; planes of W_j
 // into WP, FP32 W_j over R_j, FP64 row sums of W_j^2 into vpart (one slot per
 // 64 columns).
@@ -684,20 +733,20 @@ struct OpLauum {
     }
 };
 
-// Backward multi-RHS solve of the variance correction (x0^T = W L~^{-1}, NN form).
-// Diagonal step: Y_i = S_i Linv_ii, Linv_ii[t][c] nonzero for t >= c, so the
-// k-range of a column unit starts at its first column.  FP32 Y_i over S_i
-// (column block i of R32) and its planes into column block i of planes
-// (three planes of ldm x ldr: the W plane buffer).
+// Backward multi-RHS solve of the variance correction (x0^T = W L~^{-1}, NN
+// form), super-block step: Y_I = S_I X_I with X_I[k][n] nonzero for k >= n,
+// so the k range of a column unit starts at its first column.  FP32 Y_I over
+// S_I (column block col0 .. of R32) and its planes into the same columns of
+// planes (three planes of ldm x ldr: the W plane buffer).
 template <int N, int P = 3>
-struct OpBDiag {
+struct OpBDiagSB {
     static constexpr bool kBMN = true;
     static constexpr int kN = N;
     static constexpr int kP = P;
     float* R32;
     __nv_bfloat16* planes;
     int64_t ldr, ldm;
-    int b, i, Qn, nmb;
+    int col0, xrow0, B, Qn, nmb;
     __device__ bool skip_all() const { return false; }
     __device__ int units() const { return Qn * nmb; }
     __device__ bool active(int) const { return true; }
@@ -705,15 +754,15 @@ struct OpBDiag {
     __device__ Seg seg(int u, int) const
     {
         const int cn = u % Qn, mb = u / Qn;
-        return Seg{mb * 128, 0, i * 3 * b, cn * N, cn * N, b};
+        return Seg{mb * 128, 0, xrow0, cn * N, cn * N, B};
     }
     template <class W>
     __device__ bool epilogue(int u, int row, int c0, uint32_t t, W&& wait) const
     {
         const int cn = u % Qn, mb = u / Qn;
         const int64_t r = (int64_t)mb * 128 + row;
-        float* dst = R32 + r * ldr + (int64_t)i * b + cn * N;
-        __nv_bfloat16* yp = planes + r * ldr + (int64_t)i * b + cn * N;
+        float* dst = R32 + r * ldr + col0 + cn * N;
+        __nv_bfloat16* yp = planes + r * ldr + col0 + cn * N;
         if (!wait()) return false;
 #pragma unroll 1
         for (int h = 0; h < N / 2; h += 32) {
@@ -868,6 +917,25 @@ bool update_n(gp_t h, int k0, int nsrc, int j0, int w)
     return launch(h, GP_PH_UPDATE, mA, mB, op, (w * (w - 1) / 2 + w * (T - j0 - w + 1)) * (b / 128) * (b / N));
 }
 
+// The super-block inverses' planes as a B operand: rows are X_I rows (I B ..),
+// k (or n, MN-major) along X_I's columns.
+bool map_sbx(gp_t h, CUtensorMap* m, int box_rows, bool mn, int planes)
+{
+    const int64_t SBb = GP_SOLVE_SB * h->b, TS = (h->T + GP_SOLVE_SB - 1) / GP_SOLVE_SB;
+    return map_tiles(m, h->XsbP, 3 * TS * SBb, SBb, TS * SBb, box_rows, mn, planes);
+}
+
+template <int N, int P>
+bool diag_w_sb_n(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t I)
+{
+    const int64_t b = h->b, SBb = GP_SOLVE_SB * b, t0 = I * GP_SOLVE_SB;
+    const int64_t st = h->T - t0 < GP_SOLVE_SB ? h->T - t0 : GP_SOLVE_SB;
+    CUtensorMap mA, mB;
+    if (!map_tiles(&mA, h->RP, 3 * ldm, SBb, ldm, 128, false, P) || !map_sbx(h, &mB, N, false, P)) return false;
+    OpDiagWSB<N, P> op{h->WP, R, vpart, h->Np, ldm, (int)(t0 * b), (int)(I * SBb), (int)(st * b / N), (int)(ldm / 128)};
+    return launch(h, phase, mA, mB, op, op.Qn * op.nmb);
+}
+
 template <int N, int P>
 bool diag_w_n(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j)
 {
@@ -925,15 +993,15 @@ bool lauum_n(gp_t h)
 }
 
 template <int N, int P>
-bool bdiag_n(gp_t h, int64_t ldm, int64_t i)
+bool bdiag_sb_n(gp_t h, int64_t ldm, int64_t I)
 {
-    const int b = (int)h->b, T = (int)h->T;
+    const int64_t b = h->b, SBb = GP_SOLVE_SB * b, t0 = I * GP_SOLVE_SB;
+    const int64_t st = h->T - t0 < GP_SOLVE_SB ? h->T - t0 : GP_SOLVE_SB;
     CUtensorMap mA, mB;
-    if (!map_tiles(&mA, h->RP, 3 * ldm, b, ldm, 128, false, P) ||
-        !map_tiles(&mB, h->LinvP, 3 * (int64_t)T * b, b, b, N, true, P))
-        return false;
-    OpBDiag<N, P> op{h->R32, h->WP, h->Np, ldm, b, (int)i, b / N, (int)(ldm / 128)};
-    return launch(h, GP_PH_BSOLVE, mA, mB, op, (b / N) * (int)(ldm / 128));
+    if (!map_tiles(&mA, h->RP, 3 * ldm, SBb, ldm, 128, false, P) || !map_sbx(h, &mB, N, true, P)) return false;
+    OpBDiagSB<N, P> op{h->R32,         h->WP,           h->Np, ldm, (int)(t0 * b), (int)(I * SBb), (int)(st * b),
+                     (int)(st * b / N), (int)(ldm / 128)};
+    return launch(h, GP_PH_BSOLVE, mA, mB, op, op.Qn * op.nmb);
 }
 
 template <int N, int P>
@@ -958,6 +1026,11 @@ bool tg_update(gp_t h, int k0, int nsrc, int j0, int w)
 
 // Sweep products with P operand planes: the 128- or 256-wide instantiation.
 template <int P>
+bool diag_w_sb_p(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t I)
+{
+    return wide(h) ? diag_w_sb_n<256, P>(h, phase, R, ldm, vpart, I) : diag_w_sb_n<128, P>(h, phase, R, ldm, vpart, I);
+}
+template <int P>
 bool diag_w_p(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j)
 {
     return wide(h) ? diag_w_n<256, P>(h, phase, R, ldm, vpart, j) : diag_w_n<128, P>(h, phase, R, ldm, vpart, j);
@@ -969,10 +1042,11 @@ bool upd_w_p(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0,
                    : upd_w_n<128, P>(h, phase, R, ldm, j0, nsrc, i0, ni);
 }
 template <int P>
-bool bdiag_p(gp_t h, int64_t ldm, int64_t i)
+bool bdiag_sb_p(gp_t h, int64_t ldm, int64_t I)
 {
-    return wide(h) ? bdiag_n<256, P>(h, ldm, i) : bdiag_n<128, P>(h, ldm, i);
+    return wide(h) ? bdiag_sb_n<256, P>(h, ldm, I) : bdiag_sb_n<128, P>(h, ldm, I);
 }
+
 template <int P>
 bool bupd_p(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj)
 {
@@ -994,6 +1068,10 @@ bool tg_trtri_acc(gp_t h, int t0, int t1, int i0, int ni, int nj)
     return wide(h) ? trtri_acc_n<256>(h, t0, t1, i0, ni, nj) : trtri_acc_n<128>(h, t0, t1, i0, ni, nj);
 }
 bool tg_lauum(gp_t h) { return wide(h) ? lauum_n<256>(h) : lauum_n<128>(h); }
+bool tg_diag_w_sb(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t I, int planes)
+{
+    return planes == 2 ? diag_w_sb_p<2>(h, phase, R, ldm, vpart, I) : diag_w_sb_p<3>(h, phase, R, ldm, vpart, I);
+}
 bool tg_diag_w(gp_t h, int phase, float* R, int64_t ldm, double* vpart, int64_t j, int planes)
 {
     return planes == 2 ? diag_w_p<2>(h, phase, R, ldm, vpart, j) : diag_w_p<3>(h, phase, R, ldm, vpart, j);
@@ -1003,10 +1081,11 @@ bool tg_upd_w(gp_t h, int phase, float* R, int64_t ldm, int j0, int nsrc, int i0
     return planes == 2 ? upd_w_p<2>(h, phase, R, ldm, j0, nsrc, i0, ni)
                        : upd_w_p<3>(h, phase, R, ldm, j0, nsrc, i0, ni);
 }
-bool tg_bdiag(gp_t h, int64_t ldm, int64_t i, int planes)
+bool tg_bdiag_sb(gp_t h, int64_t ldm, int64_t I, int planes)
 {
-    return planes == 2 ? bdiag_p<2>(h, ldm, i) : bdiag_p<3>(h, ldm, i);
+    return planes == 2 ? bdiag_sb_p<2>(h, ldm, I) : bdiag_sb_p<3>(h, ldm, I);
 }
+
 bool tg_bupd(gp_t h, int64_t ldm, int i0, int nsrc, int j0, int nj, int planes)
 {
     return planes == 2 ? bupd_p<2>(h, ldm, i0, nsrc, j0, nj) : bupd_p<3>(h, ldm, i0, nsrc, j0, nj);
