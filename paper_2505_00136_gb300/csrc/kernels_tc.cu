@@ -9,10 +9,13 @@
 // given as BF16 slices of integer digits (|d| <= 2^GP_OZ_BITS, exact in
 // BF16), C = sum over digit pairs (s, u) with s + u <= GP_OZ_LMAX of
 // 2^{-GP_OZ_BITS (s+u)} Y_s K_u.  Pairs of equal level l = s + u share one
-// FP32 accumulator: at most two pairs per level, each product at most
-// 2^(2 GP_OZ_BITS), so an exact chunk of OZT_CHUNK k (2 x 512 x 2^14 = 2^24)
-// stays exact in FP32, and each chunk sum is added into a double-FP32
-// (hi + lo) running sum, about 48 bits, held in registers.  The fused
+// FP32 accumulator.  The leading digits are at most 2^GP_OZ_BITS in
+// magnitude, the others at most 2^(GP_OZ_BITS-1), so the digit products of
+// one level sum to at most 2^(2 GP_OZ_BITS) = 2^14 per k (level 2: d_1 e_1;
+// level 3: two products of at most 2^13; higher levels: 2^13 + 2^12), and a
+// chunk of OZT_CHUNK = 1024 k stays below 2^24, exact in FP32; each chunk sum
+// is added into a double-FP32 (hi + lo) running sum, about 48 bits, held in
+// registers.  The fused
 // epilogue forms r0 = Kc - C and the partial row sums of Kc x~0 and x~0 r0
 // (the terms k*^T x~0 and x~0^T r0 of the corrected variance).
 //
@@ -51,7 +54,7 @@ constexpr int OZT_STAGES = 5;
 constexpr int OZT_KS = 32;                                 // k per stage
 constexpr int OZT_SLOT = 128 * OZT_KS * 2;                 // one 128 x 32 BF16 tile, 64-byte swizzle
 constexpr int OZT_STAGE_BYTES = 5 * OZT_SLOT;              // Y_1, Y_2 and up to three K slices
-constexpr int OZT_CHUNK = 512;                             // k per exact chunk
+constexpr int OZT_CHUNK = 1024;                            // k per exact chunk
 constexpr int OZT_STAGES_PER_CHUNK = OZT_CHUNK / OZT_KS;
 constexpr int OZT_GROUPS = 3;                              // levels (2, 3), (4, 5), (6, 7)
 constexpr int OZT_THREADS = 320;
@@ -60,7 +63,7 @@ constexpr int OZT_BAR_OFF = OZT_STAGES * OZT_STAGE_BYTES;
 constexpr int OZT_SMEM = 1024 + OZT_BAR_OFF + 256;
 constexpr int OZT_RASTER = 16;                             // row blocks that share a K column block in flight
 constexpr uint32_t OZT_IDESC = tc::idesc_bf16(128, 128);
-static_assert((2 * OZT_CHUNK) << (2 * GP_OZ_BITS) <= (1 << 24), "a level's chunk sum must stay exact in FP32");
+static_assert(OZT_CHUNK << (2 * GP_OZ_BITS) <= (1 << 24), "a level's chunk sum must stay exact in FP32");
 static_assert(OZT_SMEM <= 227 * 1024, "shared memory");
 
 // Lowest K slice (1-based) and number of K slices of group g (levels 2g + 2, 2g + 3):
