@@ -40,9 +40,9 @@ METRIC = "predict+variance ms & NLML+grad steps/s @n=32768; mixed vs FP64 at 1e-
 # Exact digit-pair products of k_ozaki_tc: x~0 in 2 digits, K in 6, pairs (s, u) with s + u <= 7.
 OZAKI_PAIRS = 11
 # DRAM bytes (read + write) of one k_ozaki_tc launch at N = 32768, M = 8192: the ncu
-# capture of the current kernel at N = 8192, M = 2048 (1.645 GB) scaled by the operand
+# capture of the current kernel at N = 8192, M = 2048 (1.647 GB) scaled by the operand
 # stream M N^2 (x 64); None for any other size.
-OZAKI_TRAFFIC_FULL = 1.645e9 * 64
+OZAKI_TRAFFIC_FULL = 1.647e9 * 64
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL_BF16_TFLOPS = 2250.0      # dense, per GPU
 NOMINAL_FP64_TFLOPS = 1.25

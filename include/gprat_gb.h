@@ -287,9 +287,10 @@ typedef struct {
 gp_status gp_info(gp_t h, gp_info_t* out);
 
 /* Allocation-free predictive mean (no counterpart in the paper).  For callers
- * that cannot allocate device memory - code running during CUDA graph capture,
- * servers whose device memory belongs to a pool fixed at start-up, plug-ins of
- * hosts that forbid allocation - this computes mean = K_{Z*,Z} alpha (Eq. 3)
+ * that cannot allocate device memory - servers whose device memory belongs to
+ * a pool fixed at start-up, latency-bound loops that must not enter the
+ * allocator, plug-ins of hosts that forbid allocation - this computes
+ * mean = K_{Z*,Z} alpha (Eq. 3)
  * from trained weights (alpha from gp_get_alpha) without a handle and without
  * any cudaMalloc, cudaFree or allocating library call.  The kernel is the
  * squared exponential of Eq. 2.

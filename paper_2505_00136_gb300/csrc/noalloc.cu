@@ -1,8 +1,8 @@
 // Allocation-free predictive mean, gp_predict_mean_noalloc (see include/gprat_gb.h).
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
-// graph is being captured, serving processes whose device memory is fixed at
-// start-up by a pool they do not own, or plug-ins of a host application that
+// Some callers cannot call cudaMalloc at all: serving processes whose device
+// memory is fixed at start-up by a pool they do not own, latency-bound loops
+// that must not enter the allocator, or plug-ins of a host application that
 // forbids allocation after initialisation.  This entry point serves them: it
 // computes mean = K_{Z*,Z} alpha (Eq. 3) from caller-owned device buffers and
 // keeps its only scratch - per-chunk partial sums - in the file-scope device

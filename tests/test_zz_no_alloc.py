@@ -1,5 +1,6 @@
 """The allocation-free predictive mean, for callers that cannot allocate device
-memory (graph capture, fixed memory pools, hosts that forbid allocation).
+memory (fixed memory pools, loops that must not enter the allocator, hosts
+that forbid allocation).
 
 gp_predict_mean_noalloc is called through the C ABI on caller-owned device
 buffers and compared with the handle-based gp_predict_mean on the same inputs,
