@@ -44,7 +44,8 @@ def g():
 
 
 @pytest.mark.parametrize("n,m,d,n_tiles", [(1024, 1024, 8, 4), (1000, 77, 3, 4), (130, 5, 2, 1),
-                                           (2048, 200, 8, 16)])
+                                           (2048, 200, 8, 16),
+                                           (1500, 150, 8, 6), (1200, 64, 5, 5)])   # short last super-block of the solves
 def test_mixed_against_oracle(g, orc, n, m, d, n_tiles):
     X, y, Xs, _ = dg.msd_dataset(n, m, d, seed=1001 + n)
     hyp = (1.0, 1.0, 0.1)
