@@ -376,19 +376,41 @@ gp_status gp_mlp_adam(float* model, const float* gW, float* m, float* v, int64_t
 gp_status gp_learned_init(const double* X, const double* y, int64_t n, int64_t d, const float* model,
                           const double* omega, double* scratch, gp_hyper* out, void* stream)
 {
-    if (!X || !y || !model || !omega || !scratch || !out || n < 2 || d < 1 || d > 1024) return GP_ERR_ARG;
-    if (!dev_ptr(X) || !dev_ptr(y) || !dev_ptr(model) || !dev_ptr(omega) || !dev_ptr(scratch))
-        return GP_ERR_ARG;
+    if (!X || !y || !model || !omega || !out || n < 2 || d < 1 || d > 1024) return GP_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    // scratch (doubles): [0..63] summary, [64..66] theta, [68..69] the 3 floats of network output
-    float* o = (float*)(scratch + 68);
-    k_summary<<<1, NT, 0, st>>>(X, y, n, d, omega, scratch);
-    k_mlp_forward<<<1, NT, 0, st>>>(model, scratch, 1, o);
-    k_theta_out<<<1, 32, 0, st>>>(o, scratch + 64);
+    // Host arguments (and a NULL or host scratch) are staged in stream-ordered
+    // device memory for this call and released before it returns.
+    void* staged[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int ns = 0;
+    bool ok = true;
+    auto on_device = [&](const void* p, size_t bytes, bool copy) -> const void* {
+        if (!ok) return nullptr;
+        if (p && dev_ptr(p)) return p;
+        void* q = nullptr;
+        if (cudaMallocAsync(&q, bytes, st) != cudaSuccess) {
+            ok = false;
+            return nullptr;
+        }
+        staged[ns++] = q;
+        if (copy && cudaMemcpyAsync(q, p, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) ok = false;
+        return q;
+    };
+    const double* Xd = (const double*)on_device(X, (size_t)(n * d) * sizeof(double), true);
+    const double* yd = (const double*)on_device(y, (size_t)n * sizeof(double), true);
+    const float* md = (const float*)on_device(model, (size_t)GP_MLP_MODEL_FLOATS * sizeof(float), true);
+    const double* od = (const double*)on_device(omega, 8 * sizeof(double), true);
+    double* sd = (double*)on_device(scratch, GP_LEARNED_INIT_SCRATCH * sizeof(double), false);
     double th[3];
-    if (cudaMemcpyAsync(th, scratch + 64, sizeof(th), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return GP_ERR_CUDA;
+    if (ok) {
+        // scratch (doubles): [0..63] summary, [64..66] theta, [68..69] the 3 floats of network output
+        float* o = (float*)(sd + 68);
+        k_summary<<<1, NT, 0, st>>>(Xd, yd, n, d, od, sd);
+        k_mlp_forward<<<1, NT, 0, st>>>(md, sd, 1, o);
+        k_theta_out<<<1, 32, 0, st>>>(o, sd + 64);
+        if (cudaMemcpyAsync(th, sd + 64, sizeof(th), cudaMemcpyDeviceToHost, st) != cudaSuccess) ok = false;
+    }
+    for (int i = 0; i < ns; ++i) cudaFreeAsync(staged[i], st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || !ok) return GP_ERR_CUDA;
     if (!(th[0] > 0.0) || !(th[1] > 0.0) || !(th[2] >= 0.0) || !isfinite(th[0]) || !isfinite(th[1]) ||
         !isfinite(th[2]))
         return GP_ERR_STATE;

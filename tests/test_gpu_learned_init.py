@@ -98,6 +98,28 @@ def test_weight_adam_matches_torch_adam(env):
     assert rel(Wd[:gprat.GP_MLP_NPARAM].cpu().numpy(), p.detach().cpu().numpy()) < 1e-6
 
 
+def test_learned_init_takes_host_or_device_buffers(env):
+    """gp_learned_init detects host and device pointers per argument: the
+    same data, network and frequencies from host memory (scratch NULL) and
+    from device memory give the same hyperparameters."""
+    torch, gprat, _ = env
+    import ctypes
+    X, y, _, _ = dg.msd_dataset(512, 0, 16, seed=77)
+    om = dg.rff_frequencies()
+    W, Wd = _random_model(torch, gprat, 5)
+    Xd, yd, omd = (torch.from_numpy(a).cuda() for a in (X, y, om))
+    scratch = torch.empty(gprat.GP_LEARNED_INIT_SCRATCH, dtype=torch.float64, device="cuda")
+    hd, hh = gprat.gp_hyper(), gprat.gp_hyper()
+    assert gprat.gp_learned_init(Xd.data_ptr(), yd.data_ptr(), 512, 16, Wd.data_ptr(), omd.data_ptr(),
+                                 scratch.data_ptr(), ctypes.byref(hd), None) == 0
+    Xh, yh, omh = (np.ascontiguousarray(a) for a in (X, y, om))
+    assert gprat.gp_learned_init(Xh.ctypes.data, yh.ctypes.data, 512, 16, W.ctypes.data, omh.ctypes.data, None,
+                                 ctypes.byref(hh), None) == 0
+    a = [hd.lengthscale, hd.vertical, hd.noise_var]
+    b = [hh.lengthscale, hh.vertical, hh.noise_var]
+    assert all(np.isfinite(a)) and a == b, (a, b)
+
+
 def test_learned_initialiser_cuts_adam_steps(env):
     """Small corpus (192 systems, n=256, 32 lagged inputs, labels = log theta
     after 600 Adam steps from the default): the trained network's
