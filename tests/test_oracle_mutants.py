@@ -38,6 +38,28 @@ MUTANTS = {
                               "return nu * s * s * (1.0 + s) * exp(-s);"),
     "matern_squared_distance": ("out[i * nb + j] = matern(kind, sqrt(sqdist(A + i * d, B + j * d, d)), l, nu);",
                                 "out[i * nb + j] = matern(kind, sqdist(A + i * d, B + j * d, d), l, nu);"),
+    "chol_inverse_transposed": ("s += Linv[k * n + i] * Linv[k * n + j];", "s += Linv[i * n + k] * Linv[j * n + k];"),
+    "tri_inverse_row_col": ("for (int64_t i = 0; i < n; ++i) Linv[i * n + c] = col[i];",
+                            "for (int64_t i = 0; i < n; ++i) Linv[c * n + i] = col[i];"),
+    "logdet_doubled": ("logdet_half += log(L[i * n + i]);", "logdet_half += 2.0 * log(L[i * n + i]);"),
+    "nlml_2pi_dropped": (" + 0.5 * (double)n * log(2.0 * M_PI);", ";"),
+    "grad_nu_kernel_dropped": ("g_nu += w * kf;", "g_nu += w;"),
+    "grad_weight_sign": ("double w = Kinv[i * n + j] - alpha[i] * alpha[j];",
+                         "double w = Kinv[i * n + j] + alpha[i] * alpha[j];"),
+    "se_nu_dropped_in_gradient": ("kf = nu * exp(-r2 / (2.0 * l * l));", "kf = exp(-r2 / (2.0 * l * l));"),
+    "variance_noise_prior_dropped": ("double prior = hyp[1] + (noisy ? hyp[2] : 0.0);", "double prior = hyp[1];"),
+    "covariance_noise_dropped": ("if (noisy) cov[i * m + i] += hyp[2];", ""),
+    "summary_sample_sd": ("sd[k] = sqrt(v / (double)n);", "sd[k] = sqrt(v / (double)(n - 1));"),
+    "summary_sorted_ascending": ("return (x < y) - (x > y);", "return (x > y) - (x < y);"),
+    "summary_fourier_swapped": ("s[48 + 2 * q] = cs / (double)n;\n        s[49 + 2 * q] = sn / (double)n;",
+                                "s[48 + 2 * q] = sn / (double)n;\n        s[49 + 2 * q] = cs / (double)n;"),
+    "summary_acf_uncentred": ("c += (y[i] - ybar) * (y[i + lag] - ybar);", "c += y[i] * y[i + lag];"),
+    "mlp_loss_gradient_factor": ("dO[j] = 2.0 * e * scale;", "dO[j] = e * scale;"),
+    "mlp_output_bias_dropped": ("double a = W[OFF_B3 + j];", "double a = 0.0;"),
+    "adam_eps_inside_sqrt": ("theta[p] -= lr * mhat / (sqrt(vhat) + eps);",
+                             "theta[p] -= lr * mhat / sqrt(vhat + eps);"),
+    "adam_second_moment_not_squared": ("vel[p] = beta2 * vel[p] + (1.0 - beta2) * g[p] * g[p];",
+                                       "vel[p] = beta2 * vel[p] + (1.0 - beta2) * fabs(g[p]);"),
     # Adam on the natural scale instead of log theta: every site of the log/exp map replaced
     "optimize_natural_scale": [
         ("double theta[3] = {log(hyp[0]), log(hyp[1]), log(hyp[2])};", "double theta[3] = {hyp[0], hyp[1], hyp[2]};"),
