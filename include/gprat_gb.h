@@ -14,6 +14,8 @@
  *  - Pointers may be host or device memory; each call detects which with
  *    cudaPointerGetAttributes.  Host outputs are written before the call
  *    returns; device outputs are written in order on the handle's stream.
+ *    Device memory of a GPU other than the current one is treated like host
+ *    memory (moved by copies, never addressed by a kernel).
  *  - gp_create copies X and y into device memory owned by the handle; the
  *    caller owns every output buffer; gp_destroy frees all handle memory.
  *  - Work is issued on gp_options.cuda_stream (NULL: the legacy default
@@ -223,8 +225,9 @@ gp_status gp_get_alpha(gp_t h, double* alpha_out);
  * Learned hyperparameter initialiser (no counterpart in the paper).  A
  * 64-dimensional summary of a data set feeds a 64 -> 256 -> 256 -> 3 ReLU
  * MLP whose outputs are initial (log l, log nu, log sigma^2).  The buffers of
- * the training calls below are DEVICE memory (gp_learned_init also takes host
- * memory); calls are stream-ordered on `stream`.
+ * the training calls below are DEVICE memory of the current GPU (GP_ERR_ARG
+ * otherwise; gp_learned_init also takes host memory); calls are
+ * stream-ordered on `stream`.
  *
  * Model blob (GP_MLP_MODEL_FLOATS floats): W1[256][64] b1[256] W2[256][256]
  * b2[256] W3[3][256] b3[3] (the GP_MLP_NPARAM trained values), then the
@@ -257,10 +260,11 @@ gp_status gp_mlp_adam(float* model, const float* gW, float* m, float* v, int64_t
 /* Initial hyperparameters for a data set: summary -> network -> exp, written
  * to *out (host) on their natural scale; scratch holds GP_LEARNED_INIT_SCRATCH
  * doubles.  Unlike the calls above, X, y, model and omega may each be host or
- * device memory (detected per pointer; host ones are copied into
- * stream-ordered device memory for the call), and scratch may be NULL or host
- * memory (a device scratch is then allocated for the call); with device
- * buffers throughout nothing is allocated.  Synchronises.  GP_ERR_STATE if the
+ * device memory (detected per pointer; host ones, and those on another GPU,
+ * are copied into stream-ordered device memory for the call), and scratch may
+ * be NULL, host memory or another GPU's (a device scratch is then allocated
+ * for the call); with buffers of the current device throughout nothing is
+ * allocated.  Synchronises.  GP_ERR_STATE if the
  * network output is not finite. */
 gp_status gp_learned_init(const double* X, const double* y, int64_t n, int64_t d, const float* model,
                           const double* omega, double* scratch, gp_hyper* out, void* stream);

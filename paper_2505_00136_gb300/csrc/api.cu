@@ -16,6 +16,10 @@ constexpr int64_t TB = GP_TB;
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// True when this device's kernels may address p directly: managed memory or
+// device memory of the current device.  Device memory of another GPU is then
+// handled like host memory, through staging buffers and cudaMemcpyDefault
+// copies, so no kernel dereferences it without peer access.
 bool is_device_ptr(const void* p)
 {
     cudaPointerAttributes a;
@@ -23,7 +27,9 @@ bool is_device_ptr(const void* p)
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    return a.type == cudaMemoryTypeDevice && cudaGetDevice(&dev) == cudaSuccess && a.device == dev;
 }
 
 gp_status cuda_status(gp_t h, cudaError_t e)

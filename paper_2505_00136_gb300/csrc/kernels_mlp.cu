@@ -306,6 +306,8 @@ __global__ void k_theta_out(const float* o, double* out)
 using namespace gpk;
 
 namespace {
+// Managed memory or device memory of the current device (memory of another
+// GPU is refused by the device-only calls and copied by gp_learned_init).
 bool dev_ptr(const void* p)
 {
     cudaPointerAttributes a;
@@ -313,7 +315,9 @@ bool dev_ptr(const void* p)
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    return a.type == cudaMemoryTypeDevice && cudaGetDevice(&dev) == cudaSuccess && a.device == dev;
 }
 gp_status launched() { return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA; }
 int64_t nblocks(int64_t B) { return (B + SB - 1) / SB; }
@@ -378,8 +382,9 @@ gp_status gp_learned_init(const double* X, const double* y, int64_t n, int64_t d
 {
     if (!X || !y || !model || !omega || !out || n < 2 || d < 1 || d > 1024) return GP_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    // Host arguments (and a NULL or host scratch) are staged in stream-ordered
-    // device memory for this call and released before it returns.
+    // Host arguments, those in another GPU's memory, and a NULL or host scratch
+    // are staged in stream-ordered device memory for this call and released
+    // before it returns.
     void* staged[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int ns = 0;
     bool ok = true;
@@ -392,7 +397,7 @@ gp_status gp_learned_init(const double* X, const double* y, int64_t n, int64_t d
             return nullptr;
         }
         staged[ns++] = q;
-        if (copy && cudaMemcpyAsync(q, p, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) ok = false;
+        if (copy && cudaMemcpyAsync(q, p, bytes, cudaMemcpyDefault, st) != cudaSuccess) ok = false;
         return q;
     };
     const double* Xd = (const double*)on_device(X, (size_t)(n * d) * sizeof(double), true);
