@@ -105,3 +105,53 @@ def test_kernel_and_precision_options_are_validated(lib):
         st = gprat.gp_create(X.ctypes.data, y.ctypes.data, 64, 2, ctypes.byref(hp), ctypes.byref(opt),
                              ctypes.byref(h))
         assert st == gprat.GP_ERR_ARG and not h.value
+
+
+def test_other_entry_points_refuse_bad_arguments_before_any_cuda_call(lib):
+    """NULL buffers, empty or oversize problems and invalid options are refused
+    with GP_ERR_ARG by every other entry point, before any device work."""
+    from paper_2505_00136_gb300 import gprat as g
+    X = np.zeros((8, 2))
+    y = np.zeros(8)
+    px, py = X.ctypes.data, y.ctypes.data
+    hp = g.gp_hyper(1.0, 1.0, 0.1, (ctypes.c_int * 3)(1, 1, 1))
+    out = g.gp_hyper()
+    h = g._H()
+    # scheduler and DAG options
+    for field, bad in (("scheduler", 2), ("scheduler", -1), ("dag_timeout_ms", -5)):
+        opt = g.default_options()
+        setattr(opt, field, bad)
+        assert g.gp_create(px, py, 8, 2, ctypes.byref(hp), ctypes.byref(opt), ctypes.byref(h)) == g.GP_ERR_ARG
+    opt = g.default_options()
+    opt.scheduler = g.GP_SCHED_PERSISTENT        # the persistent DAG kernel is FP64 only
+    opt.prec = g.GP_MIXED
+    assert g.gp_create(px, py, 8, 2, ctypes.byref(hp), ctypes.byref(opt), ctypes.byref(h)) == g.GP_ERR_ARG
+    # hyperparameters: nu must be positive, sigma^2 non-negative
+    for bad in ((1.0, 0.0, 0.1), (1.0, 1.0, -0.1), (0.0, 1.0, 0.1)):
+        bh = g.gp_hyper(*bad, (ctypes.c_int * 3)(1, 1, 1))
+        assert g.gp_create(px, py, 8, 2, ctypes.byref(bh), None, ctypes.byref(h)) == g.GP_ERR_ARG
+    assert g.gp_create(px, py, 8, 2, ctypes.byref(hp), None, None) == g.GP_ERR_ARG
+    # calls on a NULL handle
+    d = ctypes.c_double()
+    for st in (g.gp_predict_mean(None, px, 4, px), g.gp_predict_var(None, px, 4, px, px),
+               g.gp_predict_full_cov(None, px, 4, px, px), g.gp_predict(None, px, 4, px, None, None),
+               g.gp_nlml(None, ctypes.byref(d)), g.gp_optimize(None, 1, 0.1, None),
+               g.gp_get_hyper(None, ctypes.byref(out)), g.gp_set_hyper(None, ctypes.byref(hp)),
+               g.gp_get_factor(None, px), g.gp_get_alpha(None, px)):
+        assert st == g.GP_ERR_ARG
+    # learned initialiser and its training calls
+    assert g.gp_learned_init(None, py, 8, 2, px, px, None, ctypes.byref(out), None) == g.GP_ERR_ARG
+    assert g.gp_learned_init(px, py, 1, 2, px, px, None, ctypes.byref(out), None) == g.GP_ERR_ARG
+    assert g.gp_learned_init(px, py, 8, 0, px, px, None, ctypes.byref(out), None) == g.GP_ERR_ARG
+    assert g.gp_summary(None, py, 8, 2, px, px, None) == g.GP_ERR_ARG
+    assert g.gp_summary(px, py, 1, 2, px, px, None) == g.GP_ERR_ARG
+    assert g.gp_mlp_forward(px, px, 0, px, None) == g.GP_ERR_ARG
+    assert g.gp_mlp_adam(px, px, px, px, 0, 0.1, 0.9, 0.999, 1e-8, None) == g.GP_ERR_ARG
+    assert g.gp_mlp_adam(px, px, px, px, 1, 0.0, 0.9, 0.999, 1e-8, None) == g.GP_ERR_ARG
+    assert g.gp_mlp_workspace_floats(0) == 0
+    assert g.gp_mlp_workspace_floats(17) == 2 * (g.GP_MLP_NPARAM + 1)   # 16 samples per block
+    # allocation-free mean: sizes (at most GP_NOALLOC_MAX_TEST = 32768 test points) and hyperparameters
+    for args in ((None, px, 8, 2, px, 4, 1.0, 1.0), (px, px, 0, 2, px, 4, 1.0, 1.0),
+                 (px, px, 8, 2, px, 0, 1.0, 1.0), (px, px, 8, 2, px, 32768 + 1, 1.0, 1.0),
+                 (px, px, 8, 2, px, 4, float("nan"), 1.0), (px, px, 8, 2, px, 4, 1.0, -1.0)):
+        assert g.gp_predict_mean_noalloc(*args, px, None) == g.GP_ERR_ARG
