@@ -77,3 +77,23 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_reference_arm_prints_one_contract_line_on_rank_zero():
+    """Rank 0 times the CPU oracle on a bounded sample and prints one JSON line
+    with the contract's keys, its cpu_baseline and a zero-copy e2e."""
+    env = _env(0, 1, _free_port())
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--cpu-sample-n", "256", "--cpu-sample-m", "64"],
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr
+    lines = [l for l in p.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    r = json.loads(lines[0])
+    assert r["impl"] == "reference" and r["unit"] == "ms" and r["higher_is_better"] is False
+    assert r["n_gpus"] == 1 and r["steps"] == 2 and r["warmup"] == 1
+    assert r["value"] > 0 and r["ms_per_step"] == r["value"]
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and "N=256" in cb["sample"]
+    assert r["e2e"] == {"value": r["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert r["config"]["n_train"] == 32768 and r["config"]["n_test"] == 8192
