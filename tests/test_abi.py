@@ -155,3 +155,16 @@ def test_other_entry_points_refuse_bad_arguments_before_any_cuda_call(lib):
                  (px, px, 8, 2, px, 0, 1.0, 1.0), (px, px, 8, 2, px, 32768 + 1, 1.0, 1.0),
                  (px, px, 8, 2, px, 4, float("nan"), 1.0), (px, px, 8, 2, px, 4, 1.0, -1.0)):
         assert g.gp_predict_mean_noalloc(*args, px, None) == g.GP_ERR_ARG
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """The binding has no CPU fallback: a copy of it next to no built library
+    raises ImportError on import."""
+    import importlib.util
+    import shutil
+    src = os.path.join(ROOT, "paper_2505_00136_gb300", "gprat.py")
+    shutil.copy(src, tmp_path / "gprat.py")
+    spec = importlib.util.spec_from_file_location("gprat_without_library", str(tmp_path / "gprat.py"))
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError, match="not built"):
+        spec.loader.exec_module(mod)
