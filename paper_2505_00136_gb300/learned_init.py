@@ -135,7 +135,7 @@ def run(n_train_sys=256, n_eval_sys=32, n=256, n_eval=256, d=32, label_steps=600
         epochs=600, lr=1e-3, rtol=1e-6, first_seed=20000, precision="fp64", workers=8, n_tiles=4):
     """Corpus -> labels -> training -> evaluation; returns a dict of results.
 
-    The judge of convergence is the default run's own optimum: NLML* = the
+    Convergence is measured against the default run's own optimum: NLML* = the
     minimum over eval_steps Adam steps (lr 0.1) from the default start.  Steps
     to converge = the first step whose NLML is within rtol of NLML* (or below
     it), for the default and the learned start alike; a learned run that never
