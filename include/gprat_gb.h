@@ -314,9 +314,8 @@ gp_status gp_info(gp_t h, gp_info_t* out);
  * (16 MiB) in the library's device data, held by every GPU that loads the
  * library until the process exits and shared by all calls on that GPU.  The
  * first call on a device looks its address up (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Calls whose
- * work overlaps on the GPU (different streams, no ordering) race on the scratch
- * and must not be issued. */
+ * device current.  Calls whose work overlaps on the GPU (different streams,
+ * no ordering) race on the scratch and must not be issued. */
 #define GP_NOALLOC_MAX_TEST 32768
 #define GP_NOALLOC_CHUNKS 64
 gp_status gp_predict_mean_noalloc(const double* X, const double* alpha, int64_t n, int64_t d,
