@@ -102,12 +102,19 @@ typedef struct {
     int dag_timeout_ms;     /* GP_SCHED_PERSISTENT: bound on any single dependency wait of
                                the persistent kernel; expiry ends the call with GP_ERR_TIMEOUT */
     gp_kernel kernel;       /* covariance function (default GP_KERNEL_SE) */
+    int jitter_retries;     /* recovery from GP_ERR_NOT_PD, 0..8 (default 0: off).  With k > 0,
+                               a factorisation that meets a non-positive pivot is retried up
+                               to k times, try t with sigma^2 = sigma0^2 + 1e-10 nu 100^(t-1);
+                               the first that succeeds is kept (gp_get_hyper returns it,
+                               gp_info reports the added jitter); if none does, sigma0^2 is
+                               restored and GP_ERR_NOT_PD returned.  Applies to gp_factor and
+                               the calls that factor on demand, not to gp_optimize's steps. */
 } gp_options;
 
 /* Fills defaults: n_tiles 16, FP64, latent variance, refine_tol 1e-14,
  * refine_max_iter 20, Adam (0.9, 0.999, 1e-8), default stream, stream
  * scheduler, variance correction on, DAG wait bound 10000 ms, squared
- * exponential kernel. */
+ * exponential kernel, no jitter retries. */
 void gp_default_options(gp_options* opt);
 
 /* Automatic tile count (the tile-size selection the paper leaves to future
@@ -293,6 +300,7 @@ typedef struct {
     int64_t device_bytes;      /* bytes currently held on the device */
     int refine_iters;          /* GP_MIXED: sweeps used by the last alpha solve */
     double refine_residual;    /* GP_MIXED: ||y - K alpha|| / ||y|| after refinement */
+    double jitter_added;       /* sigma^2 added by the last factorisation's retries (0: none) */
 } gp_info_t;
 gp_status gp_info(gp_t h, gp_info_t* out);
 

@@ -395,20 +395,53 @@ gp_status factor_mixed_refined(gp_t h)
     return check_launch(h);
 }
 
-gp_status ensure_factored(gp_t h)
+gp_status factor_once(gp_t h)
 {
-    if (h->factored) return GP_OK;
     gp_status s;
     if (h->opt.prec == GP_MIXED) {
         h->ks_valid = false;
-        if ((s = factor_mixed_refined(h)) != GP_OK) return s;
-        h->factored = true;
-        return GP_OK;
+        return factor_mixed_refined(h);
     }
     launch_factor(h);
-    s = check_launch(h);
+    if ((s = check_launch(h)) != GP_OK) return s;
+    return read_info(h);
+}
+
+// Sets sigma^2 on the host copy and on the device (natural and log scale).
+gp_status put_noise(gp_t h, double s2)
+{
+    h->h_hyp.s2 = s2;
+    h->h_hyp.log_theta[2] = s2 > 0.0 ? log(s2) : -INFINITY;
+    gp_status s = cuda_status(h, cudaMemcpyAsync(h->hyp, &h->h_hyp, sizeof(GpHyperDev), cudaMemcpyHostToDevice, h->st));
+    return s == GP_OK ? sync(h) : s;
+}
+
+gp_status ensure_factored(gp_t h)
+{
+    if (h->factored) return GP_OK;
+    h->jitter_added = 0.0;
+    gp_status s = factor_once(h);
+    if (s == GP_ERR_NOT_PD && h->opt.jitter_retries > 0) {
+        // Optional recovery: retry with a growing diagonal jitter on sigma^2.
+        const int64_t pivot = h->last_info;
+        gp_status r = cuda_status(h, cudaMemcpyAsync(&h->h_hyp, h->hyp, sizeof(GpHyperDev),
+                                                     cudaMemcpyDeviceToHost, h->st));
+        if (r == GP_OK) r = sync(h);
+        if (r != GP_OK) return r;
+        const double s2 = h->h_hyp.s2;
+        double add = 1e-10 * h->h_hyp.nu;
+        for (int t = 0; t < h->opt.jitter_retries && s == GP_ERR_NOT_PD; ++t, add *= 100.0) {
+            if ((r = put_noise(h, s2 + add)) != GP_OK) return r;
+            s = factor_once(h);
+        }
+        if (s == GP_OK) {
+            h->jitter_added = add / 100.0;
+        } else if (s == GP_ERR_NOT_PD) {
+            if ((r = put_noise(h, s2)) != GP_OK) return r;
+            h->last_info = pivot;
+        }
+    }
     if (s != GP_OK) return s;
-    if ((s = read_info(h)) != GP_OK) return s;
     h->factored = true;
     return GP_OK;
 }
@@ -541,6 +574,7 @@ void gp_default_options(gp_options* opt)
     opt->var_correction = 1;
     opt->dag_timeout_ms = 10000;
     opt->kernel = GP_KERNEL_SE;
+    opt->jitter_retries = 0;
 }
 
 const char* gp_status_str(gp_status s)
@@ -591,7 +625,8 @@ gp_status gp_create(const double* X, const double* y, int64_t n, int64_t d, cons
         (opt.prec != GP_FP64 && opt.prec != GP_MIXED && opt.prec != GP_FP64_OZAKI) ||
         (opt.scheduler != GP_SCHED_STREAM && opt.scheduler != GP_SCHED_PERSISTENT) ||
         (opt.scheduler == GP_SCHED_PERSISTENT && opt.prec != GP_FP64) || opt.dag_timeout_ms < 0 ||
-        opt.kernel < GP_KERNEL_SE || opt.kernel > GP_KERNEL_MATERN52)
+        opt.kernel < GP_KERNEL_SE || opt.kernel > GP_KERNEL_MATERN52 || opt.jitter_retries < 0 ||
+        opt.jitter_retries > 8)
         return GP_ERR_ARG;
     if (opt.dag_timeout_ms == 0) opt.dag_timeout_ms = 10000;
     if (opt.n_tiles == 0) {
@@ -980,6 +1015,7 @@ gp_status gp_info(gp_t h, gp_info_t* out)
     out->device_bytes = h->bytes;
     out->refine_iters = h->refine_iters;
     out->refine_residual = h->refine_residual;
+    out->jitter_added = h->jitter_added;
     return GP_OK;
 }
 

@@ -142,6 +142,7 @@ struct gp_handle {
     int64_t last_info;
     int refine_iters;
     double refine_residual;
+    double jitter_added;      // sigma^2 added by the last factorisation's NOT_PD retries
 
     // Launch accounting and optional per-launch event timing (gp_profile).
     int64_t launches;

@@ -45,7 +45,7 @@ class gp_options(ctypes.Structure):
                 ("adam_beta1", ctypes.c_double), ("adam_beta2", ctypes.c_double),
                 ("adam_eps", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("scheduler", ctypes.c_int), ("var_correction", ctypes.c_int),
-                ("dag_timeout_ms", ctypes.c_int), ("kernel", ctypes.c_int)]
+                ("dag_timeout_ms", ctypes.c_int), ("kernel", ctypes.c_int), ("jitter_retries", ctypes.c_int)]
 
 
 class gp_state(ctypes.Structure):
@@ -57,7 +57,7 @@ class gp_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("tile", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int64), ("n_padded", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("refine_iters", ctypes.c_int),
-                ("refine_residual", ctypes.c_double)]
+                ("refine_residual", ctypes.c_double), ("jitter_added", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
@@ -171,7 +171,8 @@ class GP:
 
     def __init__(self, X, y, hyper=(1.0, 1.0, 0.1), trainable=(1, 1, 1), n_tiles=16,
                  precision="fp64", noisy_test_var=False, stream=None, scheduler="stream",
-                 refine_tol=None, refine_max_iter=None, var_correction=True, dag_timeout_ms=None, kernel="se"):
+                 refine_tol=None, refine_max_iter=None, var_correction=True, dag_timeout_ms=None, kernel="se",
+                 jitter_retries=0):
         if not _is_torch(X):
             X = np.ascontiguousarray(X, dtype=np.float64)
             y = np.ascontiguousarray(y, dtype=np.float64)
@@ -190,6 +191,7 @@ class GP:
         if dag_timeout_ms is not None:
             opt.dag_timeout_ms = int(dag_timeout_ms)
         opt.kernel = KERNELS[kernel]
+        opt.jitter_retries = int(jitter_retries)
         if stream is None and self._torch_dev is not None:
             import torch
             stream = torch.cuda.current_stream(self._torch_dev).cuda_stream

@@ -168,3 +168,32 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     mod = importlib.util.module_from_spec(spec)
     with pytest.raises(ImportError, match="not built"):
         spec.loader.exec_module(mod)
+
+
+def test_options_struct_layout_matches_the_binding(lib):
+    """gp_default_options writes exactly the binding's gp_options: every field
+    gets its default and no byte past the struct is touched."""
+    from paper_2505_00136_gb300 import gprat as g
+    size = ctypes.sizeof(g.gp_options)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    g.gp_default_options(ctypes.cast(buf, ctypes.POINTER(g.gp_options)))
+    assert bytes(buf[size:]) == b"\xab" * 64
+    opt = g.gp_options.from_buffer(buf)
+    assert (opt.n_tiles, opt.prec, opt.noisy_test_var, opt.refine_max_iter) == (16, g.GP_FP64, 0, 20)
+    assert (opt.refine_tol, opt.adam_beta1, opt.adam_beta2, opt.adam_eps) == (1e-14, 0.9, 0.999, 1e-8)
+    assert (opt.scheduler, opt.var_correction, opt.dag_timeout_ms) == (g.GP_SCHED_STREAM, 1, 10000)
+    assert (opt.kernel, opt.jitter_retries) == (g.KERNELS["se"], 0)
+    assert opt.cuda_stream is None
+
+
+def test_jitter_retries_option_is_validated(lib):
+    from paper_2505_00136_gb300 import gprat as g
+    X = np.zeros((8, 2))
+    y = np.zeros(8)
+    hp = g.gp_hyper(1.0, 1.0, 0.1, (ctypes.c_int * 3)(1, 1, 1))
+    for bad in (-1, 9):
+        opt = g.default_options()
+        opt.jitter_retries = bad
+        h = g._H()
+        assert g.gp_create(X.ctypes.data, y.ctypes.data, 8, 2, ctypes.byref(hp), ctypes.byref(opt),
+                           ctypes.byref(h)) == g.GP_ERR_ARG

@@ -148,6 +148,29 @@ def test_not_positive_definite_reports_pivot(g):
     assert e.value.status == g.GP_ERR_NOT_PD and e.value.info == 1
 
 
+def test_jitter_retry_recovers_from_a_singular_matrix(g):
+    """Identical inputs with sigma^2 = 0 give K = nu 11^T, singular.  With
+    jitter retries the first try (sigma^2 = 1e-10 nu) factors, the added
+    jitter is reported and kept in the hyperparameters, and the mean at the
+    training input is n nu / (n nu + sigma^2) = 1 - 5e-13 for y = 1."""
+    X = np.zeros((200, 3))
+    y = np.ones(200)
+    with g.GP(X, y, (1.0, 1.0, 0.0), n_tiles=2, jitter_retries=3) as gp:
+        gp.factor()
+        info = gp.info()
+        assert info["jitter_added"] == pytest.approx(1e-10, rel=1e-12)
+        (l, nu, s2), _ = gp.get_hyper()
+        assert s2 == pytest.approx(1e-10, rel=1e-12) and (l, nu) == (1.0, 1.0)
+        mu = gp.predict_mean(X[:4])
+        assert np.allclose(mu, 200.0 / (200.0 + 1e-10), rtol=1e-4)
+    # retries off (the default): the same matrix is refused, sigma^2 untouched
+    with g.GP(X, y, (1.0, 1.0, 0.0), n_tiles=2) as gp:
+        with pytest.raises(g.GPError) as e:
+            gp.factor()
+        assert e.value.status == g.GP_ERR_NOT_PD
+        assert gp.get_hyper()[0][2] == 0.0 and gp.info()["jitter_added"] == 0.0
+
+
 def test_device_buffers_match_host_buffers(g, orc):
     import torch
     X, y, Xs, _ = dg.msd_dataset(400, 100, 8, seed=1006)
